@@ -1,0 +1,181 @@
+/*
+ * fastecdf.h -- C ABI of the GB300 (sm_103a) implementation of the fast exact
+ * multivariate ECDF / ESF and Laplacian-kernel KDE / kernel regression of
+ * Langrene & Warin, "Fast multivariate empirical cumulative distribution
+ * function with connection to kernel density estimation" (arXiv 2005.03246).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Points.  x is [N][d] row-major (point i occupies x[i*d .. i*d+d-1]) in the
+ *   dtype given by `xdtype` (FK_F32 or FK_F64).  Weights y / w, when given, are
+ *   [N] in the same dtype.  Explicit targets z are [M][d] in the same dtype.
+ * Orthants.  The problem statement (Sec. 1, eqs. ECDF, ESF, ECDFdelta) is read
+ *   in the reflected form used by eq. (Laplacian decomposition nD), Sec. 3.1:
+ *   orthant o in [0, 2^d) tests, on every axis k, x_k <= z_k when bit k of o is
+ *   clear (delta_k = +1) and x_k > z_k when bit k is set (delta_k = -1).
+ *   o = 0 is the ECDF (eq. ECDF), o = 2^d - 1 the ESF (eq. ESF); the 2^d
+ *   orthants partition the sources.  A source equal to its target is counted
+ *   once, in orthant 0.
+ * Orthant selection.  `orthant_mask` is a HOST bitset of ceil(2^d/32) uint32
+ *   words (bit o of word o/32 selects orthant o); NULL selects all orthants.
+ *   Outputs hold the selected orthants in increasing index, one row each.
+ * Normalisation.  Orthant outputs are UNNORMALISED sums (Remark 1, Sec. 2.1):
+ *   divide by N for F_N.  Counts (y == NULL) are exact int64.
+ * Precision.  FK_PATH_MIXED accumulates bulk sums in FP32 with compensated
+ *   (two-sum) arithmetic and keeps exponent arithmetic and the final
+ *   combination in FP64; FK_PATH_FP64 does everything in FP64.  Counts are
+ *   exact on both paths.
+ * Memory.  Every array argument may be a device pointer (the normal case) or
+ *   a host pointer; host arrays are staged through device buffers by the
+ *   library and the call then returns only after the host outputs are written.
+ *   With device pointers the call is asynchronous on `stream`.  The caller owns
+ *   every buffer; the library never frees caller memory and keeps no state
+ *   between calls other than the per-device error word (fk_device_status).
+ * Workspace.  `ws`/`ws_bytes` is caller-owned device scratch of at least the
+ *   size returned by the matching *_workspace function (256-byte aligned).
+ *   If ws == NULL the library allocates and frees its scratch itself
+ *   (stream-ordered).  A non-NULL ws that is too small returns FK_ERR_WORKSPACE.
+ * Limits.  1 <= d <= 4 for the sample-point (divide-and-conquer) calls and
+ *   1 <= d <= 8 for the grid call; N + M must be below 2^26 items on the
+ *   sample-point path (2N + ... when orthant sums are taken at the sample
+ *   points, which doubles each point into a source and a target copy).
+ *   Other values return FK_ERR_UNSUPPORTED.
+ * Errors.  Each call returns an fk_status; fk_last_error() gives a thread-local
+ *   message.  Nothing is thrown across the ABI.  Non-finite inputs are not
+ *   checked on the asynchronous path; they do not fault, and make the outputs
+ *   undefined.
+ */
+#ifndef FASTECDF_H
+#define FASTECDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fk_stream_t;   /* same type as cudaStream_t */
+
+typedef enum {
+    FK_OK = 0,
+    FK_ERR_INVALID_ARG = -1,
+    FK_ERR_UNSUPPORTED = -2,
+    FK_ERR_WORKSPACE = -3,
+    FK_ERR_NONFINITE = -4,
+    FK_ERR_CUDA = -5,
+    FK_ERR_TIMEOUT = -6
+} fk_status;
+
+typedef enum { FK_F32 = 0, FK_F64 = 1 } fk_dtype;
+
+typedef enum { FK_PATH_MIXED = 0, FK_PATH_FP64 = 1 } fk_path;
+
+/* flags for the kernel-density calls */
+#define FK_LOO 1u   /* leave one out: at the sample points, drop exactly the i == j term
+                       and normalise by N - 1 */
+
+/* Thread-local description of the last error returned on this thread. */
+const char* fk_last_error(void);
+
+/* Library version string. */
+const char* fk_version(void);
+
+/*
+ * ---------------------------------------------------------------- grid path
+ * fk_ecdf_grid -- orthant sums on a rectilinear grid (Sec. 2.1, Algorithm 1,
+ * with the local sums of Appendix A, Algorithms 6-7).
+ *   z_axes : concatenation of the d grid axes, axis k holding M[k] strictly
+ *            increasing FP64 values (P: "z_{k,1} < ... < z_{k,M_k}"); host or
+ *            device.  Not strictly increasing -> FK_ERR_INVALID_ARG.
+ *   M      : HOST array of d axis lengths, each >= 1.
+ *   y      : [N] weights or NULL (exact int64 counts).
+ *   out    : [n_sel][M[0]]...[M[d-1]] (last axis fastest), int64 when y == NULL,
+ *            else double.  n_sel = number of selected orthants.
+ * Each point is binned with exact comparisons (mesh division plus an exact
+ * fix-up on uniform axes, binary search otherwise), the generalized histogram
+ * of eq. (partial sums) is formed without the 1/N factor (Remark 1), and the
+ * orthant sums are obtained by per-axis inclusive prefix sums (delta_k = +1)
+ * and strict suffix sums (delta_k = -1).
+ */
+size_t fk_ecdf_grid_workspace(int64_t N, int d, const int64_t* M, int weighted, fk_path path);
+fk_status fk_ecdf_grid(const void* x, fk_dtype xdtype, int64_t N, int d, const void* y,
+                       const double* z_axes, const int64_t* M,
+                       const uint32_t* orthant_mask, void* out, fk_path path,
+                       void* ws, size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * -------------------------------------------------------- sample-point path
+ * fk_ecdf_points -- orthant sums at the sample points (z == NULL, M ignored)
+ * or at M explicit targets z [M][d], by rank transform and divide-and-conquer
+ * dominance sums (Sec. 2.2, Algorithms 2-5; all orthants in one recursion as
+ * in Appendix D, Algorithms 8-12).
+ *   out : [n_sel][M'] with M' = N (sample points) or M; int64 when y == NULL,
+ *         else double.
+ */
+size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points,
+                                int weighted, fk_path path);
+fk_status fk_ecdf_points(const void* x, fk_dtype xdtype, int64_t N, int d, const void* y,
+                         const void* z, int64_t M, const uint32_t* orthant_mask,
+                         void* out, fk_path path, void* ws, size_t ws_bytes,
+                         fk_stream_t stream);
+
+/*
+ * fk_esf_points -- the empirical survival function of eq. (ESF), Sec. 1:
+ * sum_i y_i 1{x_i1 > z_1, ..., x_id > z_d}, i.e. orthant 2^d - 1 of
+ * fk_ecdf_points.  out : [M'] int64 (y == NULL) or double.
+ * Workspace: fk_ecdf_points_workspace with the same arguments.
+ */
+fk_status fk_esf_points(const void* x, fk_dtype xdtype, int64_t N, int d, const void* y,
+                        const void* z, int64_t M, void* out, fk_path path,
+                        void* ws, size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_kde_laplace -- Laplacian kernel density estimate, eq. (Laplacian kde nD):
+ *   f(z_j) = 1/(2^d N prod_k h_k) sum_i w_i exp(-sum_k |x_ik - z_jk| / h_k),
+ * assembled from the 2^d exponentially weighted orthant sums of eq.
+ * (Laplacian decomposition nD) with source weights w_i e^{delta.x_i/h}, the
+ * exponent factors carried as an FP64-computed mantissa with a separate
+ * power-of-two shift so that no factor overflows.
+ *   w      : [N] weights or NULL (w == 1).
+ *   z      : [M][d] targets or NULL (the sample points; M ignored).
+ *   h      : HOST [d] bandwidths, each finite and > 0.
+ *   flags  : FK_LOO (only with z == NULL).
+ *   out    : [M'] double.
+ *   orthant_terms : optional [2^d][M'] double; receives the per-orthant terms
+ *            C e^{-delta.z/h} S_delta (their sum is out).
+ */
+size_t fk_kde_laplace_workspace(int64_t N, int d, int64_t M, int sample_points,
+                                int want_terms, fk_path path);
+fk_status fk_kde_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w,
+                         const void* z, int64_t M, const double* h, unsigned flags,
+                         double* out, double* orthant_terms, fk_path path,
+                         void* ws, size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_kreg_laplace -- Nadaraya-Watson kernel regression with the Laplacian
+ * kernel (the weights of eq. localdens carrying the response, Sec. 3.1 and
+ * Sec. 4): m(z_j) = sum_i y_i K_ij / sum_i K_ij, both sums taken by the same
+ * orthant decomposition as fk_kde_laplace.  out : [M'] double; NaN where the
+ * denominator underflows to zero.
+ * Workspace: fk_kde_laplace_workspace(N, d, M, sample_points, 0, path) * 2.
+ */
+size_t fk_kreg_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path);
+fk_status fk_kreg_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const void* y,
+                          const void* z, int64_t M, const double* h, unsigned flags,
+                          double* out, fk_path path, void* ws, size_t ws_bytes,
+                          fk_stream_t stream);
+
+/*
+ * fk_device_status -- synchronises `stream` and returns (and clears) the
+ * device-side error word of the current device: FK_OK, or the first error a
+ * kernel recorded since the last call (e.g. FK_ERR_TIMEOUT from a bounded
+ * wait).  Kernels never trap.
+ */
+fk_status fk_device_status(fk_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTECDF_H */

@@ -1,0 +1,64 @@
+"""ctypes loader for libfastecdf.so (the C ABI of include/fastecdf.h).
+
+Loading fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfastecdf.so")
+
+FK_F32, FK_F64 = 0, 1
+FK_PATH_MIXED, FK_PATH_FP64 = 0, 1
+FK_LOO = 1
+
+STATUS = {0: "FK_OK", -1: "FK_ERR_INVALID_ARG", -2: "FK_ERR_UNSUPPORTED", -3: "FK_ERR_WORKSPACE",
+          -4: "FK_ERR_NONFINITE", -5: "FK_ERR_CUDA", -6: "FK_ERR_TIMEOUT"}
+
+# Every symbol the header declares, with its ctypes signature.
+P, I64, I, U, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t
+SIGNATURES = {
+    "fk_last_error": (ctypes.c_char_p, []),
+    "fk_version": (ctypes.c_char_p, []),
+    "fk_device_status": (I, [P]),
+    "fk_ecdf_grid_workspace": (SZ, [I64, I, P, I, I]),
+    "fk_ecdf_grid": (I, [P, I, I64, I, P, P, P, P, P, I, P, SZ, P]),
+    "fk_ecdf_points_workspace": (SZ, [I64, I, I64, I, I, I]),
+    "fk_ecdf_points": (I, [P, I, I64, I, P, P, I64, P, P, I, P, SZ, P]),
+    "fk_esf_points": (I, [P, I, I64, I, P, P, I64, P, I, P, SZ, P]),
+    "fk_kde_laplace_workspace": (SZ, [I64, I, I64, I, I, I]),
+    "fk_kde_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, P, I, P, SZ, P]),
+    "fk_kreg_laplace_workspace": (SZ, [I64, I, I64, I, I]),
+    "fk_kreg_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
+}
+
+_lib = None
+
+
+class FastEcdfError(RuntimeError):
+    pass
+
+
+def load():
+    """Load the library (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(rc: int, what: str):
+    if rc != 0:
+        msg = load().fk_last_error().decode(errors="replace")
+        raise FastEcdfError("%s failed: %s (%s)" % (what, STATUS.get(rc, rc), msg))

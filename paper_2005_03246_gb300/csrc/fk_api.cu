@@ -1,0 +1,369 @@
+// fk_api.cu -- extern "C" entry points of fastecdf.h: argument validation,
+// host/device staging of the caller's arrays, workspace handling, dispatch.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "fk_dc_ops.cuh"
+
+namespace fk {
+
+static thread_local char g_msg[512] = "no error";
+
+fk_status set_error(fk_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+fk_status cuda_error(cudaError_t e, const char* where) {
+    return set_error(FK_ERR_CUDA, "CUDA error %d (%s) at %s", (int)e, cudaGetErrorString(e), where);
+}
+
+bool is_device_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The per-device error word: kernels record the first device-side error here
+// (atomicCAS from 0); fk_device_status reads and clears it.
+__device__ int g_fk_err_word = 0;
+
+fk_status device_error_word(int** ptr) {
+    FK_CUDA(cudaGetSymbolAddress((void**)ptr, g_fk_err_word));
+    return FK_OK;
+}
+
+// Stages caller arrays that live in host memory through device buffers.
+struct Stager {
+    cudaStream_t st;
+    std::vector<void*> allocs;
+    struct Out { void* dev; void* host; size_t bytes; };
+    std::vector<Out> outs;
+    bool any_host = false;
+    explicit Stager(cudaStream_t s) : st(s) {}
+    ~Stager() {
+        for (void* p : allocs) cudaFreeAsync(p, st);
+    }
+    // input array: returns a device pointer holding the same bytes
+    fk_status in(const void* p, size_t bytes, const void** dev) {
+        *dev = p;
+        if (!p || bytes == 0 || is_device_pointer(p)) return FK_OK;
+        any_host = true;
+        void* d = nullptr;
+        FK_CUDA(cudaMallocAsync(&d, bytes, st));
+        allocs.push_back(d);
+        FK_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, st));
+        *dev = d;
+        return FK_OK;
+    }
+    // output array: device pointer to write; host copies back in finish()
+    fk_status out(void* p, size_t bytes, void** dev) {
+        *dev = p;
+        if (!p || bytes == 0 || is_device_pointer(p)) return FK_OK;
+        any_host = true;
+        void* d = nullptr;
+        FK_CUDA(cudaMallocAsync(&d, bytes, st));
+        allocs.push_back(d);
+        outs.push_back(Out{d, p, bytes});
+        *dev = d;
+        return FK_OK;
+    }
+    fk_status finish() {
+        for (auto& o : outs)
+            FK_CUDA(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
+        if (any_host) FK_CUDA(cudaStreamSynchronize(st));
+        return FK_OK;
+    }
+};
+
+// Workspace: caller scratch, or a stream-ordered allocation of the planned size.
+struct Workspace {
+    cudaStream_t st;
+    void* owned = nullptr;
+    explicit Workspace(cudaStream_t s) : st(s) {}
+    ~Workspace() {
+        if (owned) cudaFreeAsync(owned, st);
+    }
+    fk_status bind(Arena& ar, void* ws, size_t ws_bytes, size_t need) {
+        ar.sizing = false;
+        ar.used = 0;
+        if (ws) {
+            if (ws_bytes < need)
+                return set_error(FK_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, need);
+            if (((uintptr_t)ws & 255u) != 0)
+                return set_error(FK_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+            ar.base = (char*)ws;
+            ar.cap = ws_bytes;
+            return FK_OK;
+        }
+        if (need > 0) FK_CUDA(cudaMallocAsync(&owned, need, st));
+        ar.base = (char*)owned;
+        ar.cap = need;
+        return FK_OK;
+    }
+};
+
+static size_t dtype_size(fk_dtype t) { return t == FK_F64 ? 8 : 4; }
+
+static fk_status check_common(const void* x, fk_dtype xd, int64_t N, int d, fk_path path) {
+    if (xd != FK_F32 && xd != FK_F64) return set_error(FK_ERR_INVALID_ARG, "xdtype must be FK_F32 or FK_F64");
+    if (path != FK_PATH_MIXED && path != FK_PATH_FP64) return set_error(FK_ERR_INVALID_ARG, "unknown precision path");
+    if (N < 0) return set_error(FK_ERR_INVALID_ARG, "N must be >= 0");
+    if (N > 0 && !x) return set_error(FK_ERR_INVALID_ARG, "x is NULL");
+    if (d < 1) return set_error(FK_ERR_INVALID_ARG, "d must be >= 1");
+    return FK_OK;
+}
+
+}  // namespace fk
+
+using namespace fk;
+
+extern "C" {
+
+const char* fk_last_error(void) { return g_msg; }
+
+const char* fk_version(void) { return "fastecdf-gb300 0.1 (sm_103a)"; }
+
+fk_status fk_device_status(fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int* w = nullptr;
+    FK_TRY(device_error_word(&w));
+    FK_CUDA(cudaStreamSynchronize(st));
+    int v = 0;
+    FK_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    int zero = 0;
+    FK_CUDA(cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    switch (v) {
+        case 0: return FK_OK;
+        case DEV_TIMEOUT: return set_error(FK_ERR_TIMEOUT, "a bounded device wait ran out");
+        case 3: return set_error(FK_ERR_INVALID_ARG, "grid axis not strictly increasing (device check)");
+        default: return set_error(FK_ERR_CUDA, "device error code %d", v);
+    }
+}
+
+// ------------------------------------------------------------------ grid path
+static fk_status grid_validate(const void* x, fk_dtype xd, int64_t N, int d, const int64_t* M,
+                               fk_path path) {
+    FK_TRY(check_common(x, xd, N, d, path));
+    if (d > 8) return set_error(FK_ERR_UNSUPPORTED, "ecdf_grid supports d <= 8");
+    if (!M) return set_error(FK_ERR_INVALID_ARG, "M is NULL");
+    int64_t cells = 1;
+    for (int k = 0; k < d; ++k) {
+        if (M[k] < 1) return set_error(FK_ERR_INVALID_ARG, "M[%d] must be >= 1", k);
+        if (cells > ((int64_t)1 << 40) / (M[k] + 1)) return set_error(FK_ERR_UNSUPPORTED, "grid too large");
+        cells *= (M[k] + 1);
+    }
+    if (N >= ((int64_t)1 << 32)) return set_error(FK_ERR_UNSUPPORTED, "N must be < 2^32 on the grid path");
+    return FK_OK;
+}
+
+size_t fk_ecdf_grid_workspace(int64_t N, int d, const int64_t* M, int weighted, fk_path path) {
+    if (grid_validate((const void*)1, FK_F32, N, d, M, path) != FK_OK) return 0;
+    Arena ar;
+    int one = 0;
+    grid_run(nullptr, FK_F32, N, d, weighted ? (const void*)1 : nullptr, nullptr, M, nullptr,
+             nullptr, path, ar, 0, &one);
+    return ar.used;
+}
+
+fk_status fk_ecdf_grid(const void* x, fk_dtype xd, int64_t N, int d, const void* y,
+                       const double* z_axes, const int64_t* M, const uint32_t* orthant_mask,
+                       void* out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(grid_validate(x, xd, N, d, M, path));
+    if (!z_axes) return set_error(FK_ERR_INVALID_ARG, "z_axes is NULL");
+    if (!out) return set_error(FK_ERR_INVALID_ARG, "out is NULL");   // a grid has >= 1 point
+    int64_t ztot = 0, gpts = 1;
+    for (int k = 0; k < d; ++k) { ztot += M[k]; gpts *= M[k]; }
+    // host-side monotonicity check when the axes are host memory
+    if (!is_device_pointer(z_axes)) {
+        int64_t off = 0;
+        for (int k = 0; k < d; ++k) {
+            for (int64_t j = 0; j < M[k]; ++j) {
+                double v = z_axes[off + j];
+                if (!(v == v) || (j > 0 && !(z_axes[off + j - 1] < v)))
+                    return set_error(FK_ERR_INVALID_ARG, "grid axis %d not strictly increasing at %lld", k, (long long)j);
+            }
+            off += M[k];
+        }
+    }
+    int nsel = 0;
+    for (int o = 0; o < (1 << d); ++o)
+        if (!orthant_mask || ((orthant_mask[o >> 5] >> (o & 31)) & 1u)) ++nsel;
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xd_p = nullptr, *yd_p = nullptr, *zd_p = nullptr;
+    void* od_p = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xd_p));
+    FK_TRY(sg.in(y, (size_t)N * ds, &yd_p));
+    FK_TRY(sg.in(z_axes, (size_t)ztot * sizeof(double), &zd_p));
+    FK_TRY(sg.out(out, (size_t)nsel * gpts * 8, &od_p));
+    Arena plan;
+    int dummy = 0;
+    grid_run(nullptr, xd, N, d, y, nullptr, M, nullptr, nullptr, path, plan, st, &dummy);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    int* errw = nullptr;
+    FK_TRY(device_error_word(&errw));
+    FK_TRY(grid_run(xd_p, xd, N, d, yd_p, (const double*)zd_p, M, orthant_mask, od_p, path, ar, st, errw));
+    return sg.finish();
+}
+
+// ------------------------------------------------------------------ sample-point path
+static fk_status points_validate(const void* x, fk_dtype xd, int64_t N, int d, const void* z, int64_t M,
+                                 fk_path path, bool doubled) {
+    FK_TRY(check_common(x, xd, N, d, path));
+    if (d > 4) return set_error(FK_ERR_UNSUPPORTED, "the sample-point path supports d <= 4");
+    if (z && M < 0) return set_error(FK_ERR_INVALID_ARG, "M must be >= 0");
+    const int64_t items = z ? N + M : (doubled ? 2 * N : N);
+    if (items >= ((int64_t)1 << dc::kItemBits))
+        return set_error(FK_ERR_UNSUPPORTED, "too many items (%lld) for the sample-point path", (long long)items);
+    return FK_OK;
+}
+
+static fk_status check_h(const double* h, int d) {
+    if (!h) return set_error(FK_ERR_INVALID_ARG, "h is NULL");
+    for (int k = 0; k < d; ++k)
+        if (!(h[k] > 0.0) || !(h[k] < 1e300)) return set_error(FK_ERR_INVALID_ARG, "h[%d] must be finite and > 0", k);
+    return FK_OK;
+}
+
+size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
+    const void* z = sample_points ? nullptr : (const void*)1;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, true) != FK_OK) return 0;
+    size_t best = 0;
+    for (int t = 0; t < 2; ++t) {   // size for both dtypes (FP64 keys are wider)
+        Arena ar;
+        points_orthant(nullptr, t ? FK_F64 : FK_F32, N, d, weighted ? (const void*)1 : nullptr, z, M, nullptr,
+                       nullptr, path, ar, 0);
+        if (ar.used > best) best = ar.used;
+    }
+    return best;
+}
+
+static fk_status ecdf_points_impl(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,
+                                  int64_t M, const uint32_t* mask, void* out, fk_path path, void* ws,
+                                  size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(points_validate(x, xd, N, d, z, M, path, true));
+    const int64_t m_out = z ? M : N;
+    int nsel = 0;
+    for (int o = 0; o < (1 << d); ++o)
+        if (!mask || ((mask[o >> 5] >> (o & 31)) & 1u)) ++nsel;
+    if (nsel == 0 || m_out == 0) return FK_OK;          // nothing to write
+    if (!out) return set_error(FK_ERR_INVALID_ARG, "out is NULL");
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xp = nullptr, *yp = nullptr, *zp = nullptr;
+    void* op = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xp));
+    FK_TRY(sg.in(y, (size_t)N * ds, &yp));
+    FK_TRY(sg.in(z, z ? (size_t)M * d * ds : 0, &zp));
+    FK_TRY(sg.out(out, (size_t)nsel * m_out * 8, &op));
+    if (z && !zp) zp = z;
+    Arena plan;
+    points_orthant(nullptr, xd, N, d, y, z, M, mask, nullptr, path, plan, st);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    FK_TRY(points_orthant(xp, xd, N, d, yp, zp, M, mask, op, path, ar, st));
+    return sg.finish();
+}
+
+fk_status fk_ecdf_points(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
+                         const uint32_t* orthant_mask, void* out, fk_path path, void* ws, size_t ws_bytes,
+                         fk_stream_t stream) {
+    return ecdf_points_impl(x, xd, N, d, y, z, M, orthant_mask, out, path, ws, ws_bytes, stream);
+}
+
+fk_status fk_esf_points(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
+                        void* out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "d out of range");
+    uint32_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int o = (1 << d) - 1;
+    mask[o >> 5] = 1u << (o & 31);
+    return ecdf_points_impl(x, xd, N, d, y, z, M, mask, out, path, ws, ws_bytes, stream);
+}
+
+size_t fk_kde_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, int want_terms, fk_path path) {
+    const void* z = sample_points ? nullptr : (const void*)1;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, false) != FK_OK) return 0;
+    double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    size_t best = 0;
+    for (int t = 0; t < 2; ++t) {
+        Arena ar;
+        points_kernel(nullptr, t ? FK_F64 : FK_F32, N, d, (const void*)1, z, M, h, 0, 1, nullptr,
+                      want_terms ? (double*)1 : nullptr, path, ar, 0);
+        if (ar.used > best) best = ar.used;
+    }
+    return best;
+}
+
+size_t fk_kreg_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
+    const void* z = sample_points ? nullptr : (const void*)1;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, false) != FK_OK) return 0;
+    double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    size_t best = 0;
+    for (int t = 0; t < 2; ++t) {
+        Arena ar;
+        points_kernel(nullptr, t ? FK_F64 : FK_F32, N, d, (const void*)1, z, M, h, 0, 2, nullptr, nullptr, path,
+                      ar, 0);
+        if (ar.used > best) best = ar.used;
+    }
+    return best;
+}
+
+static fk_status kernel_impl(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                             const double* h, unsigned flags, int nw, double* out, double* terms, fk_path path,
+                             void* ws, size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(points_validate(x, xd, N, d, z, M, path, false));
+    FK_TRY(check_h(h, d));
+    if ((flags & FK_LOO) && z) return set_error(FK_ERR_INVALID_ARG, "FK_LOO needs z == NULL");
+    const int64_t m_out = z ? M : N;
+    if (m_out == 0) return FK_OK;                        // nothing to write
+    if (!out) return set_error(FK_ERR_INVALID_ARG, "out is NULL");
+    if (nw == 2 && !w && N > 0) return set_error(FK_ERR_INVALID_ARG, "y is NULL");
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xp = nullptr, *wp = nullptr, *zp = nullptr;
+    void *op = nullptr, *tp = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xp));
+    FK_TRY(sg.in(w, (size_t)N * ds, &wp));
+    FK_TRY(sg.in(z, z ? (size_t)M * d * ds : 0, &zp));
+    FK_TRY(sg.out(out, (size_t)m_out * 8, &op));
+    FK_TRY(sg.out(terms, terms ? ((size_t)1 << d) * m_out * 8 : 0, &tp));
+    Arena plan;
+    points_kernel(nullptr, xd, N, d, w, z, M, h, flags, nw, nullptr, terms, path, plan, st);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    FK_TRY(points_kernel(xp, xd, N, d, wp, zp, M, h, flags, nw, (double*)op, (double*)tp, path, ar, st));
+    return sg.finish();
+}
+
+fk_status fk_kde_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                         const double* h, unsigned flags, double* out, double* orthant_terms, fk_path path,
+                         void* ws, size_t ws_bytes, fk_stream_t stream) {
+    return kernel_impl(x, xd, N, d, w, z, M, h, flags, 1, out, orthant_terms, path, ws, ws_bytes, stream);
+}
+
+fk_status fk_kreg_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
+                          const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
+                          fk_stream_t stream) {
+    return kernel_impl(x, xd, N, d, y, z, M, h, flags, 2, out, nullptr, path, ws, ws_bytes, stream);
+}
+
+}  // extern "C"

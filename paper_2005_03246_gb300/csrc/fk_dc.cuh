@@ -1,0 +1,405 @@
+// fk_dc.cuh -- divide-and-conquer dominance sums at the sample points.
+//
+// Sec. 2.2 (Algorithms 2-5) and Appendix D (Algorithms 8-12) of the paper
+// compute, for every target, the sum of the source weights lying in each of
+// the 2^d orthants, by splitting on the last axis, recursing on both halves,
+// and merging the cross pairs one dimension lower, down to a one-dimensional
+// sweep (Merge1D).  This file re-expresses that recursion as nested bottom-up
+// merge sorts so that every step is a data-parallel pass:
+//
+//  * items are sources and targets (a point evaluated at the sample points is
+//    one source item plus one target item, so that the <= / > relation on tied
+//    coordinates is decided by ordering sources before targets);
+//  * P_k[item] is the item's position in the order of axis k (coordinate, then
+//    source-before-target): a source s precedes a target t in that order iff
+//    x_k(s) <= z_k(t), so every orthant relation becomes "precedes/follows";
+//  * the tree of axis k (k >= 2) is a bottom-up merge sort of the axis-k order
+//    by key P_{k-1}: after level l its runs are the level-l nodes (size
+//    2^{l+1}) already sorted for the next axis, which is exactly the split of
+//    Algorithm 3/4 with the children's sub-permutations phi_{l,m};
+//  * at the innermost tree axis (axis 1) the merge sort is by key P_0 and each
+//    merge of a left run C with a right run D is the Merge1D sweep: a target in
+//    D adds the weights of the C sources before it (delta_0 = +1) and after it
+//    (delta_0 = -1); a target in C does the same with the D sources.  Only
+//    pairs on opposite sides at every enclosing level are cross pairs; the side
+//    bits ("class") of the enclosing axes travel in the item's meta word and a
+//    target reads the channel of the complementary class.
+//
+// One kernel (k_merge) implements all merges; its sweep uses per-channel
+// forward and backward scans so that no suffix is ever formed by subtraction.
+#pragma once
+
+#include "fk_internal.cuh"
+
+namespace fk {
+namespace dc {
+
+constexpr int MT = 256;            // threads per CTA
+constexpr int MI = 8;              // outputs per thread
+constexpr int MTILE = MT * MI;     // outputs per CTA
+constexpr int kItemBits = 26;      // meta = item | cls << 26
+constexpr uint32_t kItemMask = (1u << kItemBits) - 1u;
+
+struct MergeArgs {
+    const uint32_t* key_in;
+    const uint32_t* meta_in;
+    uint32_t* key_out;
+    uint32_t* meta_out;
+    int64_t n;
+    int logR;     // input runs of length R = 2^logR, output runs 2R
+};
+
+// ------------------------------------------------------------ generic shuffles
+template <class T>
+__device__ __forceinline__ T shfl_up_t(const T& v, int o, int width) {
+    static_assert(sizeof(T) % 4 == 0, "shuffle of non-word type");
+    T r;
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(&v);
+    uint32_t* q = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) q[i] = __shfl_up_sync(0xffffffffu, p[i], o, width);
+    return r;
+}
+template <class T>
+__device__ __forceinline__ T shfl_down_t(const T& v, int o, int width) {
+    T r;
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(&v);
+    uint32_t* q = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) q[i] = __shfl_down_sync(0xffffffffu, p[i], o, width);
+    return r;
+}
+
+// Merge path: number of elements taken from A among the first q outputs of a
+// stable merge (A first on ties) of sorted A[0,la) and B[0,lb).
+template <class Acc>
+__device__ __forceinline__ int64_t merge_path(Acc A, int64_t la, Acc B, int64_t lb, int64_t q) {
+    int64_t lo = q > lb ? q - lb : 0;
+    int64_t hi = q < la ? q : la;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (A(mid) <= B(q - 1 - mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct GAcc {
+    const uint32_t* p;
+    __device__ uint32_t operator()(int64_t i) const { return p[i]; }
+};
+struct SAcc {
+    const uint32_t* p;
+    __device__ uint32_t operator()(int64_t i) const { return p[i]; }
+};
+
+// Phases of k_merge.
+enum { PH_PLAIN = 0, PH_TOTALS = 1, PH_SWEEP = 2 };
+
+// Scan of per-thread channel values over segments of `ts` consecutive threads
+// (ts a power of two, 1 < ts <= MT).  On return fe/be hold the exclusive
+// prefix (forward) and exclusive suffix (backward) within the segment.
+template <class Pol, int NCH>
+__device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Pol::V (&be)[NCH],
+                                         int ts, typename Pol::V* sh /* [2][NCH][MT/32] */) {
+    typedef typename Pol::V V;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = ts < 32 ? ts : 32;
+    const int lw = lane & (w - 1);
+    V fi[NCH], bi[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) { fi[c] = fe[c]; bi[c] = be[c]; }
+    // inclusive scans within sub-warps of width w
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        if (o >= w) break;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            V yf = shfl_up_t(fi[c], o, w);
+            V yb = shfl_down_t(bi[c], o, w);
+            if (lw >= o) fi[c] = Pol::add(yf, fi[c]);
+            if (lw + o < w) bi[c] = Pol::add(bi[c], yb);
+        }
+    }
+    // exclusive versions within the sub-warp
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        V ef = shfl_up_t(fi[c], 1, w);
+        V eb = shfl_down_t(bi[c], 1, w);
+        fe[c] = (lw == 0) ? Pol::zero() : ef;
+        be[c] = (lw == w - 1) ? Pol::zero() : eb;
+    }
+    if (ts <= 32) return;
+    // segments spanning several warps: add the totals of earlier / later warps
+    const int wps = ts >> 5;                 // warps per segment
+    if (lane == 31) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) sh[(0 * NCH + c) * (MT / 32) + warp] = fi[c];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) sh[(1 * NCH + c) * (MT / 32) + warp] = bi[c];
+    }
+    __syncthreads();
+    const int seg0 = warp & ~(wps - 1);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        V accf = Pol::zero(), accb = Pol::zero();
+        for (int q = seg0; q < warp; ++q) accf = Pol::add(accf, sh[(0 * NCH + c) * (MT / 32) + q]);
+        for (int q = warp + 1; q < seg0 + wps; ++q) accb = Pol::add(accb, sh[(1 * NCH + c) * (MT / 32) + q]);
+        fe[c] = Pol::add(accf, fe[c]);
+        be[c] = Pol::add(be[c], accb);
+    }
+    __syncthreads();
+}
+
+// The merge kernel.  PH_PLAIN: merge only.  PH_TOTALS: per-CTA channel totals
+// of the source weights (CTAs inside a merged block longer than a tile).
+// PH_SWEEP: merge plus the Merge1D sweep contributions to the targets.
+template <class Pol, int CLSB, int PHASE>
+__global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol::V* __restrict__ totals,
+                                              const typename Pol::V* __restrict__ carries) {
+    typedef typename Pol::V V;
+    constexpr int NCH = 2 << CLSB;
+    constexpr uint32_t CMASK = (1u << CLSB) - 1u;
+    __shared__ uint32_t s_key[MTILE];
+    __shared__ uint32_t s_meta[MTILE];
+    __shared__ int64_t s_co[4];
+    __shared__ V s_scan[(PHASE == PH_PLAIN) ? 1 : 2 * NCH * (MT / 32)];
+
+    const int64_t n = a.n;
+    const int64_t R = (int64_t)1 << a.logR;
+    const int64_t R2 = R << 1;
+    const int64_t o0 = (int64_t)blockIdx.x * MTILE;
+    if (o0 >= n) return;
+    const int64_t o1 = min(o0 + (int64_t)MTILE, n);
+    const int64_t ln = o1 - o0;                 // outputs of this CTA
+    const bool big = R2 > MTILE;
+    int64_t lc = 0;                              // big: local length of the C part
+    if (big) {
+        if (threadIdx.x == 0) {
+            const int64_t bs = (o0 / R2) * R2;
+            const int64_t cl = min(R, n - bs);
+            const int64_t dl = max((int64_t)0, min(R2, n - bs) - cl);
+            GAcc A{a.key_in + bs}, B{a.key_in + bs + cl};
+            const int64_t q0 = o0 - bs, q1 = o1 - bs;
+            const int64_t i0 = merge_path(A, cl, B, dl, q0);
+            const int64_t i1 = merge_path(A, cl, B, dl, q1);
+            s_co[0] = bs + i0;                 // C range [bs+i0, bs+i1)
+            s_co[1] = i1 - i0;
+            s_co[2] = bs + cl + (q0 - i0);     // D range start
+            s_co[3] = (q1 - i1) - (q0 - i0);
+        }
+        __syncthreads();
+        lc = s_co[1];
+        const int64_t cs = s_co[0], ds = s_co[2], ldd = s_co[3];
+        for (int64_t i = threadIdx.x; i < lc; i += MT) { s_key[i] = a.key_in[cs + i]; s_meta[i] = a.meta_in[cs + i]; }
+        for (int64_t i = threadIdx.x; i < ldd; i += MT) { s_key[lc + i] = a.key_in[ds + i]; s_meta[lc + i] = a.meta_in[ds + i]; }
+    } else {
+        for (int64_t i = threadIdx.x; i < ln; i += MT) { s_key[i] = a.key_in[o0 + i]; s_meta[i] = a.meta_in[o0 + i]; }
+    }
+    __syncthreads();
+
+    if (PHASE == PH_TOTALS) {
+        // channel totals of this CTA's inputs (order does not matter)
+        V tf[NCH], tb[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { tf[c] = Pol::zero(); tb[c] = Pol::zero(); }
+        for (int64_t i = threadIdx.x; i < ln; i += MT) {
+            const uint32_t m = s_meta[i];
+            const int half = (i >= lc) ? 1 : 0;
+            const uint32_t item = m & kItemMask;
+            if (pol.is_src(item)) {
+                V wf, wb;
+                pol.src_weights(item, half, wf, wb);
+                const int ch = (half << CLSB) | (int)(m >> kItemBits);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (c == ch) { tf[c] = Pol::add(tf[c], wf); tb[c] = Pol::add(tb[c], wb); }
+            }
+        }
+        // CTA reduction through the scan helper: inclusive total = excl + own
+        V fe[NCH], be[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { fe[c] = tf[c]; be[c] = tb[c]; }
+        seg_scan<Pol, NCH>(fe, be, MT, s_scan);
+        if (threadIdx.x == MT - 1) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) totals[((int64_t)blockIdx.x * 2 + 0) * NCH + c] = Pol::add(fe[c], tf[c]);
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) totals[((int64_t)blockIdx.x * 2 + 1) * NCH + c] = Pol::add(be[c], tb[c]);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- merge
+    uint32_t ek[MI], em[MI];
+    int eh[MI];
+    int cnt = 0;
+    {
+        const int64_t p0 = (int64_t)threadIdx.x * MI;
+        int64_t bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+        for (int e = 0; e < MI; ++e) {
+            const int64_t p = p0 + e;
+            if (p >= ln) break;
+            if (e == 0 || (!big && (p % R2) == 0)) {
+                if (big) { bsl = 0; cl = lc; dl = ln - lc; }
+                else { bsl = (p / R2) * R2; cl = min(R, ln - bsl); dl = min(R2, ln - bsl) - cl; }
+                SAcc A{s_key + bsl}, B{s_key + bsl + cl};
+                i = merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+            }
+            bool takeC = (i < cl) && (j >= dl || s_key[bsl + i] <= s_key[bsl + cl + j]);
+            if (takeC) { ek[e] = s_key[bsl + i]; em[e] = s_meta[bsl + i]; eh[e] = 0; ++i; }
+            else { ek[e] = s_key[bsl + cl + j]; em[e] = s_meta[bsl + cl + j]; eh[e] = 1; ++j; }
+            cnt = e + 1;
+        }
+    }
+    // write merged output (the class bits travel unchanged)
+    {
+        const int64_t p0 = o0 + (int64_t)threadIdx.x * MI;
+        if (cnt == MI) {
+            uint4* kk = reinterpret_cast<uint4*>(a.key_out + p0);
+            uint4* mm = reinterpret_cast<uint4*>(a.meta_out + p0);
+            kk[0] = make_uint4(ek[0], ek[1], ek[2], ek[3]);
+            kk[1] = make_uint4(ek[4], ek[5], ek[6], ek[7]);
+            mm[0] = make_uint4(em[0], em[1], em[2], em[3]);
+            mm[1] = make_uint4(em[4], em[5], em[6], em[7]);
+        } else {
+            for (int e = 0; e < cnt; ++e) { a.key_out[p0 + e] = ek[e]; a.meta_out[p0 + e] = em[e]; }
+        }
+    }
+    if (PHASE == PH_PLAIN) return;
+
+    // ---------------------------------------------------------------- sweep
+    // per-element source weights (zero for pure targets)
+    V wf[MI], wb[MI];
+#pragma unroll
+    for (int e = 0; e < MI; ++e) {
+        wf[e] = Pol::zero();
+        wb[e] = Pol::zero();
+        if (e < cnt) {
+            const uint32_t item = em[e] & kItemMask;
+            if (pol.is_src(item)) pol.src_weights(item, eh[e], wf[e], wb[e]);
+        }
+    }
+    const int ts = big ? MT : (int)(R2 / MI);   // threads per merged block (0/1: thread-local)
+    V fe[NCH], be[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) { fe[c] = Pol::zero(); be[c] = Pol::zero(); }
+    if (ts > 1) {
+        // thread totals -> exclusive segmented scans
+#pragma unroll
+        for (int e = 0; e < MI; ++e) {
+            if (e < cnt) {
+                const int ch = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (c == ch) { fe[c] = Pol::add(fe[c], wf[e]); be[c] = Pol::add(be[c], wb[e]); }
+            }
+        }
+        seg_scan<Pol, NCH>(fe, be, ts, s_scan);
+        if (big && carries) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                fe[c] = Pol::add(carries[((int64_t)blockIdx.x * 2 + 0) * NCH + c], fe[c]);
+                be[c] = Pol::add(be[c], carries[((int64_t)blockIdx.x * 2 + 1) * NCH + c]);
+            }
+        }
+    }
+    // forward walk: value before each element of the complementary channel
+    V fwd[MI];
+    {
+        V run[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) run[c] = fe[c];
+        const int64_t p0 = (int64_t)threadIdx.x * MI;
+#pragma unroll
+        for (int e = 0; e < MI; ++e) {
+            fwd[e] = Pol::zero();
+            if (e < cnt) {
+                if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
+                }
+                const int cls = (int)(em[e] >> kItemBits);
+                const int own = (eh[e] << CLSB) | cls;
+                const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (c == opp) fwd[e] = run[c];
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (c == own) run[c] = Pol::add(run[c], wf[e]);
+            }
+        }
+    }
+    // backward walk and target update
+    {
+        V run[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) run[c] = be[c];
+        const int64_t p0 = (int64_t)threadIdx.x * MI;
+#pragma unroll
+        for (int e = MI - 1; e >= 0; --e) {
+            if (e < cnt) {
+                if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
+                }
+                const int cls = (int)(em[e] >> kItemBits);
+                const int own = (eh[e] << CLSB) | cls;
+                const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+                V bwd = Pol::zero();
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (c == opp) bwd = run[c];
+                const uint32_t item = em[e] & kItemMask;
+                if (pol.is_tgt(item)) {
+                    // position bits: bit 0 = half on axis 1, bit j = class bit of axis j+1
+                    const uint32_t pb = (uint32_t)eh[e] | ((uint32_t)cls << 1);
+                    pol.target(item, pb, fwd[e], bwd);
+                }
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (c == own) run[c] = Pol::add(run[c], wb[e]);
+            }
+        }
+    }
+}
+
+// Carries for merged blocks that span several CTAs: exclusive prefix of the
+// forward totals and exclusive suffix of the backward totals over the CTAs of
+// each merged block.  One thread per (block, channel, direction).
+template <class Pol, int NCH>
+__global__ void k_carries(const typename Pol::V* __restrict__ totals, typename Pol::V* __restrict__ carries,
+                          int64_t n, int logR) {
+    typedef typename Pol::V V;
+    const int64_t R2 = (int64_t)2 << logR;
+    const int64_t ctas = (n + MTILE - 1) / MTILE;
+    const int64_t per = R2 / MTILE;            // CTAs per full merged block
+    const int64_t nblocks = (ctas + per - 1) / per;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nblocks * NCH * 2) return;
+    const int dir = (int)(t % 2);
+    const int c = (int)((t / 2) % NCH);
+    const int64_t b = t / (2 * NCH);
+    const int64_t c0 = b * per, c1 = min(c0 + per, ctas);
+    V run = Pol::zero();
+    if (dir == 0) {
+        for (int64_t q = c0; q < c1; ++q) {
+            carries[(q * 2 + 0) * NCH + c] = run;
+            run = Pol::add(run, totals[(q * 2 + 0) * NCH + c]);
+        }
+    } else {
+        for (int64_t q = c1 - 1; q >= c0; --q) {
+            carries[(q * 2 + 1) * NCH + c] = run;
+            run = Pol::add(run, totals[(q * 2 + 1) * NCH + c]);
+        }
+    }
+}
+
+}  // namespace dc
+}  // namespace fk

@@ -1,0 +1,393 @@
+// fk_dc_drv.cuh -- accumulation policies and the host recursion of the
+// divide-and-conquer engine (see fk_dc.cuh for the formulation).
+#pragma once
+
+#include "fk_dc.cuh"
+
+namespace fk {
+namespace dc {
+
+// Which items are sources and which are targets.
+//   sample points, orthant sums : items [0,N) sources, [N,2N) target copies
+//   sample points, kernel sums  : items [0,N) are both (the self pair is added
+//                                 separately, or dropped for leave-one-out)
+//   explicit targets            : items [0,N) sources, [N,N+M) targets
+struct ItemMap {
+    int64_t n_src, tgt_off, n_tgt;
+    __device__ __forceinline__ bool is_src(uint32_t it) const { return (int64_t)it < n_src; }
+    __device__ __forceinline__ bool is_tgt(uint32_t it) const {
+        return (int64_t)it >= tgt_off && (int64_t)it < tgt_off + n_tgt;
+    }
+};
+
+// Orthant index receiving the forward sum of a target with position bits pb
+// (bit 0: half on axis 1, bit j: side on axis j+1).  A target on the upper
+// side of an axis receives from sources below it (delta = +1, bit clear);
+// the backward sum (delta_0 = -1) goes to the same index | 1.
+__device__ __forceinline__ uint32_t fwd_orthant(uint32_t pb, uint32_t pbmask) {
+    return ((~pb) & pbmask) << 1;
+}
+
+// ------------------------------------------------------------------ orthant sums
+struct PolCount : ItemMap {
+    typedef uint32_t V;
+    uint32_t* acc;        // [2^d][n_tgt]
+    uint32_t pbmask;
+    __device__ static V zero() { return 0u; }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ void src_weights(uint32_t, int, V& f, V& b) const { f = 1u; b = 1u; }
+    __device__ void prep_item(uint32_t, uint32_t) const {}
+    __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const uint32_t o = fwd_orthant(pb, pbmask);
+        acc[(int64_t)o * n_tgt + t] += f;
+        acc[(int64_t)(o | 1u) * n_tgt + t] += b;
+    }
+};
+
+struct PolW64 : ItemMap {
+    typedef double V;
+    const double* w;      // [n_src]
+    double* acc;          // [2^d][n_tgt]
+    uint32_t pbmask;
+    __device__ static V zero() { return 0.0; }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ void src_weights(uint32_t item, int, V& f, V& b) const { f = b = w[item]; }
+    __device__ void prep_item(uint32_t, uint32_t) const {}
+    __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const uint32_t o = fwd_orthant(pb, pbmask);
+        acc[(int64_t)o * n_tgt + t] += f;
+        acc[(int64_t)(o | 1u) * n_tgt + t] += b;
+    }
+};
+
+struct PolWFF : ItemMap {
+    typedef FF V;
+    const FF* w;          // [n_src] weights split into hi + lo
+    FF* acc;              // [2^d][n_tgt]
+    uint32_t pbmask;
+    __device__ static V zero() { return ff_zero(); }
+    __device__ static V add(V a, V b) { return ff_add(a, b); }
+    __device__ void src_weights(uint32_t item, int, V& f, V& b) const { f = b = w[item]; }
+    __device__ void prep_item(uint32_t, uint32_t) const {}
+    __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const uint32_t o = fwd_orthant(pb, pbmask);
+        acc[(int64_t)o * n_tgt + t] = ff_add(acc[(int64_t)o * n_tgt + t], f);
+        acc[(int64_t)(o | 1u) * n_tgt + t] = ff_add(acc[(int64_t)(o | 1u) * n_tgt + t], b);
+    }
+};
+
+// ------------------------------------------------------------------ kernel sums
+// Exponent factors e^{+-v/h} are stored per item and axis as an FP64-computed
+// mantissa (rounded to FP32 on the mixed path) and a power-of-two shift, and
+// the product over the enclosing axes (chosen by the item's side bits, the
+// same factor in the source and the target role) as `base`.  A forward
+// contribution is then  (sum_s w_s B_s E1_s E0+_s) * B_t E1_t E0-_t  with
+// every factor pair bounded by 1, the shifted form of eq. (Laplacian
+// decomposition nD) with the shift taken at the split of each level.
+struct BaseF { float m; int s; };
+struct BaseD { double m; int s; int pad; };
+
+template <int NW>
+struct SFFn { SFF v[NW]; };
+template <int NW>
+struct SDn { SD v[NW]; };
+
+// Mixed path: FP32 compensated bulk sums, FP64 exponent arithmetic.
+template <int NW>
+struct PolKF : ItemMap {
+    typedef SFFn<NW> V;
+    const float* w;           // [n_src] weights (kreg: y), or nullptr for 1
+    const FacF* fac;          // [d][n_items]
+    int64_t n_items;
+    int nbase;                // number of enclosing axes (d - 2)
+    BaseF* base;              // [n_items]
+    FF* acc;                  // [NW][n_tgt]
+    FF* terms;                // optional [2^d][n_tgt]
+    uint32_t pbmask;
+    __device__ static V zero() {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sff_zero();
+        return r;
+    }
+    __device__ static V add(V a, V b) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sff_add(a.v[i], b.v[i]);
+        return r;
+    }
+    __device__ void prep_item(uint32_t item, uint32_t cls) const {
+        float m = 1.f;
+        int s = 0;
+        for (int j = 0; j < nbase; ++j) {
+            const FacF f = fac[(int64_t)(j + 2) * n_items + item];
+            const bool up = (cls >> j) & 1u;
+            m *= up ? f.mm : f.mp;
+            s += up ? -f.s : f.s;
+        }
+        base[item] = BaseF{m, s};
+    }
+    __device__ void src_weights(uint32_t item, int half, V& f, V& b) const {
+        const FacF e1 = fac[(int64_t)1 * n_items + item];
+        const FacF e0 = fac[item];
+        const BaseF B = base[item];
+        const float m1 = half ? e1.mm : e1.mp;
+        const int s1 = half ? -e1.s : e1.s;
+        const float mb = B.m * m1;
+        const float w0 = w ? w[item] : 1.f;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const float wi = (NW == 2 && i == 1) ? 1.f : w0;
+            f.v[i] = SFF{wi * mb * e0.mp, 0.f, B.s + s1 + e0.s};
+            b.v[i] = SFF{wi * mb * e0.mm, 0.f, B.s + s1 - e0.s};
+        }
+    }
+    __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const FacF e1 = fac[(int64_t)1 * n_items + item];
+        const FacF e0 = fac[item];
+        const BaseF B = base[item];
+        const int half = pb & 1u;
+        const float m1 = half ? e1.mm : e1.mp;
+        const int s1 = half ? -e1.s : e1.s;
+        const float tf = B.m * m1 * e0.mm;            // forward: E0^-(t)
+        const int sf = B.s + s1 - e0.s;
+        const float tb = B.m * m1 * e0.mp;            // backward: E0^+(t)
+        const int sb = B.s + s1 + e0.s;
+        const uint32_t o = fwd_orthant(pb, pbmask);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const float cf = (f.v[i].hi + f.v[i].lo) * tf * pow2f_any(f.v[i].e + sf);
+            const float cb = (b.v[i].hi + b.v[i].lo) * tb * pow2f_any(b.v[i].e + sb);
+            FF a = acc[(int64_t)i * n_tgt + t];
+            a = ff_add_f(ff_add_f(a, cf), cb);
+            acc[(int64_t)i * n_tgt + t] = a;
+            if (i == 0 && terms) {
+                terms[(int64_t)o * n_tgt + t] = ff_add_f(terms[(int64_t)o * n_tgt + t], cf);
+                terms[(int64_t)(o | 1u) * n_tgt + t] = ff_add_f(terms[(int64_t)(o | 1u) * n_tgt + t], cb);
+            }
+        }
+    }
+};
+
+// All-FP64 path.
+template <int NW>
+struct PolKD : ItemMap {
+    typedef SDn<NW> V;
+    const double* w;
+    const FacD* fac;
+    int64_t n_items;
+    int nbase;
+    BaseD* base;
+    double* acc;
+    double* terms;
+    uint32_t pbmask;
+    __device__ static V zero() {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sd_zero();
+        return r;
+    }
+    __device__ static V add(V a, V b) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sd_add(a.v[i], b.v[i]);
+        return r;
+    }
+    __device__ void prep_item(uint32_t item, uint32_t cls) const {
+        double m = 1.0;
+        int s = 0;
+        for (int j = 0; j < nbase; ++j) {
+            const FacD f = fac[(int64_t)(j + 2) * n_items + item];
+            const bool up = (cls >> j) & 1u;
+            m *= up ? f.mm : f.mp;
+            s += up ? -f.s : f.s;
+        }
+        base[item] = BaseD{m, s, 0};
+    }
+    __device__ void src_weights(uint32_t item, int half, V& f, V& b) const {
+        const FacD e1 = fac[(int64_t)1 * n_items + item];
+        const FacD e0 = fac[item];
+        const BaseD B = base[item];
+        const double m1 = half ? e1.mm : e1.mp;
+        const int s1 = half ? -e1.s : e1.s;
+        const double mb = B.m * m1;
+        const double w0 = w ? w[item] : 1.0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const double wi = (NW == 2 && i == 1) ? 1.0 : w0;
+            f.v[i] = SD{wi * mb * e0.mp, B.s + s1 + e0.s};
+            b.v[i] = SD{wi * mb * e0.mm, B.s + s1 - e0.s};
+        }
+    }
+    __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const FacD e1 = fac[(int64_t)1 * n_items + item];
+        const FacD e0 = fac[item];
+        const BaseD B = base[item];
+        const int half = pb & 1u;
+        const double m1 = half ? e1.mm : e1.mp;
+        const int s1 = half ? -e1.s : e1.s;
+        const double tf = B.m * m1 * e0.mm;
+        const int sf = B.s + s1 - e0.s;
+        const double tb = B.m * m1 * e0.mp;
+        const int sb = B.s + s1 + e0.s;
+        const uint32_t o = fwd_orthant(pb, pbmask);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const double cf = f.v[i].m * tf * pow2d_any(f.v[i].e + sf);
+            const double cb = b.v[i].m * tb * pow2d_any(b.v[i].e + sb);
+            acc[(int64_t)i * n_tgt + t] += cf + cb;
+            if (i == 0 && terms) {
+                terms[(int64_t)o * n_tgt + t] += cf;
+                terms[(int64_t)(o | 1u) * n_tgt + t] += cb;
+            }
+        }
+    }
+};
+
+// ------------------------------------------------------------------ gathers
+// Class bits of an item for the innermost sort: bit j = bit lvl[j] of idx[j][item].
+struct ClassSpec {
+    const uint32_t* idx[6];
+    int lvl[6];
+    int nb;
+};
+
+__device__ __forceinline__ uint32_t class_of(const ClassSpec& cs, uint32_t item) {
+    uint32_t c = 0;
+    for (int j = 0; j < cs.nb; ++j) c |= ((cs.idx[j][item] >> cs.lvl[j]) & 1u) << j;
+    return c;
+}
+
+// Inner (sweep) sort input: key = P_0[item], meta = item | class << 26.
+template <class Pol>
+__global__ void k_gather_inner(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0,
+                               ClassSpec cs, Pol pol, uint32_t* __restrict__ key, uint32_t* __restrict__ meta) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t item = seq[p];
+    const uint32_t c = class_of(cs, item);
+    key[p] = P0[item];
+    meta[p] = item | (c << kItemBits);
+    pol.prep_item(item, c);
+}
+
+// ------------------------------------------------------------------ driver
+struct DCBuffers {
+    uint32_t* k[2];   // inner sort ping-pong keys
+    uint32_t* m[2];   // inner sort ping-pong metas
+    void* totals;
+    void* carries;
+};
+
+// host-side common pieces (fk_dc_common.cu)
+fk_status plain_merge_level(const MergeArgs& a, cudaStream_t st);
+fk_status gather_outer(const uint32_t* seq, int64_t n, const uint32_t* Pkey, uint32_t* key,
+                       uint32_t* meta, cudaStream_t st);
+fk_status record_index(const uint32_t* seq, int64_t n, int E, uint32_t* idx, cudaStream_t st);
+inline int ceil_log2(int64_t n) {
+    int e = 0;
+    while (((int64_t)1 << e) < n) ++e;
+    return e;
+}
+
+template <class Pol, int CLSB>
+fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
+                     const Pol& pol, DCBuffers& b, cudaStream_t st) {
+    typedef typename Pol::V V;
+    constexpr int NCH = 2 << CLSB;
+    k_gather_inner<Pol><<<grid_for(n, 256), 256, 0, st>>>(seq, n, P0, cs, pol, b.k[0], b.m[0]);
+    FK_LAUNCH_CHECK();
+    int cur = 0;
+    const unsigned ctas = grid_for(n, MTILE);
+    for (int m = 0; m < E; ++m) {
+        MergeArgs a{b.k[cur], b.m[cur], b.k[cur ^ 1], b.m[cur ^ 1], n, m};
+        const int64_t R2 = (int64_t)2 << m;
+        if (R2 > MTILE) {
+            k_merge<Pol, CLSB, PH_TOTALS><<<ctas, MT, 0, st>>>(a, pol, (V*)b.totals, nullptr);
+            FK_LAUNCH_CHECK();
+            const int64_t per = R2 / MTILE;
+            const int64_t nblk = ((int64_t)ctas + per - 1) / per;
+            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2, 128), 128, 0, st>>>((const V*)b.totals,
+                                                                              (V*)b.carries, n, m);
+            FK_LAUNCH_CHECK();
+            k_merge<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, pol, nullptr, (const V*)b.carries);
+        } else {
+            k_merge<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, pol, nullptr, nullptr);
+        }
+        FK_LAUNCH_CHECK();
+        cur ^= 1;
+    }
+    return FK_OK;
+}
+
+// Recursion over the tree axes.  `seq` holds the items sorted by P_k inside
+// nodes of size 2^E.  For k == 1 the innermost sweep sort runs directly; for
+// k >= 2 the axis-k tree is a merge sort of seq by P_{k-1} whose level l
+// states (nodes of 2^{l+1} sorted by P_{k-1}) each start the recursion one
+// axis lower with the side bit l of the axis-k index added to the class.
+struct OuterBuffers {
+    uint32_t* k[2];
+    uint32_t* m[2];
+    uint32_t* idx;    // index of every item inside its axis-k node
+};
+
+template <class Pol, int CLSB>
+fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* const* P,
+                  ClassSpec cs, const Pol& pol, OuterBuffers* ob, DCBuffers& ib, cudaStream_t st) {
+    if (k == 1) return inner_sort<Pol, CLSB>(seq, n, E, P[0], cs, pol, ib, st);
+    OuterBuffers& o = ob[k];
+    const uint32_t* idx = P[k];
+    if (o.idx) {
+        FK_TRY(record_index(seq, n, E, o.idx, st));
+        idx = o.idx;
+    }
+    FK_TRY(gather_outer(seq, n, P[k - 1], o.k[0], o.m[0], st));
+    int cur = 0;
+    for (int l = 0; l < E; ++l) {
+        MergeArgs a{o.k[cur], o.m[cur], o.k[cur ^ 1], o.m[cur ^ 1], n, l};
+        FK_TRY(plain_merge_level(a, st));
+        cur ^= 1;
+        ClassSpec c2 = cs;
+        // the enclosing axes keep their bits; axis k contributes bit (k - 2)
+        c2.idx[k - 2] = idx;
+        c2.lvl[k - 2] = l;
+        if (c2.nb < k - 1) c2.nb = k - 1;
+        FK_TRY((recurse<Pol, CLSB>(k - 1, o.m[cur], n, l + 1, P, c2, pol, ob, ib, st)));
+    }
+    return FK_OK;
+}
+
+// Plans (sizing) and runs the whole sweep for a given policy.  P[0..d_eff-1]
+// are the per-axis positions, seq_top the items sorted by P[d_eff-1].
+template <class Pol, int CLSB>
+fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,
+                   const Pol& pol, Arena& ar, cudaStream_t st) {
+    typedef typename Pol::V V;
+    constexpr int NCH = 2 << CLSB;
+    OuterBuffers ob[8] = {};
+    for (int k = 2; k < d_eff; ++k) {
+        for (int q = 0; q < 2; ++q) { ob[k].k[q] = ar.take<uint32_t>(n); ob[k].m[q] = ar.take<uint32_t>(n); }
+        ob[k].idx = (k < d_eff - 1) ? ar.take<uint32_t>(n) : nullptr;
+    }
+    DCBuffers ib;
+    for (int q = 0; q < 2; ++q) { ib.k[q] = ar.take<uint32_t>(n); ib.m[q] = ar.take<uint32_t>(n); }
+    const int64_t ctas = (n + MTILE - 1) / MTILE;
+    ib.totals = ar.take<V>((size_t)ctas * 2 * NCH);
+    ib.carries = ar.take<V>((size_t)ctas * 2 * NCH);
+    if (ar.sizing) return FK_OK;
+    if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (dominance sweep)");
+    if (n <= 1) return FK_OK;
+    ClassSpec cs = {};
+    const int E = ceil_log2(n);
+    // for k == d_eff-1 the axis index is P[d_eff-1] itself (idx == nullptr above)
+    if (d_eff - 1 >= 2) ob[d_eff - 1].idx = nullptr;
+    return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, st);
+}
+
+}  // namespace dc
+}  // namespace fk

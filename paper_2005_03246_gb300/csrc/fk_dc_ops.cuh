@@ -1,0 +1,47 @@
+// fk_dc_ops.cuh -- declarations shared by the divide-and-conquer translation
+// units (engine instantiations and the operation orchestration).
+#pragma once
+
+#include "fk_dc_drv.cuh"
+
+namespace fk {
+namespace dc {
+
+struct HVec { double v[8]; };
+struct SelMap { int n; int o[256]; };   // output row r <- internal orthant o[r]
+
+// Instantiated sweeps (one per accumulation policy); CLSB is d_eff - 2.
+#define FK_DC_SWEEP_DECL(NAME, POL)                                                              \
+    fk_status NAME(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,    \
+                   const POL& pol, Arena& ar, cudaStream_t st);
+FK_DC_SWEEP_DECL(sweep_count, PolCount)
+FK_DC_SWEEP_DECL(sweep_w64, PolW64)
+FK_DC_SWEEP_DECL(sweep_wff, PolWFF)
+FK_DC_SWEEP_DECL(sweep_kf1, PolKF<1>)
+FK_DC_SWEEP_DECL(sweep_kf2, PolKF<2>)
+FK_DC_SWEEP_DECL(sweep_kd1, PolKD<1>)
+FK_DC_SWEEP_DECL(sweep_kd2, PolKD<2>)
+#undef FK_DC_SWEEP_DECL
+
+#define FK_DC_SWEEP_DEF(NAME, POL)                                                               \
+    fk_status NAME(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,    \
+                   const POL& pol, Arena& ar, cudaStream_t st) {                               \
+        switch (d_eff) {                                                                        \
+            case 2: return dc_sweep<POL, 0>(d_eff, n, P, seq_top, pol, ar, st);                 \
+            case 3: return dc_sweep<POL, 1>(d_eff, n, P, seq_top, pol, ar, st);                 \
+            case 4: return dc_sweep<POL, 2>(d_eff, n, P, seq_top, pol, ar, st);                 \
+            default: return set_error(FK_ERR_UNSUPPORTED, "sample-point path supports d <= 4"); \
+        }                                                                                       \
+    }
+
+}  // namespace dc
+
+// Operations (fk_dc_common.cu).  All pointers are device pointers.
+fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,
+                         int64_t M, const uint32_t* mask, void* out, fk_path path, Arena& ar,
+                         cudaStream_t st);
+fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
+                        int64_t M, const double* h, unsigned flags, int nw, double* out, double* terms,
+                        fk_path path, Arena& ar, cudaStream_t st);
+
+}  // namespace fk

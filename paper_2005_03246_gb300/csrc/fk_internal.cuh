@@ -1,0 +1,173 @@
+// fk_internal.cuh -- shared internals of the fastecdf library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/fastecdf.h"
+
+namespace fk {
+
+// ------------------------------------------------------------------ errors
+fk_status set_error(fk_status st, const char* fmt, ...);
+fk_status cuda_error(cudaError_t e, const char* where);
+
+#define FK_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t fk_e_ = (call);                                     \
+        if (fk_e_ != cudaSuccess) return ::fk::cuda_error(fk_e_, #call); \
+    } while (0)
+
+#define FK_TRY(call)                        \
+    do {                                    \
+        fk_status fk_s_ = (call);           \
+        if (fk_s_ != FK_OK) return fk_s_;   \
+    } while (0)
+
+#define FK_LAUNCH_CHECK() FK_CUDA(cudaGetLastError())
+
+// Device-side error codes recorded in the per-device error word.
+enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
+
+// ------------------------------------------------------------------ workspace arena
+// A bump allocator over caller scratch.  In sizing mode (base == nullptr) it
+// only accumulates the total so that the same plan code gives the size.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    bool sizing = true;
+    template <class T>
+    T* take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        size_t bytes = count * sizeof(T);
+        used = off + ((bytes + 255) & ~size_t(255));
+        if (sizing) return nullptr;
+        if (used > cap) return nullptr;
+        return reinterpret_cast<T*>(base + off);
+    }
+    bool overflow() const { return !sizing && used > cap; }
+};
+
+// ------------------------------------------------------------------ launch helpers
+constexpr int kSMs = 152;
+inline unsigned grid_for(int64_t n, int per_block) {
+    int64_t g = (n + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+// ------------------------------------------------------------------ value types
+// FF: unevaluated sum hi + lo of two floats (compensated FP32).
+struct FF { float hi, lo; };
+
+__device__ __forceinline__ FF ff_zero() { return FF{0.f, 0.f}; }
+
+// Knuth two-sum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    float hi = s + e;
+    return FF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    e += a.lo;
+    float hi = s + e;
+    return FF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ FF ff_from_double(double v) {
+    float hi = (float)v;
+    return FF{hi, (float)(v - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Exact powers of two for k <= 0 (flush below the normal range).
+__device__ __forceinline__ float pow2f_le0(int k) {
+    return (k >= -126) ? __int_as_float((k + 127) << 23) : 0.0f;
+}
+__device__ __forceinline__ double pow2d_le0(int k) {
+    return (k >= -1022) ? __longlong_as_double((long long)(k + 1023) << 52) : 0.0;
+}
+__device__ __forceinline__ float pow2f_any(int k) {
+    if (k > 127) return __int_as_float(0x7f800000);
+    return (k >= -126) ? __int_as_float((k + 127) << 23) : 0.0f;
+}
+__device__ __forceinline__ double pow2d_any(int k) {
+    if (k > 1023) return __longlong_as_double(0x7ff0000000000000LL);
+    return (k >= -1022) ? __longlong_as_double((long long)(k + 1023) << 52) : 0.0;
+}
+
+// Shifted compensated value (hi + lo) * 2^e; the zero value has e = kEmin.
+constexpr int kEmin = -(1 << 28);
+struct SFF { float hi, lo; int e; };
+__device__ __forceinline__ SFF sff_zero() { return SFF{0.f, 0.f, kEmin}; }
+__device__ __forceinline__ SFF sff_add(SFF a, SFF b) {
+    int e = max(a.e, b.e);
+    float sa = pow2f_le0(a.e - e), sb = pow2f_le0(b.e - e);
+    FF r = ff_add(FF{a.hi * sa, a.lo * sa}, FF{b.hi * sb, b.lo * sb});
+    return SFF{r.hi, r.lo, e};
+}
+// Shifted FP64 value m * 2^e.
+struct SD { double m; int e; };
+__device__ __forceinline__ SD sd_zero() { return SD{0.0, kEmin}; }
+__device__ __forceinline__ SD sd_add(SD a, SD b) {
+    int e = max(a.e, b.e);
+    return SD{a.m * pow2d_le0(a.e - e) + b.m * pow2d_le0(b.e - e), e};
+}
+
+// Full-warp shuffles for every accumulator type.
+__device__ __forceinline__ uint32_t shfl_up_any(uint32_t v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ uint32_t shfl_down_any(uint32_t v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ uint32_t shfl_idx_any(uint32_t v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ double shfl_up_any(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_down_any(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_idx_any(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ FF shfl_up_any(FF v, int o) {
+    return FF{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ FF shfl_down_any(FF v, int o) {
+    return FF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ FF shfl_idx_any(FF v, int l) {
+    return FF{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
+}
+
+// Per-item, per-axis exponent factor e^{+-v/h} = m_plus * 2^s, m_minus * 2^-s.
+struct FacF { float mp, mm; int s; };
+struct FacD { double mp, mm; int s; int pad; };
+
+// ------------------------------------------------------------------ host helpers
+bool is_device_pointer(const void* p);
+fk_status device_error_word(int** ptr);   // address of the current device's error word
+
+// scan.cu
+// Exclusive scan of n uint32 values (in may equal out).  `tmp` needs
+// scan_u32_tmp_words(n) words.
+size_t scan_u32_tmp_words(int64_t n);
+fk_status scan_u32_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
+                             cudaStream_t st);
+
+// sort.cu -- stable LSD radix sort of (key, value) pairs.
+size_t radix_sort_tmp_bytes(int64_t n, int key_bits);
+fk_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                               uint32_t* vals_alt, int64_t n, int key_bits, void* tmp,
+                               size_t tmp_bytes, cudaStream_t st, bool* result_in_alt);
+fk_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                               uint32_t* vals_alt, int64_t n, int key_bits, void* tmp,
+                               size_t tmp_bytes, cudaStream_t st, bool* result_in_alt);
+
+// grid.cu
+fk_status grid_run(const void* x, fk_dtype xd, int64_t N, int d, const void* y,
+                   const double* z_dev, const int64_t* M, const uint32_t* mask, void* out,
+                   fk_path path, Arena& ar, cudaStream_t st, int* err_word);
+
+}  // namespace fk

@@ -1,0 +1,219 @@
+"""GPU parity of the sample-point path (Sec. 2.2 and Appendix D: rank transform
++ divide-and-conquer) and of the Laplacian kernel sums (Sec. 3.1) against the
+CPU oracle, through the C ABI.
+
+Counts must be bit-exact.  Weighted sums of signed terms are compared against
+the orthant sums of |y| (the condition of a sum); kernel values use the
+relative error on entries >= 1e-6 max, within 1e-5 (mixed path) and 1e-12
+(FP64 path).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_03246_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL = {"mixed": 1e-5, "fp64": 1e-12}
+
+
+def _fk():
+    import paper_2005_03246_gb300 as fk
+    return fk
+
+
+def _t(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda:0")
+
+
+def _rel_kde(got, ref):
+    big = np.abs(ref) >= 1e-6 * np.abs(ref).max()
+    return np.max(np.abs(got[big] - ref[big]) / np.abs(ref[big]))
+
+
+def _rel_signed(got, ref, absref):
+    return np.max(np.abs(got - ref) / np.maximum(absref, 1e-300))
+
+
+def _points(n, d, seed, ties=True, dtype=np.float32):
+    r = np.random.default_rng(seed)
+    x = r.standard_normal((n, d))
+    if ties:
+        m = r.random((n, d)) < 0.3
+        x[m] = np.round(x[m] * 8) / 8
+    return x.astype(dtype)
+
+
+# ------------------------------------------------------------------ orthant sums
+
+
+def test_tie_example_golden():
+    """The hand-worked 5-point example with ties (eq. ECDFdelta)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "tie2d_orthants.txt"))
+            if l.strip() and not l.startswith("#")]
+    pts = np.array([[float(v) for v in r] for r in rows[1:6]])
+    expect = np.array([[int(v) for v in rows[7 + 2 * o]] for o in range(4)])
+    got = _fk().ecdf_points(_t(pts)).cpu().numpy()
+    assert np.array_equal(got, expect)
+
+
+def test_small_config_counts_and_weights():
+    """d=2, N=1e4, FP64, 10% rounded coordinates: all orthants at the sample points."""
+    data = datagen.ecdf_small()
+    x, y = data["x"], data["y"]
+    ref = oracle.orthant_sums(x)
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(got, ref)
+    refw = oracle.orthant_sums(x, y=y)
+    absw = oracle.orthant_sums(x, y=np.abs(y))
+    for path in ("fp64", "mixed"):
+        gw = _fk().ecdf_points(_t(x), y=_t(y), path=path).cpu().numpy()
+        assert _rel_signed(gw, refw, absw) <= TOL[path], path
+
+
+def test_small_config_explicit_grid_targets_match_grid_path():
+    """The same counts at the 128x128 grid points as explicit targets equal the
+    grid path and the oracle."""
+    data = datagen.ecdf_small()
+    x = data["x"]
+    z = oracle.grid_points(data["grid"])
+    got = _fk().ecdf_points(_t(x), z=_t(z)).cpu().numpy()
+    ref = oracle.orthant_sums(x, z=z)
+    assert np.array_equal(got, ref)
+    grid = _fk().ecdf_grid(_t(x), data["grid"]).cpu().numpy().reshape(4, -1)
+    assert np.array_equal(got, grid)
+
+
+@pytest.mark.parametrize("d,n", [(1, 3000), (2, 2500), (3, 3100), (4, 1500), (3, 70000)])
+def test_orthant_counts_dims(d, n):
+    """All orthants, ties on every axis, sizes spanning several CTA tiles and a
+    ragged tail; n=70000 exercises merged blocks larger than one tile."""
+    x = _points(n, d, seed=100 + d)
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    if n <= 5000:
+        ref = oracle.orthant_sums(x)
+        assert np.array_equal(got, ref)
+    else:
+        idx = datagen.sample_targets(n, 512, seed=7, include=(0, n - 1))
+        ref = oracle.orthant_sums(x, z=x[idx])
+        assert np.array_equal(got[:, idx], ref)
+    assert np.all(got.sum(axis=0) == n)          # the orthants partition the sources
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_esf_and_mask(d):
+    x = _points(1200, d, seed=300 + d)
+    y = np.random.default_rng(1).random(1200).astype(np.float32)
+    full = (1 << d) - 1
+    got = _fk().esf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(got, oracle.orthant_sums(x, mask=[full])[0])
+    sel = [full, 0] if d > 0 else [0]
+    g2 = _fk().ecdf_points(_t(x), y=_t(y), orthants=sel, path="fp64").cpu().numpy()
+    r2 = oracle.orthant_sums(x, y=y, mask=sorted(sel))
+    assert np.max(np.abs(g2 - r2) / np.maximum(r2, 1e-300)) <= 1e-12
+
+
+def test_explicit_targets_with_ties_between_sources_and_targets():
+    r = np.random.default_rng(9)
+    x = np.round(r.random((4000, 3)) * 20) / 20
+    z = np.round(r.random((900, 3)) * 20) / 20
+    got = _fk().ecdf_points(_t(x), z=_t(z)).cpu().numpy()
+    assert np.array_equal(got, oracle.orthant_sums(x, z=z))
+
+
+def test_empty_and_single_point():
+    fk = _fk()
+    x0 = np.zeros((0, 2), dtype=np.float32)
+    assert fk.ecdf_points(_t(x0)).shape == (4, 0)
+    x1 = np.array([[0.5, -1.0]], dtype=np.float32)
+    got = fk.ecdf_points(_t(x1)).cpu().numpy()
+    assert got.tolist() == [[1], [0], [0], [0]]
+    z = np.array([[0.0, 0.0], [1.0, -2.0]], dtype=np.float32)
+    got = fk.ecdf_points(_t(x1), z=_t(z)).cpu().numpy()
+    assert np.array_equal(got, oracle.orthant_sums(x1, z=z))
+
+
+def test_full_size_d3_sampled_targets():
+    """d=3, N=1e6 correlated Gaussian (FP32): 2048 sampled targets against the
+    oracle, plus the exact partition invariant on every target."""
+    data = datagen.ecdf_gauss3()
+    x = data["x"]
+    n = x.shape[0]
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    assert np.all(got.sum(axis=0) == n)
+    idx = datagen.sample_targets(n, 2048, seed=5, include=(0, n - 1, int(np.argmax(x[:, 0]))))
+    ref = oracle.orthant_sums(x, z=x[idx])
+    assert np.array_equal(got[:, idx], ref)
+
+
+def test_full_size_d2_fenwick_every_target():
+    """d=2, N=1e6 (copula, FP32): every output checked by the Fenwick sweep."""
+    x = datagen.copula_t4()["x"]
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(got, oracle.fenwick2d(x))
+
+
+# ------------------------------------------------------------------ kernel sums
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+@pytest.mark.parametrize("d,n", [(1, 2000), (2, 3000), (3, 2500), (4, 1200)])
+def test_kde_sample_points(path, d, n):
+    x = _points(n, d, seed=500 + d)
+    h = np.linspace(0.15, 0.4, d)
+    w = np.random.default_rng(d).random(n).astype(np.float32)
+    got = _fk().kde_laplace(_t(x), h, w=_t(w), path=path).cpu().numpy()
+    ref = oracle.kde_laplace(x, h, w=w)
+    assert _rel_kde(got, ref) <= TOL[path]
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+def test_kde_explicit_targets_terms_and_loo(path):
+    x = _points(3000, 3, seed=11)
+    z = _points(700, 3, seed=12)
+    h = [0.2, 0.3, 0.25]
+    got, terms = _fk().kde_laplace(_t(x), h, z=_t(z), terms=True, path=path)
+    ref, rterms = oracle.kde_laplace(x, h, z=z, terms=True)
+    assert _rel_kde(got.cpu().numpy(), ref) <= TOL[path]
+    tt = terms.cpu().numpy()
+    assert np.max(np.abs(tt - rterms)) <= TOL[path] * ref.max() * 8
+    gl = _fk().kde_laplace(_t(x), h, loo=True, path=path).cpu().numpy()
+    assert _rel_kde(gl, oracle.kde_laplace(x, h, loo=True)) <= TOL[path]
+
+
+@pytest.mark.parametrize("h", [0.05, 0.1, 0.3])
+def test_kde_copula_heavy_tails_no_overflow(h):
+    """Student-t tails with small h: e^{|x|/h} overflows FP64 without the shifts."""
+    x = datagen.copula_t4(n=20000)["x"]
+    for path in ("mixed", "fp64"):
+        got = _fk().kde_laplace(_t(x), h, path=path).cpu().numpy()
+        idx = datagen.sample_targets(x.shape[0], 800, seed=3, include=(int(np.argmax(x[:, 0])),))
+        ref = oracle.kde_laplace(x, h, z=x[idx])
+        assert np.all(np.isfinite(got))
+        assert _rel_kde(got[idx], ref) <= TOL[path], path
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+def test_kreg(path):
+    d = datagen.copula_t4(n=6000)
+    x, y = d["x"], d["y"]
+    h = 0.1
+    got = _fk().kreg_laplace(_t(x), _t(y), h, path=path).cpu().numpy()
+    ref = oracle.kreg_laplace(x, y, h)
+    # NW is a ratio of two kernel sums; scale the error by the magnitude of y
+    assert np.max(np.abs(got - ref)) <= TOL[path] * 10 * np.abs(y).max()
+
+
+def test_kde_full_size_d3_sampled():
+    """d=3, N=1e6, h=0.1 (the paper's bandwidth): 1024 sampled targets."""
+    x = datagen.ecdf_gauss3()["x"]
+    n = x.shape[0]
+    idx = datagen.sample_targets(n, 1024, seed=8, include=(0, n - 1))
+    ref = oracle.kde_laplace(x, 0.1, z=x[idx])
+    for path in ("mixed", "fp64"):
+        got = _fk().kde_laplace(_t(x), 0.1, path=path).cpu().numpy()
+        assert _rel_kde(got[idx], ref) <= TOL[path], path
