@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the fast multivariate ECDF / Laplacian KDE hot path on GB300.
+
+One step is one pass of the whole hot path over the d=3, N=1e6 workload
+(correlated Gaussian, S_ij = 0.5, FP32 inputs):
+
+  * ecdf_grid   -- binning + histogram + orthant scans on a 256^3 grid, all
+                   8 orthants, exact int64 counts (Sec. 2.1);
+  * ecdf_points -- rank transform + divide-and-conquer, all 8 orthants at the
+                   N sample points, exact counts (Sec. 2.2, Appendix D);
+  * kde_laplace -- Laplacian KDE at the N sample points, h = 0.1, mixed
+                   precision (Sec. 3.1).
+
+value = N sample points / step time (each point gets its 8 orthant counts and
+its density; the 256^3 grid is evaluated alongside).  Inputs are resident in
+HBM; L2 (129 MB) is flushed by writing a 256 MB buffer between timed steps.
+`e2e` times the same step through the C ABI with pinned HOST buffers (copies
+in and out inside the timed region).  `--impl reference` times the CPU oracle
+on a bounded sample of the same workload.
+
+With --gpus N (torchrun) every rank runs an independent replica (the
+single-dataset sample-point problem couples every pair of points and does not
+shard); value aggregates all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ECDF/Laplace-KDE points/sec at N=1e6 vs FP64 GPU path; % HBM roofline"
+UNIT = "points/s"
+N_POINTS = 1_000_000
+D = 3
+M_AXIS = 256
+H = 0.1
+WORKLOAD = "ecdf_gauss3_d3_n1e6_grid256_kde_h0.1"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
+                    help="run one operation per step (profiling of a single kernel family)")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(n):
+    from paper_2005_03246_gb300 import datagen
+    data = datagen.ecdf_gauss3(n=n)
+    return data["x"], data["grid"]
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+
+def _oracle_sample(x, grid, s, seed=0):
+    """The oracle on s sample points: their 8 orthant counts and density, plus
+    s * (grid points / N) grid points' 8 orthant counts.  Returns seconds."""
+    import oracle
+    from paper_2005_03246_gb300 import datagen
+    n = x.shape[0]
+    idx = datagen.sample_targets(n, s, seed=seed)
+    r = np.random.default_rng(seed)
+    gcount = max(1, int(round(s * (M_AXIS ** D) / n)))
+    gz = np.stack([grid[k][r.integers(0, M_AXIS, size=gcount)] for k in range(D)], axis=1)
+    t0 = time.perf_counter()
+    oracle.orthant_sums(x, z=x[idx])
+    oracle.kde_laplace(x, H, z=x[idx])
+    oracle.orthant_sums(x, z=gz)
+    return time.perf_counter() - t0
+
+
+def _cpu_baseline(x, grid, target_s=15.0):
+    import oracle
+    oracle.build()
+    s = 16
+    t = _oracle_sample(x, grid, s)
+    s = int(max(16, min(4096, s * target_s / max(t, 1e-3) * 0.8)))
+    t = _oracle_sample(x, grid, s, seed=1)
+    return {"value": s / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d of the %d sample points (8 orthant counts + density each, h=%g) and %d "
+                      "random grid points (8 orthant counts each), all against the full N sources; "
+                      "%.1f s" % (s, x.shape[0], H, max(1, int(round(s * M_AXIS ** D / x.shape[0]))), t)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    x, grid = _workload(args.n)
+    # each step: a bounded sample sized for ~3 s of oracle work
+    s = 16
+    t = _oracle_sample(x, grid, s)
+    s = int(max(16, min(4096, s * 3.0 / max(t, 1e-3))))
+    for w in range(args.warmup):
+        _oracle_sample(x, grid, s, seed=100 + w)
+    times = [_oracle_sample(x, grid, s, seed=200 + k) for k in range(args.steps)]
+    tm = sum(times) / len(times)
+    value = s / tm
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tm * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": args.n, "d": D, "grid": [M_AXIS] * D, "h": H,
+                       "sample_points_per_step": s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "%d sample points + %d grid points per step against all N sources"
+                                       % (s, max(1, int(round(s * M_AXIS ** D / args.n))))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2005_03246_gb300 as fk
+    from paper_2005_03246_gb300 import _lib
+    lib = _lib.load()
+
+    x_np, grid = _workload(args.n)
+    n = x_np.shape[0]
+    x = torch.as_tensor(x_np, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ywt = torch.as_tensor(np.sin(x_np.astype(np.float64).sum(axis=1)).astype(np.float32), device=dev)
+    only = {"grid": lambda: fk.ecdf_grid(x, grid), "points": lambda: fk.ecdf_points(x),
+            "kde": lambda: fk.kde_laplace(x, H, path="mixed"),
+            "kde64": lambda: fk.kde_laplace(x, H, path="fp64"),
+            "kreg": lambda: fk.kreg_laplace(x, ywt, H, path="mixed")}
+
+    def step():
+        if args.only:
+            return only[args.only]()
+        g = fk.ecdf_grid(x, grid)
+        p = fk.ecdf_points(x)
+        f = fk.kde_laplace(x, H, path="mixed")
+        return g, p, f
+
+    for _ in range(max(3, args.warmup)):
+        out = step()
+    del out
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    lib.fk_profile_reset()
+    lib.fk_profile_enable(1)
+    l0 = lib.fk_kernel_launches()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        del out
+    torch.cuda.synchronize()
+    launches = lib.fk_kernel_launches() - l0
+    lib.fk_profile_enable(0)
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    ms_step = float(t_max.item()) / args.steps
+    value = ws * n / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel family
+    fams = {}
+    for name, fid in _lib.PROFILE_FAMILIES.items():
+        tot = ctypes.c_double(0)
+        cnt = ctypes.c_uint64(0)
+        by = ctypes.c_double(0)
+        lib.fk_profile_read(fid, ctypes.byref(tot), ctypes.byref(cnt), ctypes.byref(by))
+        if cnt.value:
+            fams[name] = (tot.value, cnt.value, by.value)
+    lib.fk_profile_reset()
+    peak, peak_kind = _peaks()
+    dom = max(fams.items(), key=lambda kv: kv[1][0]) if fams else None
+    roofline = None
+    if dom:
+        name, (tms, cnt, by) = dom
+        achieved = (by / cnt) / ((tms / cnt) / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": _traffic(name, by / cnt), "launches": cnt,
+                    "avg_launch_us": tms / cnt * 1e3, "alg_bytes_per_launch": by / cnt,
+                    "share_of_step": tms / total_ms}
+    breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                     "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None} for k, v in fams.items()}
+
+    # ---- per-call split and the FP64 GPU path on the same inputs
+    def timed(fn, reps=3):
+        vals = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            b.synchronize()
+            vals.append(a.elapsed_time(b))
+            del r
+        return statistics.median(vals)
+
+    if args.only:
+        print(json.dumps({"only": args.only, "n": n, "ms_per_step": ms_step, "families": breakdown}), flush=True)
+        return 0
+    split = {"ecdf_grid_ms": timed(lambda: fk.ecdf_grid(x, grid)),
+             "ecdf_points_ms": timed(lambda: fk.ecdf_points(x)),
+             "kde_mixed_ms": timed(lambda: fk.kde_laplace(x, H, path="mixed"))}
+    kde64 = timed(lambda: fk.kde_laplace(x, H, path="fp64"))
+    fp64 = {"kde_fp64_ms": kde64, "kde_mixed_ms": split["kde_mixed_ms"],
+            "mixed_speedup": kde64 / split["kde_mixed_ms"]}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(lib, x_np, grid, args, dev)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = _cpu_baseline(x_np, grid)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32/i64 counts; f32+f64 (mixed KDE)", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "d": D, "grid": [M_AXIS] * D, "orthants": 8,
+                           "h": H, "kde_path": "mixed", "l2": "flushed (256 MB write) between steps",
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "gpu_launches": int(launches), "roofline": roofline, "kernel_families": breakdown,
+                "split": split, "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _traffic(kernel, alg_bytes):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current build of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        from paper_2005_03246_gb300 import build as _b
+        if t.get("digest") != _b._digest() or kernel not in t.get("kernels", {}):
+            return None
+        return t["kernels"][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def _e2e(lib, x_np, grid, args, dev):
+    """Same step through the C ABI, inputs and outputs in pinned host memory."""
+    import torch
+    from paper_2005_03246_gb300 import _lib, mask_words
+    n = x_np.shape[0]
+    xh = torch.empty(x_np.shape, dtype=torch.float32).pin_memory()
+    xh.numpy()[:] = x_np
+    M = np.array([len(a) for a in grid], dtype=np.int64)
+    z = np.concatenate(grid).astype(np.float64)
+    gpts = int(np.prod(M))
+    og = torch.empty((8, gpts), dtype=torch.int64).pin_memory()
+    op = torch.empty((8, n), dtype=torch.int64).pin_memory()
+    of = torch.empty((n,), dtype=torch.float64).pin_memory()
+    h = np.array([H] * D, dtype=np.float64)
+    P = ctypes.c_void_p
+    st = P(torch.cuda.current_stream(dev).cuda_stream)
+
+    def call():
+        rc = lib.fk_ecdf_grid(P(xh.data_ptr()), _lib.FK_F32, n, D, None, z.ctypes.data_as(P),
+                              M.ctypes.data_as(P), None, P(og.data_ptr()), 0, None, 0, st)
+        _lib.check(rc, "fk_ecdf_grid(host)")
+        rc = lib.fk_ecdf_points(P(xh.data_ptr()), _lib.FK_F32, n, D, None, None, 0, None, P(op.data_ptr()), 0,
+                                None, 0, st)
+        _lib.check(rc, "fk_ecdf_points(host)")
+        rc = lib.fk_kde_laplace(P(xh.data_ptr()), _lib.FK_F32, n, D, None, None, 0, h.ctypes.data_as(P), 0,
+                                P(of.data_ptr()), None, 0, None, 0, st)
+        _lib.check(rc, "fk_kde_laplace(host)")
+
+    call()
+    torch.cuda.synchronize()
+    reps = max(2, min(args.steps, 5))
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        call()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    h2d = 3 * x_np.nbytes + z.nbytes
+    d2h = og.numel() * 8 + op.numel() * 8 + of.numel() * 8
+    return {"value": n / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": t * 1e3}
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -174,6 +174,24 @@ fk_status fk_kreg_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, cons
  */
 fk_status fk_device_status(fk_stream_t stream);
 
+/*
+ * ---------------------------------------------------------------- diagnostics
+ * Not part of the paper's problem statement: counters used to report
+ * performance.  fk_kernel_launches returns the number of CUDA kernels this
+ * library has launched in the calling process.  When profiling is enabled,
+ * the main kernel families are bracketed by CUDA events recorded on the
+ * stream each kernel is launched on, together with the algorithmic bytes the
+ * launch moves (inputs read once, outputs written once); fk_profile_read
+ * synchronises on those events and sums them for one family:
+ *   0 divide-and-conquer merge with sweep, 1 its per-tile totals pass,
+ *   2 plain merge (tree construction), 3 grid orthant pass, 4 grid histogram,
+ *   5 radix-sort pass, 6 gathers, 7 tile-local merge levels with sweep.
+ */
+uint64_t fk_kernel_launches(void);
+void fk_profile_enable(int on);
+void fk_profile_reset(void);
+fk_status fk_profile_read(int family, double* total_ms, uint64_t* launches, double* alg_bytes);
+
 #ifdef __cplusplus
 }
 #endif

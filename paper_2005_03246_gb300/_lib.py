@@ -32,7 +32,14 @@ SIGNATURES = {
     "fk_kde_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, P, I, P, SZ, P]),
     "fk_kreg_laplace_workspace": (SZ, [I64, I, I64, I, I]),
     "fk_kreg_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
+    "fk_kernel_launches": (ctypes.c_uint64, []),
+    "fk_profile_enable": (None, [I]),
+    "fk_profile_reset": (None, []),
+    "fk_profile_read": (I, [I, P, P, P]),
 }
+
+PROFILE_FAMILIES = {"merge_sweep": 0, "merge_totals": 1, "merge_plain": 2, "grid_pass": 3,
+                    "grid_hist": 4, "radix": 5, "gather": 6, "local_sweep": 7}
 
 _lib = None
 

@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "fk_dc_ops.cuh"
@@ -33,6 +35,31 @@ bool is_device_pointer(const void* p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfRec { int fam; double bytes; cudaEvent_t a, b; };
+static std::mutex g_prof_mu;
+static std::atomic<bool> g_prof_on{false};
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_free_events;
+bool profiling_on() { return g_prof_on.load(std::memory_order_relaxed); }
+cudaEvent_t prof_event() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+void prof_record(int family, double bytes, cudaEvent_t a, cudaEvent_t b) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(ProfRec{family, bytes, a, b});
 }
 
 // The per-device error word: kernels record the first device-side error here
@@ -134,6 +161,35 @@ extern "C" {
 const char* fk_last_error(void) { return g_msg; }
 
 const char* fk_version(void) { return "fastecdf-gb300 0.1 (sm_103a)"; }
+
+uint64_t fk_kernel_launches(void) { return (uint64_t)g_launches.load(); }
+
+void fk_profile_enable(int on) { g_prof_on.store(on != 0); }
+
+void fk_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof) { g_free_events.push_back(r.a); g_free_events.push_back(r.b); }
+    g_prof.clear();
+}
+
+fk_status fk_profile_read(int family, double* total_ms, uint64_t* launches, double* alg_bytes) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double ms = 0.0, by = 0.0;
+    uint64_t cnt = 0;
+    for (auto& r : g_prof) {
+        if (r.fam != family) continue;
+        FK_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        FK_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        by += r.bytes;
+        ++cnt;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = cnt;
+    if (alg_bytes) *alg_bytes = by;
+    return FK_OK;
+}
 
 fk_status fk_device_status(fk_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;

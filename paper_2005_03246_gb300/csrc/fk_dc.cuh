@@ -93,15 +93,27 @@ struct SAcc {
     __device__ uint32_t operator()(int64_t i) const { return p[i]; }
 };
 
+// Class bits of an item for the innermost sort: bit j = bit lvl[j] of idx[j][item].
+struct ClassSpecK {
+    const uint32_t* idx[6];
+    int lvl[6];
+    int nb;
+};
+__device__ __forceinline__ uint32_t class_of_k(const ClassSpecK& cs, uint32_t item) {
+    uint32_t c = 0;
+    for (int j = 0; j < cs.nb; ++j) c |= ((cs.idx[j][item] >> cs.lvl[j]) & 1u) << j;
+    return c;
+}
+
 // Phases of k_merge.
 enum { PH_PLAIN = 0, PH_TOTALS = 1, PH_SWEEP = 2 };
 
 // Scan of per-thread channel values over segments of `ts` consecutive threads
 // (ts a power of two, 1 < ts <= MT).  On return fe/be hold the exclusive
 // prefix (forward) and exclusive suffix (backward) within the segment.
-template <class Pol, int NCH>
+template <class Pol, int NCH, int NT = MT>
 __device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Pol::V (&be)[NCH],
-                                         int ts, typename Pol::V* sh /* [2][NCH][MT/32] */) {
+                                         int ts, typename Pol::V* sh /* [2][NCH][NT/32] */) {
     typedef typename Pol::V V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = ts < 32 ? ts : 32;
@@ -134,19 +146,19 @@ __device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Po
     const int wps = ts >> 5;                 // warps per segment
     if (lane == 31) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) sh[(0 * NCH + c) * (MT / 32) + warp] = fi[c];
+        for (int c = 0; c < NCH; ++c) sh[(0 * NCH + c) * (NT / 32) + warp] = fi[c];
     }
     if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) sh[(1 * NCH + c) * (MT / 32) + warp] = bi[c];
+        for (int c = 0; c < NCH; ++c) sh[(1 * NCH + c) * (NT / 32) + warp] = bi[c];
     }
     __syncthreads();
     const int seg0 = warp & ~(wps - 1);
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         V accf = Pol::zero(), accb = Pol::zero();
-        for (int q = seg0; q < warp; ++q) accf = Pol::add(accf, sh[(0 * NCH + c) * (MT / 32) + q]);
-        for (int q = warp + 1; q < seg0 + wps; ++q) accb = Pol::add(accb, sh[(1 * NCH + c) * (MT / 32) + q]);
+        for (int q = seg0; q < warp; ++q) accf = Pol::add(accf, sh[(0 * NCH + c) * (NT / 32) + q]);
+        for (int q = warp + 1; q < seg0 + wps; ++q) accb = Pol::add(accb, sh[(1 * NCH + c) * (NT / 32) + q]);
         fe[c] = Pol::add(accf, fe[c]);
         be[c] = Pol::add(be[c], accb);
     }
@@ -368,6 +380,226 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
             }
         }
     }
+}
+
+
+// ------------------------------------------------------------------ tile-local levels
+// All merge levels whose merged runs fit in one tile of LT items run in shared
+// memory in one launch.  The tile is gathered straight from the enclosing
+// state (items sorted by P_1 inside their nodes): key = P_0[item], class bits,
+// and the policy's per-item weights.  Targets accumulate their sums in shared
+// memory, indexed by the item's slot in the tile and by (half, direction):
+// inside one innermost sort the side bits of the enclosing axes are fixed, so
+// those four sums are all a target receives; they are flushed to the global
+// accumulators once (Pol::flush) after the last local level.
+template <class Pol>
+struct LocalCfg {
+    static constexpr int T = Pol::kLocalT;     // items per tile
+    static constexpr int NT = 512;             // threads
+    static constexpr int IT = T / NT;          // items per thread
+};
+
+template <class Pol, int CLSB>
+__global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict__ seq, int64_t n,
+                                                     const uint32_t* __restrict__ P0, ClassSpecK cs, int levels,
+                                                     Pol pol, uint32_t* __restrict__ key_out,
+                                                     uint32_t* __restrict__ meta_out, int write_out) {
+    typedef typename Pol::V V;
+    typedef typename Pol::LW LW;
+    constexpr int T = LocalCfg<Pol>::T, NT = LocalCfg<Pol>::NT, IT = LocalCfg<Pol>::IT;
+    constexpr int NCH = 2 << CLSB;
+    constexpr uint32_t CMASK = (1u << CLSB) - 1u;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw);             // [2][T]
+    uint32_t* s_meta = s_key + 2 * T;                                   // [2][T]
+    uint16_t* s_home = reinterpret_cast<uint16_t*>(s_meta + 2 * T);     // [2][T]
+    V* s_acc = reinterpret_cast<V*>(s_home + 2 * T);                    // [T][4]
+    LW* s_w = reinterpret_cast<LW*>(s_acc + 4 * T);                     // [T][4]
+    V* s_scan = reinterpret_cast<V*>(s_w + (Pol::kUnitWeights ? 0 : 4 * T));   // [2][NCH][NT/32]
+
+    const int64_t t0 = (int64_t)blockIdx.x * T;
+    const int ln = (int)min((int64_t)T, n - t0);
+    for (int i = threadIdx.x; i < T; i += NT) {
+        if (i < ln) {
+            const uint32_t item = seq[t0 + i];
+            const uint32_t c = class_of_k(cs, item);
+            s_key[i] = P0[item];
+            s_meta[i] = item | (c << kItemBits);
+            s_home[i] = (uint16_t)i;
+            pol.prep_item(item, c);
+            if constexpr (!Pol::kUnitWeights) {
+                if (pol.is_src(item)) pol.local_weights(item, c, &s_w[4 * i]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s_acc[4 * i + j] = Pol::zero();
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int m = 0; m < levels; ++m) {
+        const int R = 1 << m, R2 = 2 << m;
+        const uint32_t* ik = s_key + buf * T;
+        const uint32_t* im = s_meta + buf * T;
+        const uint16_t* ih = s_home + buf * T;
+        uint32_t em[IT];
+        uint16_t eh2[IT];
+        uint32_t ek[IT];
+        int eh[IT];
+        int cnt = 0;
+        {
+            const int p0 = threadIdx.x * IT;
+            int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+                const int p = p0 + e;
+                if (p < ln) {
+                    if (e == 0 || (p % R2) == 0) {
+                        bsl = (p / R2) * R2;
+                        cl = min(R, ln - bsl);
+                        dl = min(R2, ln - bsl) - cl;
+                        SAcc A{ik + bsl}, B{ik + bsl + cl};
+                        i = (int)merge_path(A, cl, B, dl, p - bsl);
+                        j = (p - bsl) - i;
+                    }
+                    const bool takeC = (i < cl) && (j >= dl || ik[bsl + i] <= ik[bsl + cl + j]);
+                    const int src = takeC ? bsl + i : bsl + cl + j;
+                    ek[e] = ik[src];
+                    em[e] = im[src];
+                    eh2[e] = ih[src];
+                    eh[e] = takeC ? 0 : 1;
+                    if (takeC) ++i; else ++j;
+                    cnt = e + 1;
+                }
+            }
+        }
+        // sweep over the merged blocks of length R2
+        V wf[IT], wb[IT];
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+            wf[e] = Pol::zero();
+            wb[e] = Pol::zero();
+            if (e < cnt) {
+                const uint32_t item = em[e] & kItemMask;
+                if (pol.is_src(item)) {
+                    if constexpr (Pol::kUnitWeights) { wf[e] = Pol::one(); wb[e] = Pol::one(); }
+                    else {
+                        wf[e] = Pol::from_lw(s_w[4 * eh2[e] + eh[e] * 2 + 0]);
+                        wb[e] = Pol::from_lw(s_w[4 * eh2[e] + eh[e] * 2 + 1]);
+                    }
+                }
+            }
+        }
+        const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
+        V fe[NCH], be[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { fe[c] = Pol::zero(); be[c] = Pol::zero(); }
+        if (ts > 1) {
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+                if (e < cnt) {
+                    const int ch = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c)
+                        if (c == ch) { fe[c] = Pol::add(fe[c], wf[e]); be[c] = Pol::add(be[c], wb[e]); }
+                }
+            }
+            seg_scan<Pol, NCH, NT>(fe, be, ts, s_scan);
+        }
+        V fwd[IT];
+        {
+            V run[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) run[c] = fe[c];
+            const int p0 = threadIdx.x * IT;
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+                fwd[e] = Pol::zero();
+                if (e < cnt) {
+                    if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
+                    }
+                    const int cls = (int)(em[e] >> kItemBits);
+                    const int own = (eh[e] << CLSB) | cls;
+                    const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c)
+                        if (c == opp) fwd[e] = run[c];
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c)
+                        if (c == own) run[c] = Pol::add(run[c], wf[e]);
+                }
+            }
+        }
+        {
+            V run[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) run[c] = be[c];
+            const int p0 = threadIdx.x * IT;
+#pragma unroll
+            for (int e = IT - 1; e >= 0; --e) {
+                if (e < cnt) {
+                    if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
+                    }
+                    const int cls = (int)(em[e] >> kItemBits);
+                    const int own = (eh[e] << CLSB) | cls;
+                    const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+                    V bwd = Pol::zero();
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c)
+                        if (c == opp) bwd = run[c];
+                    const uint32_t item = em[e] & kItemMask;
+                    if (pol.is_tgt(item)) {
+                        V* a = s_acc + 4 * eh2[e] + 2 * eh[e];
+                        a[0] = Pol::add(a[0], fwd[e]);
+                        a[1] = Pol::add(a[1], bwd);
+                    }
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c)
+                        if (c == own) run[c] = Pol::add(run[c], wb[e]);
+                }
+            }
+        }
+        // write the merged level into the other buffer
+        uint32_t* ok = s_key + (buf ^ 1) * T;
+        uint32_t* om = s_meta + (buf ^ 1) * T;
+        uint16_t* oh = s_home + (buf ^ 1) * T;
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+            if (e < cnt) {
+                const int p = threadIdx.x * IT + e;
+                ok[p] = ek[e];
+                om[p] = em[e];
+                oh[p] = eh2[e];
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    // flush the per-target sums and write the tile out for the global levels
+    for (int i = threadIdx.x; i < ln; i += NT) {
+        const uint32_t m = s_meta[buf * T + i];
+        const uint32_t item = m & kItemMask;
+        if (write_out) {
+            key_out[t0 + i] = s_key[buf * T + i];
+            meta_out[t0 + i] = m;
+        }
+        if (pol.is_tgt(item)) {
+            const int h = s_home[buf * T + i];
+            pol.flush(item, m >> kItemBits, s_acc + 4 * h);
+        }
+    }
+}
+
+template <class Pol, int CLSB>
+constexpr size_t local_smem_bytes() {
+    constexpr int T = LocalCfg<Pol>::T, NT = LocalCfg<Pol>::NT;
+    constexpr int NCH = 2 << CLSB;
+    return (size_t)T * (2 * 4 + 2 * 4 + 2 * 2) + (size_t)T * 4 * sizeof(typename Pol::V) +
+           (Pol::kUnitWeights ? 0 : (size_t)T * 4 * sizeof(typename Pol::LW)) +
+           (size_t)2 * NCH * (NT / 32) * sizeof(typename Pol::V) + 64;
 }
 
 // Carries for merged blocks that span several CTAs: exclusive prefix of the

@@ -160,6 +160,7 @@ using namespace dc;
 namespace dc {
 fk_status plain_merge_level(const MergeArgs& a, cudaStream_t st) {
     PolCount dummy{};
+    ProfScope ps(PF_MERGE_PLAIN, 16.0 * a.n, st);
     k_merge<PolCount, 0, PH_PLAIN><<<grid_for(a.n, MTILE), MT, 0, st>>>(a, dummy, nullptr, nullptr);
     FK_LAUNCH_CHECK();
     return FK_OK;
@@ -366,12 +367,19 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
     const unsigned gt = grid_for(n_tgt, 256);
     if (fp64) {
         k_fin_kernel<double, double><<<gt, 256, 0, st>>>((const double*)acc, n_tgt, nw, C, (const double*)wts, has_self, out);
-        if (tacc) k_fin_terms<double, double><<<gt, 256, 0, st>>>((const double*)tacc, n_tgt, d, d_eff, C, (const double*)wts, has_self, terms);
+        FK_LAUNCH_CHECK();
+        if (tacc) {
+            k_fin_terms<double, double><<<gt, 256, 0, st>>>((const double*)tacc, n_tgt, d, d_eff, C, (const double*)wts, has_self, terms);
+            FK_LAUNCH_CHECK();
+        }
     } else {
         k_fin_kernel<FF, float><<<gt, 256, 0, st>>>((const FF*)acc, n_tgt, nw, C, (const float*)wts, has_self, out);
-        if (tacc) k_fin_terms<FF, float><<<gt, 256, 0, st>>>((const FF*)tacc, n_tgt, d, d_eff, C, (const float*)wts, has_self, terms);
+        FK_LAUNCH_CHECK();
+        if (tacc) {
+            k_fin_terms<FF, float><<<gt, 256, 0, st>>>((const FF*)tacc, n_tgt, d, d_eff, C, (const float*)wts, has_self, terms);
+            FK_LAUNCH_CHECK();
+        }
     }
-    FK_LAUNCH_CHECK();
     return FK_OK;
 }
 

@@ -31,10 +31,26 @@ __device__ __forceinline__ uint32_t fwd_orthant(uint32_t pb, uint32_t pbmask) {
 // ------------------------------------------------------------------ orthant sums
 struct PolCount : ItemMap {
     typedef uint32_t V;
+    static constexpr int kSrcBytes = 0, kTgtBytes = 16, kTgtFacBytes = 0;
+    static constexpr int kLocalT = 4096;
+    static constexpr bool kUnitWeights = true;
+    struct LW { uint32_t unused; };
     uint32_t* acc;        // [2^d][n_tgt]
     uint32_t pbmask;
     __device__ static V zero() { return 0u; }
+    __device__ static V one() { return 1u; }
+    __device__ static V from_lw(LW) { return 1u; }
     __device__ static V add(V a, V b) { return a + b; }
+    __device__ void local_weights(uint32_t, uint32_t, LW*) const {}
+    __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
+        const int64_t t = (int64_t)item - tgt_off;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!loc[j]) continue;
+            const uint32_t o = fwd_orthant((uint32_t)(j >> 1) | (cls << 1), pbmask) | (uint32_t)(j & 1);
+            acc[(int64_t)o * n_tgt + t] += loc[j];
+        }
+    }
     __device__ void src_weights(uint32_t, int, V& f, V& b) const { f = 1u; b = 1u; }
     __device__ void prep_item(uint32_t, uint32_t) const {}
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
@@ -47,11 +63,29 @@ struct PolCount : ItemMap {
 
 struct PolW64 : ItemMap {
     typedef double V;
+    static constexpr int kSrcBytes = 8, kTgtBytes = 32, kTgtFacBytes = 0;
+    static constexpr int kLocalT = 2048;
+    static constexpr bool kUnitWeights = false;
+    typedef double LW;
     const double* w;      // [n_src]
     double* acc;          // [2^d][n_tgt]
     uint32_t pbmask;
     __device__ static V zero() { return 0.0; }
+    __device__ static V one() { return 1.0; }
+    __device__ static V from_lw(LW v) { return v; }
     __device__ static V add(V a, V b) { return a + b; }
+    __device__ void local_weights(uint32_t item, uint32_t, LW* o) const {
+        const double v = w[item];
+        o[0] = o[1] = o[2] = o[3] = v;
+    }
+    __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
+        const int64_t t = (int64_t)item - tgt_off;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t o = fwd_orthant((uint32_t)(j >> 1) | (cls << 1), pbmask) | (uint32_t)(j & 1);
+            acc[(int64_t)o * n_tgt + t] += loc[j];
+        }
+    }
     __device__ void src_weights(uint32_t item, int, V& f, V& b) const { f = b = w[item]; }
     __device__ void prep_item(uint32_t, uint32_t) const {}
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
@@ -64,11 +98,29 @@ struct PolW64 : ItemMap {
 
 struct PolWFF : ItemMap {
     typedef FF V;
+    static constexpr int kSrcBytes = 8, kTgtBytes = 32, kTgtFacBytes = 0;
+    static constexpr int kLocalT = 2048;
+    static constexpr bool kUnitWeights = false;
+    typedef FF LW;
     const FF* w;          // [n_src] weights split into hi + lo
     FF* acc;              // [2^d][n_tgt]
     uint32_t pbmask;
     __device__ static V zero() { return ff_zero(); }
+    __device__ static V one() { return FF{1.f, 0.f}; }
+    __device__ static V from_lw(LW v) { return v; }
     __device__ static V add(V a, V b) { return ff_add(a, b); }
+    __device__ void local_weights(uint32_t item, uint32_t, LW* o) const {
+        const FF v = w[item];
+        o[0] = o[1] = o[2] = o[3] = v;
+    }
+    __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
+        const int64_t t = (int64_t)item - tgt_off;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t o = fwd_orthant((uint32_t)(j >> 1) | (cls << 1), pbmask) | (uint32_t)(j & 1);
+            acc[(int64_t)o * n_tgt + t] = ff_add(acc[(int64_t)o * n_tgt + t], loc[j]);
+        }
+    }
     __device__ void src_weights(uint32_t item, int, V& f, V& b) const { f = b = w[item]; }
     __device__ void prep_item(uint32_t, uint32_t) const {}
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
@@ -99,6 +151,10 @@ struct SDn { SD v[NW]; };
 template <int NW>
 struct PolKF : ItemMap {
     typedef SFFn<NW> V;
+    static constexpr int kSrcBytes = 36, kTgtBytes = 16 * NW, kTgtFacBytes = 32;
+    static constexpr int kLocalT = NW == 1 ? 2048 : 1024;
+    static constexpr bool kUnitWeights = false;
+    struct LW { float m[NW]; int s; };
     const float* w;           // [n_src] weights (kreg: y), or nullptr for 1
     const FacF* fac;          // [d][n_items]
     int64_t n_items;
@@ -119,7 +175,19 @@ struct PolKF : ItemMap {
         for (int i = 0; i < NW; ++i) r.v[i] = sff_add(a.v[i], b.v[i]);
         return r;
     }
-    __device__ void prep_item(uint32_t item, uint32_t cls) const {
+    __device__ static V one() {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = SFF{1.f, 0.f, 0};
+        return r;
+    }
+    __device__ static V from_lw(const LW& l) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = SFF{l.m[i], 0.f, l.s};
+        return r;
+    }
+    __device__ BaseF base_of(uint32_t item, uint32_t cls) const {
         float m = 1.f;
         int s = 0;
         for (int j = 0; j < nbase; ++j) {
@@ -128,7 +196,52 @@ struct PolKF : ItemMap {
             m *= up ? f.mm : f.mp;
             s += up ? -f.s : f.s;
         }
-        base[item] = BaseF{m, s};
+        return BaseF{m, s};
+    }
+    __device__ void prep_item(uint32_t item, uint32_t cls) const { base[item] = base_of(item, cls); }
+    // source weights w B E1^{+-} E0^{+-} for (half, direction) = (j >> 1, j & 1)
+    __device__ void local_weights(uint32_t item, uint32_t cls, LW* o) const {
+        const BaseF B = base_of(item, cls);
+        const FacF e1 = fac[(int64_t)1 * n_items + item];
+        const FacF e0 = fac[item];
+        const float w0 = w ? w[item] : 1.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int h = j >> 1, dir = j & 1;
+            const float mm = B.m * (h ? e1.mm : e1.mp) * (dir ? e0.mm : e0.mp);
+            LW l;
+            l.s = B.s + (h ? -e1.s : e1.s) + (dir ? -e0.s : e0.s);
+#pragma unroll
+            for (int i = 0; i < NW; ++i) l.m[i] = ((NW == 2 && i == 1) ? 1.f : w0) * mm;
+            o[j] = l;
+        }
+    }
+    // target factors B E1^{+-} E0^{-+} applied once to the four local sums
+    __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const BaseF B = base_of(item, cls);
+        const FacF e1 = fac[(int64_t)1 * n_items + item];
+        const FacF e0 = fac[item];
+        FF a[NW];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) a[i] = acc[(int64_t)i * n_tgt + t];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int h = j >> 1, dir = j & 1;
+            const float tf = B.m * (h ? e1.mm : e1.mp) * (dir ? e0.mp : e0.mm);
+            const int ts = B.s + (h ? -e1.s : e1.s) + (dir ? e0.s : -e0.s);
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                const float c = (loc[j].v[i].hi + loc[j].v[i].lo) * tf * pow2f_any(loc[j].v[i].e + ts);
+                a[i] = ff_add_f(a[i], c);
+                if (i == 0 && terms) {
+                    const uint32_t o = fwd_orthant((uint32_t)h | (cls << 1), pbmask) | (uint32_t)dir;
+                    terms[(int64_t)o * n_tgt + t] = ff_add_f(terms[(int64_t)o * n_tgt + t], c);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] = a[i];
     }
     __device__ void src_weights(uint32_t item, int half, V& f, V& b) const {
         const FacF e1 = fac[(int64_t)1 * n_items + item];
@@ -177,6 +290,10 @@ struct PolKF : ItemMap {
 template <int NW>
 struct PolKD : ItemMap {
     typedef SDn<NW> V;
+    static constexpr int kSrcBytes = 72, kTgtBytes = 16 * NW, kTgtFacBytes = 64;
+    static constexpr int kLocalT = NW == 1 ? 1024 : 512;
+    static constexpr bool kUnitWeights = false;
+    struct LW { double m[NW]; int s; int pad; };
     const double* w;
     const FacD* fac;
     int64_t n_items;
@@ -197,7 +314,19 @@ struct PolKD : ItemMap {
         for (int i = 0; i < NW; ++i) r.v[i] = sd_add(a.v[i], b.v[i]);
         return r;
     }
-    __device__ void prep_item(uint32_t item, uint32_t cls) const {
+    __device__ static V one() {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = SD{1.0, 0};
+        return r;
+    }
+    __device__ static V from_lw(const LW& l) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = SD{l.m[i], l.s};
+        return r;
+    }
+    __device__ BaseD base_of(uint32_t item, uint32_t cls) const {
         double m = 1.0;
         int s = 0;
         for (int j = 0; j < nbase; ++j) {
@@ -206,7 +335,46 @@ struct PolKD : ItemMap {
             m *= up ? f.mm : f.mp;
             s += up ? -f.s : f.s;
         }
-        base[item] = BaseD{m, s, 0};
+        return BaseD{m, s, 0};
+    }
+    __device__ void prep_item(uint32_t item, uint32_t cls) const { base[item] = base_of(item, cls); }
+    __device__ void local_weights(uint32_t item, uint32_t cls, LW* o) const {
+        const BaseD B = base_of(item, cls);
+        const FacD e1 = fac[(int64_t)1 * n_items + item];
+        const FacD e0 = fac[item];
+        const double w0 = w ? w[item] : 1.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int h = j >> 1, dir = j & 1;
+            const double mm = B.m * (h ? e1.mm : e1.mp) * (dir ? e0.mm : e0.mp);
+            LW l;
+            l.s = B.s + (h ? -e1.s : e1.s) + (dir ? -e0.s : e0.s);
+            l.pad = 0;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) l.m[i] = ((NW == 2 && i == 1) ? 1.0 : w0) * mm;
+            o[j] = l;
+        }
+    }
+    __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
+        const int64_t t = (int64_t)item - tgt_off;
+        const BaseD B = base_of(item, cls);
+        const FacD e1 = fac[(int64_t)1 * n_items + item];
+        const FacD e0 = fac[item];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int h = j >> 1, dir = j & 1;
+            const double tf = B.m * (h ? e1.mm : e1.mp) * (dir ? e0.mp : e0.mm);
+            const int ts = B.s + (h ? -e1.s : e1.s) + (dir ? e0.s : -e0.s);
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                const double c = loc[j].v[i].m * tf * pow2d_any(loc[j].v[i].e + ts);
+                acc[(int64_t)i * n_tgt + t] += c;
+                if (i == 0 && terms) {
+                    const uint32_t o = fwd_orthant((uint32_t)h | (cls << 1), pbmask) | (uint32_t)dir;
+                    terms[(int64_t)o * n_tgt + t] += c;
+                }
+            }
+        }
     }
     __device__ void src_weights(uint32_t item, int half, V& f, V& b) const {
         const FacD e1 = fac[(int64_t)1 * n_items + item];
@@ -250,31 +418,7 @@ struct PolKD : ItemMap {
 };
 
 // ------------------------------------------------------------------ gathers
-// Class bits of an item for the innermost sort: bit j = bit lvl[j] of idx[j][item].
-struct ClassSpec {
-    const uint32_t* idx[6];
-    int lvl[6];
-    int nb;
-};
-
-__device__ __forceinline__ uint32_t class_of(const ClassSpec& cs, uint32_t item) {
-    uint32_t c = 0;
-    for (int j = 0; j < cs.nb; ++j) c |= ((cs.idx[j][item] >> cs.lvl[j]) & 1u) << j;
-    return c;
-}
-
-// Inner (sweep) sort input: key = P_0[item], meta = item | class << 26.
-template <class Pol>
-__global__ void k_gather_inner(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0,
-                               ClassSpec cs, Pol pol, uint32_t* __restrict__ key, uint32_t* __restrict__ meta) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t item = seq[p];
-    const uint32_t c = class_of(cs, item);
-    key[p] = P0[item];
-    meta[p] = item | (c << kItemBits);
-    pol.prep_item(item, c);
-}
+typedef ClassSpecK ClassSpec;
 
 // ------------------------------------------------------------------ driver
 struct DCBuffers {
@@ -300,26 +444,54 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
                      const Pol& pol, DCBuffers& b, cudaStream_t st) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
-    k_gather_inner<Pol><<<grid_for(n, 256), 256, 0, st>>>(seq, n, P0, cs, pol, b.k[0], b.m[0]);
-    FK_LAUNCH_CHECK();
+    // tile-local levels (gather fused into the tile load)
+    constexpr int T = LocalCfg<Pol>::T;
+    int lt = 0;
+    while ((1 << (lt + 1)) <= T) ++lt;
+    const int L0 = E < lt ? E : lt;
+    {
+        constexpr size_t smem = local_smem_bytes<Pol, CLSB>();
+        static bool attr_set = false;
+        if (!attr_set) {
+            FK_CUDA(cudaFuncSetAttribute(k_local_sweep<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+            attr_set = true;
+        }
+        const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
+                              (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes) + (E > L0 ? 8.0 * n : 0.0);
+        ProfScope ps(PF_LOCAL, lbytes, st);
+        k_local_sweep<Pol, CLSB><<<grid_for(n, T), LocalCfg<Pol>::NT, smem, st>>>(seq, n, P0, cs, L0, pol, b.k[0],
+                                                                                 b.m[0], E > L0 ? 1 : 0);
+        FK_LAUNCH_CHECK();
+    }
     int cur = 0;
     const unsigned ctas = grid_for(n, MTILE);
-    for (int m = 0; m < E; ++m) {
+    // algorithmic bytes of one sweep merge: keys+metas in and out, source
+    // weights read once, target accumulators read and written once
+    const double sweep_bytes = 16.0 * n + (double)pol.n_src * Pol::kSrcBytes + (double)pol.n_tgt * Pol::kTgtBytes +
+                               (pol.tgt_off > 0 ? (double)pol.n_tgt * Pol::kTgtFacBytes : 0.0);
+    for (int m = L0; m < E; ++m) {
         MergeArgs a{b.k[cur], b.m[cur], b.k[cur ^ 1], b.m[cur ^ 1], n, m};
         const int64_t R2 = (int64_t)2 << m;
         if (R2 > MTILE) {
-            k_merge<Pol, CLSB, PH_TOTALS><<<ctas, MT, 0, st>>>(a, pol, (V*)b.totals, nullptr);
-            FK_LAUNCH_CHECK();
+            {
+                ProfScope ps(PF_MERGE_TOTALS, 8.0 * n + (double)pol.n_src * Pol::kSrcBytes, st);
+                k_merge<Pol, CLSB, PH_TOTALS><<<ctas, MT, 0, st>>>(a, pol, (V*)b.totals, nullptr);
+                FK_LAUNCH_CHECK();
+            }
             const int64_t per = R2 / MTILE;
             const int64_t nblk = ((int64_t)ctas + per - 1) / per;
             k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2, 128), 128, 0, st>>>((const V*)b.totals,
                                                                               (V*)b.carries, n, m);
             FK_LAUNCH_CHECK();
+            ProfScope ps(PF_MERGE_SWEEP, sweep_bytes, st);
             k_merge<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, pol, nullptr, (const V*)b.carries);
+            FK_LAUNCH_CHECK();
         } else {
+            ProfScope ps(PF_MERGE_SWEEP, sweep_bytes, st);
             k_merge<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, pol, nullptr, nullptr);
+            FK_LAUNCH_CHECK();
         }
-        FK_LAUNCH_CHECK();
         cur ^= 1;
     }
     return FK_OK;

@@ -273,6 +273,9 @@ fk_status run_passes(typename Op::A* hist, typename Op::A* b1, typename Op::A* b
         for (int a = 0; a < k; ++a) outer *= (M[a] + 1);
         for (int a = k + 1; a < d; ++a) inner *= M[a];
         int64_t E = M[k] + 1;
+        // algorithmic bytes: every input cell read once, every output written once
+        const double obytes = fin ? (double)sizeof(typename Op::O) : (double)sizeof(A);
+        ProfScope ps(PF_GRID_PASS, (double)cin * outer * inner * ((double)E * sizeof(A) + 2.0 * (E - 1) * obytes), st);
         if (inner == 1) {
             int64_t warps = cin * outer;
             unsigned blocks = grid_for(warps * 32, 256);
@@ -341,6 +344,7 @@ fk_status grid_run(const void* x, fk_dtype xd, int64_t N, int d, const void* y,
     FK_LAUNCH_CHECK();
     unsigned blocks = grid_for(N, 256);
     if (N > 0) {
+        ProfScope ps(PF_GRID_HIST, (double)N * (d * (xd == FK_F64 ? 8 : 4) + (weighted ? 16 : 8)), st);
         if (!weighted) {
             if (xd == FK_F32) k_grid_hist_count<float><<<blocks, 256, 0, st>>>((const float*)x, N, g, (uint32_t*)hist);
             else k_grid_hist_count<double><<<blocks, 256, 0, st>>>((const double*)x, N, g, (uint32_t*)hist);

@@ -25,7 +25,39 @@ fk_status cuda_error(cudaError_t e, const char* where);
         if (fk_s_ != FK_OK) return fk_s_;   \
     } while (0)
 
-#define FK_LAUNCH_CHECK() FK_CUDA(cudaGetLastError())
+// Every kernel launch site is followed by FK_LAUNCH_CHECK(), which also counts it.
+void note_launch();
+#define FK_LAUNCH_CHECK()          \
+    do {                           \
+        ::fk::note_launch();       \
+        FK_CUDA(cudaGetLastError()); \
+    } while (0)
+
+// Optional CUDA-event timing of kernel families (fk_profile_*).
+enum ProfFamily : int { PF_MERGE_SWEEP = 0, PF_MERGE_TOTALS = 1, PF_MERGE_PLAIN = 2, PF_GRID_PASS = 3,
+                        PF_GRID_HIST = 4, PF_RADIX = 5, PF_GATHER = 6, PF_LOCAL = 7, PF_COUNT = 8 };
+bool profiling_on();
+void prof_record(int family, double bytes, cudaEvent_t a, cudaEvent_t b);
+cudaEvent_t prof_event();
+struct ProfScope {
+    int fam;
+    double bytes;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(int f, double b, cudaStream_t s) : fam(f), bytes(b), st(s) {
+        if (profiling_on()) {
+            a = prof_event();
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEvent_t b2 = prof_event();
+            cudaEventRecord(b2, st);
+            prof_record(fam, bytes, a, b2);
+        }
+    }
+};
 
 // Device-side error codes recorded in the per-device error word.
 enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };

@@ -191,6 +191,7 @@ fk_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_a
     K* src_k = keys; uint32_t* src_v = vals;
     K* dst_k = keys_alt; uint32_t* dst_v = vals_alt;
     for (int shift = 0; shift < key_bits; shift += kRadixBits) {
+        ProfScope ps(PF_RADIX, 3.0 * n * (sizeof(K) + 4), st);
         k_radix_hist<K><<<(unsigned)tiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, tiles);
         FK_LAUNCH_CHECK();
         FK_TRY(scan_u32_exclusive(hist, hist, hn, stmp, st));
