@@ -167,6 +167,29 @@ fk_status fk_kreg_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, cons
                           fk_stream_t stream);
 
 /*
+ * fk_ecdf_grid_counts_noalloc -- the paper has no counterpart to this call; it
+ * exists for callers that may not allocate device memory while they run: loops
+ * that forbid allocation after start-up (cudaMalloc can synchronise the device
+ * and take unbounded time) and host applications that own the whole device
+ * memory budget.  It computes the same int64 orthant counts as fk_ecdf_grid
+ * with y == NULL, but never allocates: its scratch is a fixed 16 MiB array in
+ * the library image, reserved on every GPU that loads the library until the
+ * process exits.  A grid whose scratch (histogram and per-axis pass buffers,
+ * about 4 bytes per cell of the (M_1+1)...(M_d+1) histogram plus two pass
+ * buffers of up to 2^(d-1) (M_1+1)...(M_d+1) 4-byte entries) would exceed it
+ * returns FK_ERR_UNSUPPORTED.  x, z_axes and out must be device pointers
+ * (host arrays would need staging buffers); M and orthant_mask are host
+ * arrays as for fk_ecdf_grid.  The first call on a device looks up the
+ * scratch's device address on that device (make it the current device).
+ * Every call uses the same scratch and zeroes the part it accumulates into;
+ * calls whose work overlaps on the GPU (concurrent streams, or several host
+ * threads on one device) race on it and must be serialised by the caller.
+ */
+fk_status fk_ecdf_grid_counts_noalloc(const void* x, fk_dtype xdtype, int64_t N, int d, const double* z_axes,
+                                      const int64_t* M, const uint32_t* orthant_mask, int64_t* out,
+                                      fk_stream_t stream);
+
+/*
  * fk_device_status -- synchronises `stream` and returns (and clears) the
  * device-side error word of the current device: FK_OK, or the first error a
  * kernel recorded since the last call (e.g. FK_ERR_TIMEOUT from a bounded
