@@ -167,6 +167,39 @@ fk_status fk_kreg_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, cons
                           fk_stream_t stream);
 
 /*
+ * ---------------------------------------------------------------- adjoints
+ * fk_kde_laplace_backward -- exact adjoint of fk_kde_laplace (derivatives of
+ * eq. Laplacian kde nD), for the upstream gradient grad_out [M'] (double):
+ *   grad_w [N]    sum_j g_j C e^{-D_ij}: the transposed kernel sum, computed by
+ *                 the same engine with sources and targets swapped;
+ *   grad_z [M][d] (explicit targets only) g_j (1/h_k) sum_delta (-delta_k) T_delta(j)
+ *                 from the per-orthant terms T of eq. (Laplacian decomposition
+ *                 nD); where x_ik == z_jk the pair counts in the <= orthant;
+ *   grad_h [d]    sum_j g_j (-f_j/h_k + (1/h_k^2) sum_i C w_i e^{-D_ij}|x_ik - z_jk|),
+ *                 the distance sums taken from d extra orthant-term passes with
+ *                 weights w_i x_ik (|x - z|-weighted orthant sums).
+ * Any of the three outputs may be NULL.  Same flags (FK_LOO), precision paths
+ * and conventions as fk_kde_laplace.
+ */
+size_t fk_kde_laplace_backward_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path);
+fk_status fk_kde_laplace_backward(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w,
+                                  const void* z, int64_t M, const double* h, unsigned flags,
+                                  const double* grad_out, double* grad_w, double* grad_z, double* grad_h,
+                                  fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_loo_laplace -- leave-one-out log-likelihood of the Laplacian KDE at the
+ * sample points, L(h) = (1/N) sum_j log f_{-j}(x_j) with f_{-j} the density of
+ * the other N-1 points (normalised by N-1), and its gradient dL/dh [d]
+ * (grad_h may be NULL): the forward pass with FK_LOO followed by the h-adjoint
+ * with g_j = 1/(N f_{-j}).  loglik: [1] double.  N >= 2.
+ */
+size_t fk_loo_laplace_workspace(int64_t N, int d, fk_path path);
+fk_status fk_loo_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w, const double* h,
+                         double* loglik, double* grad_h, fk_path path, void* ws, size_t ws_bytes,
+                         fk_stream_t stream);
+
+/*
  * fk_ecdf_grid_counts_noalloc -- the paper has no counterpart to this call; it
  * exists for callers that may not allocate device memory while they run: loops
  * that forbid allocation after start-up (cudaMalloc can synchronise the device

@@ -16,7 +16,8 @@ import numpy as np
 from . import _lib
 from ._lib import FastEcdfError
 
-__all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplace",
+__all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplace", "kde",
+           "kde_laplace_backward", "loo_laplace", "select_bandwidth_loo",
            "FastEcdfError", "mask_words"]
 
 
@@ -228,3 +229,129 @@ def kreg_laplace(x, y, h, z=None, loo=False, path="mixed"):
                              pc, _ptr(ws), wsb, _stream_ptr(dev))
     _lib.check(rc, "fk_kreg_laplace")
     return out
+
+
+# ----------------------------------------------------------------------------- adjoints
+
+
+def kde_laplace_backward(x, h, grad_out, w=None, z=None, loo=False, need_w=True, need_z=True, need_h=True,
+                         path="mixed"):
+    """Adjoint of ``kde_laplace`` for the upstream gradient ``grad_out`` [M']:
+    returns (grad_w [N] or None, grad_z [M, d] or None, grad_h [d] or None),
+    float64 tensors on x's device (exact derivatives of eq. Laplacian kde nD)."""
+    torch = _torch()
+    lib = _lib.load()
+    x = _prep_points(x)
+    n, d = x.shape
+    dev = x.device
+    w = _weights(w, x)
+    z, m = _prep_targets(z, x)
+    hh = _h_array(h, d)
+    mo = m if z is not None else n
+    g = grad_out.to(device=dev, dtype=torch.float64).reshape(-1).contiguous()
+    if g.shape[0] != mo:
+        raise ValueError("grad_out must have one entry per target")
+    gw = torch.empty((n,), dtype=torch.float64, device=dev) if need_w else None
+    gz = torch.empty((mo, d), dtype=torch.float64, device=dev) if (need_z and z is not None) else None
+    gh = torch.empty((d,), dtype=torch.float64, device=dev) if need_h else None
+    pc = _path_code(path)
+    need = lib.fk_kde_laplace_backward_workspace(n, d, m, int(z is None), pc)
+    ws, wsb = _workspace(need, dev)
+    rc = lib.fk_kde_laplace_backward(_ptr(x), _dtype_code(x.dtype), n, d, _ptr(w), _ptr(z), m,
+                                     hh.ctypes.data_as(ctypes.c_void_p), _lib.FK_LOO if loo else 0, _ptr(g),
+                                     _ptr(gw), _ptr(gz), _ptr(gh), pc, _ptr(ws), wsb, _stream_ptr(dev))
+    _lib.check(rc, "fk_kde_laplace_backward")
+    return gw, gz, gh
+
+
+def loo_laplace(x, h, w=None, path="mixed", grad=True):
+    """Leave-one-out log-likelihood L(h) = mean_j log f_{-j}(x_j) of the
+    Laplacian KDE and dL/dh [d].  Returns (L as a 0-d float64 tensor, grad_h)."""
+    torch = _torch()
+    lib = _lib.load()
+    x = _prep_points(x)
+    n, d = x.shape
+    dev = x.device
+    w = _weights(w, x)
+    hh = _h_array(h, d)
+    L = torch.empty((1,), dtype=torch.float64, device=dev)
+    gh = torch.empty((d,), dtype=torch.float64, device=dev) if grad else None
+    pc = _path_code(path)
+    need = lib.fk_loo_laplace_workspace(n, d, pc)
+    ws, wsb = _workspace(need, dev)
+    rc = lib.fk_loo_laplace(_ptr(x), _dtype_code(x.dtype), n, d, _ptr(w), hh.ctypes.data_as(ctypes.c_void_p),
+                            _ptr(L), _ptr(gh), pc, _ptr(ws), wsb, _stream_ptr(dev))
+    _lib.check(rc, "fk_loo_laplace")
+    return L[0], gh
+
+
+def _kde_function():
+    torch = _torch()
+
+    class KDELaplace(torch.autograd.Function):
+        """f = kde_laplace(x, h, w, z) with the hand-written adjoint in w, z and h."""
+
+        @staticmethod
+        def forward(ctx, x, w, z, h, loo, path):
+            hv = h.detach().to(torch.float64).cpu().numpy()
+            f = kde_laplace(x, hv, w=w, z=z, loo=loo, path=path)
+            ctx.save_for_backward(x, w if w is not None else torch.empty(0), z if z is not None else torch.empty(0))
+            ctx.has_w, ctx.has_z = w is not None, z is not None
+            ctx.hv, ctx.loo, ctx.path, ctx.hdev, ctx.hdt = hv, loo, path, h.device, h.dtype
+            return f
+
+        @staticmethod
+        def backward(ctx, gf):
+            x, w, z = ctx.saved_tensors
+            w = w if ctx.has_w else None
+            z = z if ctx.has_z else None
+            nw, nz, nh = ctx.needs_input_grad[1], ctx.needs_input_grad[2], ctx.needs_input_grad[3]
+            gw, gz, gh = kde_laplace_backward(x, ctx.hv, gf, w=w, z=z, loo=ctx.loo, need_w=nw, need_z=nz,
+                                              need_h=nh, path=ctx.path)
+            if gw is not None and w is not None:
+                gw = gw.to(w.dtype)
+            if gz is not None and z is not None:
+                gz = gz.to(z.dtype)
+            if gh is not None:
+                gh = gh.to(device=ctx.hdev, dtype=ctx.hdt)
+            return None, gw, gz, gh, None, None
+
+    return KDELaplace
+
+
+_KDE_FN = None
+
+
+def kde(x, h, w=None, z=None, loo=False, path="mixed"):
+    """Differentiable Laplacian KDE: gradients flow to w, z and h (a tensor of
+    shape [d] or scalar) through the C-ABI adjoint (fk_kde_laplace_backward)."""
+    global _KDE_FN
+    torch = _torch()
+    if _KDE_FN is None:
+        _KDE_FN = _kde_function()
+    x = _prep_points(x)
+    d = x.shape[1]
+    if not isinstance(h, torch.Tensor):
+        h = torch.tensor(h, dtype=torch.float64)
+    hfull = h.reshape(-1).expand(d) if h.numel() == 1 else h.reshape(-1)
+    return _KDE_FN.apply(x, w, z, hfull, loo, path)
+
+
+def select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, w=None, path="mixed", per_axis=False):
+    """Leave-one-out likelihood bandwidth selection: gradient ascent on u = log h,
+    u <- u + lr * dL/du (dL/du = h * dL/dh), from h0, for `steps` steps.
+    Returns a list of (h, L, dL/dh) per step (h before the step)."""
+    x = _prep_points(x)
+    d = x.shape[1]
+    u = np.log(np.broadcast_to(np.asarray(h0, dtype=np.float64), (d,)).copy())
+    hist = []
+    for _ in range(steps):
+        h = np.exp(u)
+        L, gh = loo_laplace(x, h, w=w, path=path)
+        g = gh.cpu().numpy()
+        hist.append((h.copy(), float(L.item()), g.copy()))
+        if per_axis:
+            u = u + lr * h * g
+        else:
+            u = u + lr * float(np.sum(h * g))
+    return hist

@@ -32,6 +32,10 @@ SIGNATURES = {
     "fk_kde_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, P, I, P, SZ, P]),
     "fk_kreg_laplace_workspace": (SZ, [I64, I, I64, I, I]),
     "fk_kreg_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
+    "fk_kde_laplace_backward_workspace": (SZ, [I64, I, I64, I, I]),
+    "fk_kde_laplace_backward": (I, [P, I, I64, I, P, P, I64, P, U, P, P, P, P, I, P, SZ, P]),
+    "fk_loo_laplace_workspace": (SZ, [I64, I, I]),
+    "fk_loo_laplace": (I, [P, I, I64, I, P, P, P, P, I, P, SZ, P]),
     "fk_ecdf_grid_counts_noalloc": (I, [P, I, I64, I, P, P, P, P, P]),
     "fk_kernel_launches": (ctypes.c_uint64, []),
     "fk_profile_enable": (None, [I]),

@@ -11,6 +11,11 @@
 #include "fk_dc_ops.cuh"
 
 namespace fk {
+fk_status kde_backward_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                           const double* h, unsigned flags, const double* g, double* gw, double* gz, double* gh,
+                           fk_path path, Arena& ar, cudaStream_t st);
+fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* h, double* L,
+                  double* gh, fk_path path, Arena& ar, cudaStream_t st);
 
 static thread_local char g_msg[512] = "no error";
 
@@ -420,6 +425,97 @@ fk_status fk_kreg_laplace(const void* x, fk_dtype xd, int64_t N, int d, const vo
                           const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
                           fk_stream_t stream) {
     return kernel_impl(x, xd, N, d, y, z, M, h, flags, 2, out, nullptr, path, ws, ws_bytes, stream);
+}
+
+// ------------------------------------------------------------------ adjoints
+size_t fk_kde_laplace_backward_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
+    const void* z = sample_points ? nullptr : (const void*)1;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, false) != FK_OK) return 0;
+    double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    size_t best = 0;
+    for (int t = 0; t < 2; ++t) {
+        Arena ar;
+        kde_backward_run(nullptr, t ? FK_F64 : FK_F32, N, d, (const void*)1, z, M, h, 0, nullptr, (double*)1,
+                         sample_points ? nullptr : (double*)1, (double*)1, path, ar, 0);
+        if (ar.used > best) best = ar.used;
+    }
+    return best;
+}
+
+fk_status fk_kde_laplace_backward(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
+                                  int64_t M, const double* h, unsigned flags, const double* grad_out,
+                                  double* grad_w, double* grad_z, double* grad_h, fk_path path, void* ws,
+                                  size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(points_validate(x, xd, N, d, z, M, path, false));
+    FK_TRY(check_h(h, d));
+    if ((flags & FK_LOO) && z) return set_error(FK_ERR_INVALID_ARG, "FK_LOO needs z == NULL");
+    if (grad_z && !z) return set_error(FK_ERR_INVALID_ARG, "grad_z needs explicit targets z");
+    const int64_t m_out = z ? M : N;
+    if (m_out > 0 && !grad_out) return set_error(FK_ERR_INVALID_ARG, "grad_out is NULL");
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xp = nullptr, *wp = nullptr, *zp = nullptr, *gp = nullptr;
+    void *gwp = nullptr, *gzp = nullptr, *ghp = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xp));
+    FK_TRY(sg.in(w, (size_t)N * ds, &wp));
+    FK_TRY(sg.in(z, z ? (size_t)M * d * ds : 0, &zp));
+    FK_TRY(sg.in(grad_out, (size_t)m_out * 8, &gp));
+    FK_TRY(sg.out(grad_w, (size_t)N * 8, &gwp));
+    FK_TRY(sg.out(grad_z, z ? (size_t)M * d * 8 : 0, &gzp));
+    FK_TRY(sg.out(grad_h, (size_t)d * 8, &ghp));
+    Arena plan;
+    kde_backward_run(nullptr, xd, N, d, w, z, M, h, flags, nullptr, (double*)grad_w, (double*)grad_z,
+                     (double*)grad_h, path, plan, st);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    if (N == 0 || m_out == 0) {
+        if (gwp && N) FK_CUDA(cudaMemsetAsync(gwp, 0, (size_t)N * 8, st));
+        if (gzp && M) FK_CUDA(cudaMemsetAsync(gzp, 0, (size_t)M * d * 8, st));
+        if (ghp) FK_CUDA(cudaMemsetAsync(ghp, 0, (size_t)d * 8, st));
+        return sg.finish();
+    }
+    FK_TRY(kde_backward_run(xp, xd, N, d, wp, zp, M, h, flags, (const double*)gp, (double*)gwp, (double*)gzp,
+                            (double*)ghp, path, ar, st));
+    return sg.finish();
+}
+
+size_t fk_loo_laplace_workspace(int64_t N, int d, fk_path path) {
+    if (points_validate((const void*)1, FK_F32, N, d, nullptr, 0, path, false) != FK_OK) return 0;
+    double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    size_t best = 0;
+    for (int t = 0; t < 2; ++t) {
+        Arena ar;
+        loo_run(nullptr, t ? FK_F64 : FK_F32, N, d, (const void*)1, h, (double*)1, (double*)1, path, ar, 0);
+        if (ar.used > best) best = ar.used;
+    }
+    return best;
+}
+
+fk_status fk_loo_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* h,
+                         double* loglik, double* grad_h, fk_path path, void* ws, size_t ws_bytes,
+                         fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(points_validate(x, xd, N, d, nullptr, 0, path, false));
+    FK_TRY(check_h(h, d));
+    if (N < 2) return set_error(FK_ERR_INVALID_ARG, "leave-one-out needs N >= 2");
+    if (!loglik) return set_error(FK_ERR_INVALID_ARG, "loglik is NULL");
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xp = nullptr, *wp = nullptr;
+    void *lp = nullptr, *ghp = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xp));
+    FK_TRY(sg.in(w, (size_t)N * ds, &wp));
+    FK_TRY(sg.out(loglik, 8, &lp));
+    FK_TRY(sg.out(grad_h, (size_t)d * 8, &ghp));
+    Arena plan;
+    loo_run(nullptr, xd, N, d, w, h, (double*)loglik, grad_h, path, plan, st);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    FK_TRY(loo_run(xp, xd, N, d, wp, h, (double*)lp, (double*)ghp, path, ar, st));
+    return sg.finish();
 }
 
 }  // extern "C"

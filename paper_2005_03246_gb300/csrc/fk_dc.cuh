@@ -84,6 +84,35 @@ __device__ __forceinline__ int64_t merge_path(Acc A, int64_t la, Acc B, int64_t 
     return lo;
 }
 
+// Warp-cooperative merge path over global memory: each step probes 32
+// candidate split points at once, so a search over R elements takes about
+// log_32(R) dependent round trips instead of log_2(R).  All 32 lanes must
+// call it; every lane returns the same value.
+__device__ __forceinline__ int64_t merge_path_warp(const uint32_t* __restrict__ A, int64_t la,
+                                                   const uint32_t* __restrict__ B, int64_t lb, int64_t q) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = q > lb ? q - lb : 0;
+    int64_t hi = q < la ? q : la;
+    // invariant: the answer p (smallest p with A[p] > B[q-1-p], or hi) lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t span = hi - lo;
+        const int64_t p = lo + (span * (lane + 1)) / 33;
+        const bool f = A[p] <= B[q - 1 - p];           // true below the answer
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        // last lane with f true -> the answer is above its probe
+        const int last = 31 - __clz((int)m);            // -1 when m == 0
+        const int64_t nlo = (m == 0u) ? lo : lo + (span * (last + 1)) / 33 + 1;
+        const int64_t nhi = (m == 0xffffffffu) ? hi : lo + (span * (last + 2)) / 33;
+        lo = nlo;
+        hi = nhi;
+    }
+    // final range of at most 32 candidates: one probe per lane
+    const int64_t p = lo + lane;
+    const bool f = (p < hi) && (A[p] <= B[q - 1 - p]);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    return lo + __popc(m);
+}
+
 struct GAcc {
     const uint32_t* p;
     __device__ uint32_t operator()(int64_t i) const { return p[i]; }
@@ -176,7 +205,7 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     constexpr uint32_t CMASK = (1u << CLSB) - 1u;
     __shared__ uint32_t s_key[MTILE];
     __shared__ uint32_t s_meta[MTILE];
-    __shared__ int64_t s_co[4];
+    __shared__ int64_t s_co[6];
     __shared__ V s_scan[(PHASE == PH_PLAIN) ? 1 : 2 * NCH * (MT / 32)];
 
     const int64_t n = a.n;
@@ -189,18 +218,23 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     const bool big = R2 > MTILE;
     int64_t lc = 0;                              // big: local length of the C part
     if (big) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 64) {
             const int64_t bs = (o0 / R2) * R2;
             const int64_t cl = min(R, n - bs);
             const int64_t dl = max((int64_t)0, min(R2, n - bs) - cl);
-            GAcc A{a.key_in + bs}, B{a.key_in + bs + cl};
             const int64_t q0 = o0 - bs, q1 = o1 - bs;
-            const int64_t i0 = merge_path(A, cl, B, dl, q0);
-            const int64_t i1 = merge_path(A, cl, B, dl, q1);
-            s_co[0] = bs + i0;                 // C range [bs+i0, bs+i1)
-            s_co[1] = i1 - i0;
-            s_co[2] = bs + cl + (q0 - i0);     // D range start
-            s_co[3] = (q1 - i1) - (q0 - i0);
+            const int64_t iq = merge_path_warp(a.key_in + bs, cl, a.key_in + bs + cl, dl,
+                                               threadIdx.x < 32 ? q0 : q1);
+            if (threadIdx.x == 0) { s_co[0] = bs + iq; s_co[2] = bs + cl + (q0 - iq); s_co[4] = iq; }
+            if (threadIdx.x == 32) s_co[5] = iq;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int64_t i0 = s_co[4], i1 = s_co[5];
+            const int64_t bs = (o0 / R2) * R2;
+            const int64_t q0 = o0 - bs, q1 = o1 - bs;
+            s_co[1] = i1 - i0;                 // C range [bs+i0, bs+i1)
+            s_co[3] = (q1 - i1) - (q0 - i0);   // D range length
         }
         __syncthreads();
         lc = s_co[1];

@@ -246,6 +246,11 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
     const size_t asz = kind == 0 ? 4 : 8;
     Positions pos;
     FK_TRY(plan_positions(x, z, xd, N, n, d, d_eff, pos, ar, st));
+    if (kind == 0) {
+        // counts: exact inclusion-exclusion over single-orthant dominance counts
+        if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
+        return dom_orthant_counts(d, n, N, N, n_tgt, pos.P, mask, (int64_t*)out, ar, st);
+    }
     void* acc = ar.take<char>((size_t)(1 << d_eff) * n_tgt * asz);
     void* wts = (kind == 0) ? nullptr : ar.take<char>((size_t)N * 8);
     // the sweep plans its own buffers
@@ -291,7 +296,8 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
 // ------------------------------------------------------------------ kernel sums
 fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                         const double* h, unsigned flags, int nw, double* out, double* terms, fk_path path,
-                        Arena& ar, cudaStream_t st) {
+                        Arena& ar, cudaStream_t st, fk_dtype wd) {
+    if ((int)wd < 0) wd = xd;
     const int d_eff = d < 2 ? 2 : d;
     const bool sample = (z == nullptr);
     const bool loo = sample && (flags & FK_LOO);
@@ -343,7 +349,7 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
     FK_LAUNCH_CHECK();
     if (w) {
         const unsigned gw = grid_for(N, 256);
-        if (xd == FK_F32) {
+        if (wd == FK_F32) {
             if (fp64) k_convert<float, double><<<gw, 256, 0, st>>>((const float*)w, N, (double*)wts);
             else k_convert<float, float><<<gw, 256, 0, st>>>((const float*)w, N, (float*)wts);
         } else {

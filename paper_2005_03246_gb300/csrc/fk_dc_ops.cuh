@@ -36,12 +36,18 @@ FK_DC_SWEEP_DECL(sweep_kd2, PolKD<2>)
 
 }  // namespace dc
 
+// Exact orthant counts by inclusion-exclusion over dominance counts (fk_dom.cu).
+fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, int64_t n_tgt,
+                             const uint32_t* const* P, const uint32_t* mask, int64_t* out, Arena& ar,
+                             cudaStream_t st);
+
 // Operations (fk_dc_common.cu).  All pointers are device pointers.
 fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,
                          int64_t M, const uint32_t* mask, void* out, fk_path path, Arena& ar,
                          cudaStream_t st);
+// `wd` is the dtype of w (default: that of x).
 fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
                         int64_t M, const double* h, unsigned flags, int nw, double* out, double* terms,
-                        fk_path path, Arena& ar, cudaStream_t st);
+                        fk_path path, Arena& ar, cudaStream_t st, fk_dtype wd = (fk_dtype)-1);
 
 }  // namespace fk

@@ -1,0 +1,675 @@
+// fk_dom.cu -- exact orthant counts at the sample points by inclusion-exclusion
+// over single-orthant dominance counts.
+//
+// With y == 1 every orthant sum is an integer count, so the 2^d orthants of
+// eq. (ECDFdelta) follow exactly from the "<= on every axis of A" counts
+//     C_A(t) = #{ sources s : x_k(s) <= z_k(t) for all k in A },  A subset of axes,
+// by inclusion-exclusion: with pos(o) the axes tested with <= and neg(o) those
+// tested with >,  S_o(t) = sum_{T subset neg(o)} (-1)^{|T|} C_{pos(o) u T}(t),
+// and C_{} = N.  |A| = 1 is a rank count; |A| >= 2 is the dominance problem of
+// Sec. 2.2 (Algorithms 2-5) in |A| dimensions, needing only the sources that
+// lie below the target on every axis (a single channel, forward only).
+//
+// The dominance engine is the same nested merge-sort formulation as fk_dc.cuh
+// but carries, with every item, the number of "active" sources before it in
+// its current run (pref) and the count it has received so far (acc).  At a
+// merge of runs C and D, an element at merged position p has i(p) elements of
+// C and j(p) of D before it, so its new prefix is pref_C[i] + pref_D[j], and a
+// target from D receives pref_C[i] -- both lookups, no scan.  Active sources
+// are sources on the lower side of every enclosing axis (class 0); receiving
+// targets are targets on the upper side of every enclosing axis (class all
+// ones) and in D.
+#include "fk_dc_ops.cuh"
+
+namespace fk {
+namespace dom {
+
+using dc::kItemBits;
+using dc::kItemMask;
+using dc::merge_path;
+using dc::SAcc;
+using dc::GAcc;
+using dc::ClassSpecK;
+using dc::class_of_k;
+
+// Shared-memory index padding: one spare word per 32 makes the stride-8 access
+// pattern of "each thread owns 8 consecutive outputs" free of bank conflicts.
+__device__ __forceinline__ int pd(int p) { return p + (p >> 5); }
+struct SAccP {
+    const uint32_t* p;
+    int base;
+    __device__ uint32_t operator()(int64_t i) const { return p[pd(base + (int)i)]; }
+};
+
+struct Items {
+    int64_t n_src, tgt_off, n_tgt;
+    uint32_t full;      // class value of a receiving target (all enclosing bits set)
+    __device__ __forceinline__ bool src_active(uint32_t meta) const {
+        return (int64_t)(meta & kItemMask) < n_src && (meta >> kItemBits) == 0u;
+    }
+    __device__ __forceinline__ bool tgt_active(uint32_t meta) const {
+        const int64_t it = (int64_t)(meta & kItemMask);
+        return it >= tgt_off && it < tgt_off + n_tgt && (meta >> kItemBits) == full;
+    }
+};
+
+constexpr int LT = 2048;          // tile-local items
+constexpr int LNT = 256;          // threads
+constexpr int LIT = LT / LNT;     // items per thread
+
+// Tile-local merge levels.  Input: the enclosing state (items sorted by the
+// tree axis inside their nodes); output (if more levels follow): key, meta,
+// pref, acc in merged order; otherwise the received counts are flushed.
+__global__ void __launch_bounds__(LNT) k_dom_local(const uint32_t* __restrict__ seq, int64_t n,
+                                                   const uint32_t* __restrict__ P0, ClassSpecK cs, int levels,
+                                                   Items im, uint32_t* __restrict__ key_out,
+                                                   uint32_t* __restrict__ meta_out, uint32_t* __restrict__ pref_out,
+                                                   uint32_t* __restrict__ acc_out, int write_out,
+                                                   uint32_t* __restrict__ C) {
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    constexpr int LP = LT + LT / 32;   // padded row
+    uint32_t(*s_key)[LP] = reinterpret_cast<uint32_t(*)[LP]>(s_dyn);
+    uint32_t(*s_meta)[LP] = reinterpret_cast<uint32_t(*)[LP]>(s_dyn + 2 * LP);
+    uint32_t(*s_pref)[LP] = reinterpret_cast<uint32_t(*)[LP]>(s_dyn + 4 * LP);
+    uint32_t(*s_acc)[LP] = reinterpret_cast<uint32_t(*)[LP]>(s_dyn + 6 * LP);
+    const int64_t t0 = (int64_t)blockIdx.x * LT;
+    const int ln = (int)min((int64_t)LT, n - t0);
+    {
+        uint32_t it[LIT];
+#pragma unroll
+        for (int e = 0; e < LIT; ++e) {
+            const int i = threadIdx.x + e * LNT;
+            it[e] = (i < ln) ? seq[t0 + i] : 0u;
+        }
+        uint32_t kk[LIT], cc[LIT];
+#pragma unroll
+        for (int e = 0; e < LIT; ++e) {
+            const int i = threadIdx.x + e * LNT;
+            if (i < ln) { kk[e] = P0[it[e]]; cc[e] = class_of_k(cs, it[e]); }
+        }
+#pragma unroll
+        for (int e = 0; e < LIT; ++e) {
+            const int i = threadIdx.x + e * LNT;
+            if (i < ln) {
+                s_key[0][pd(i)] = kk[e];
+                s_meta[0][pd(i)] = it[e] | (cc[e] << kItemBits);
+                s_pref[0][pd(i)] = 0u;
+                s_acc[0][pd(i)] = 0u;
+            }
+        }
+    }
+    __syncthreads();
+    int b = 0;
+    for (int m = 0; m < levels; ++m) {
+        const int R = 1 << m, R2 = 2 << m;
+        const uint32_t* ik = s_key[b];
+        const uint32_t* imt = s_meta[b];
+        const uint32_t* ip = s_pref[b];
+        const uint32_t* ia = s_acc[b];
+        uint32_t ok[LIT], om[LIT], op[LIT], oa[LIT];
+        int cnt = 0;
+        const int p0 = threadIdx.x * LIT;
+        int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+        uint32_t ctot = 0, dtot = 0;
+#pragma unroll
+        for (int e = 0; e < LIT; ++e) {
+            const int p = p0 + e;
+            if (p < ln) {
+                if (e == 0 || (p % R2) == 0) {
+                    bsl = (p / R2) * R2;
+                    cl = min(R, ln - bsl);
+                    dl = min(R2, ln - bsl) - cl;
+                    SAccP A{ik, bsl}, B{ik, bsl + cl};
+                    i = (int)merge_path(A, cl, B, dl, p - bsl);
+                    j = (p - bsl) - i;
+                    ctot = ip[pd(bsl + cl - 1)] + (im.src_active(imt[pd(bsl + cl - 1)]) ? 1u : 0u);
+                    dtot = dl > 0 ? ip[pd(bsl + cl + dl - 1)] + (im.src_active(imt[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
+                }
+                const bool takeC = (i < cl) && (j >= dl || ik[pd(bsl + i)] <= ik[pd(bsl + cl + j)]);
+                if (takeC) {
+                    const int s = pd(bsl + i);
+                    const uint32_t other = (j < dl) ? ip[pd(bsl + cl + j)] : dtot;
+                    ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other; oa[e] = ia[s];
+                    ++i;
+                } else {
+                    const int s = pd(bsl + cl + j);
+                    const uint32_t other = (i < cl) ? ip[pd(bsl + i)] : ctot;
+                    ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other;
+                    oa[e] = ia[s] + (im.tgt_active(imt[s]) ? other : 0u);
+                    ++j;
+                }
+                cnt = e + 1;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < LIT; ++e) {
+            if (e < cnt) {
+                const int p = pd(p0 + e);
+                s_key[b ^ 1][p] = ok[e];
+                s_meta[b ^ 1][p] = om[e];
+                s_pref[b ^ 1][p] = op[e];
+                s_acc[b ^ 1][p] = oa[e];
+            }
+        }
+        __syncthreads();
+        b ^= 1;
+    }
+    for (int i = threadIdx.x; i < ln; i += LNT) {
+        const uint32_t m = s_meta[b][pd(i)];
+        if (write_out) {
+            key_out[t0 + i] = s_key[b][pd(i)];
+            meta_out[t0 + i] = m;
+            pref_out[t0 + i] = s_pref[b][pd(i)];
+            acc_out[t0 + i] = s_acc[b][pd(i)];
+        } else if (s_acc[b][pd(i)]) {
+            C[(int64_t)(m & kItemMask) - im.tgt_off] += s_acc[b][pd(i)];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ nested tile levels
+// For the outermost-but-one tree axis (axis index 2 of the subset): every
+// outer level l whose nodes (2^{l+1} items) fit in a tile of NTT items is done
+// inside one CTA -- the outer merge by P_1 (the tree of Algorithm 3/4) and,
+// for each l, the complete inner dominance sort of that level -- with the
+// received counts summed per item in shared memory and flushed once.  The
+// side bit of axis 2 at level l is bit l of the item's slot in the tile
+// (tiles start at multiples of NTT inside the enclosing nodes).
+constexpr int NTT = 1024;          // items per tile
+constexpr int NTN = 256;           // threads
+constexpr int NTI = NTT / NTN;     // items per thread
+constexpr int NTP = NTT + NTT / 32; // padded row
+
+struct DomSmem {
+    uint32_t* key;     // [2][NTT]
+    uint32_t* meta;    // [2][NTT]  slot | class << 16
+    uint32_t* pref;    // [2][NTT]
+    uint32_t* acc;     // [2][NTT]
+};
+
+// One merge level (runs 2^m -> 2^{m+1}) of the propagated-prefix dominance
+// merge on shared-memory state.  Activity of an element is decided from its
+// slot and class bits through the two predicates.
+template <class SrcF, class TgtF>
+__device__ __forceinline__ void dom_level_smem(DomSmem S, int b, int ln, int m, SrcF src_active, TgtF tgt_active) {
+    const int R = 1 << m, R2 = 2 << m;
+    const uint32_t* ik = S.key + b * NTP;
+    const uint32_t* imt = S.meta + b * NTP;
+    const uint32_t* ip = S.pref + b * NTP;
+    const uint32_t* ia = S.acc + b * NTP;
+    uint32_t ok[NTI], om[NTI], op[NTI], oa[NTI];
+    int cnt = 0;
+    const int p0 = threadIdx.x * NTI;
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+    uint32_t ctot = 0, dtot = 0;
+#pragma unroll
+    for (int e = 0; e < NTI; ++e) {
+        const int p = p0 + e;
+        if (p < ln) {
+            if (e == 0 || (p % R2) == 0) {
+                bsl = (p / R2) * R2;
+                cl = min(R, ln - bsl);
+                dl = min(R2, ln - bsl) - cl;
+                SAccP A{ik, bsl}, B{ik, bsl + cl};
+                i = (int)merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+                ctot = ip[pd(bsl + cl - 1)] + (src_active(imt[pd(bsl + cl - 1)]) ? 1u : 0u);
+                dtot = dl > 0 ? ip[pd(bsl + cl + dl - 1)] + (src_active(imt[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
+            }
+            const bool takeC = (i < cl) && (j >= dl || ik[pd(bsl + i)] <= ik[pd(bsl + cl + j)]);
+            if (takeC) {
+                const int s = pd(bsl + i);
+                const uint32_t other = (j < dl) ? ip[pd(bsl + cl + j)] : dtot;
+                ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other; oa[e] = ia[s];
+                ++i;
+            } else {
+                const int s = pd(bsl + cl + j);
+                const uint32_t other = (i < cl) ? ip[pd(bsl + i)] : ctot;
+                ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other;
+                oa[e] = ia[s] + (tgt_active(imt[s]) ? other : 0u);
+                ++j;
+            }
+            cnt = e + 1;
+        }
+    }
+    uint32_t* wk = S.key + (b ^ 1) * NTP;
+    uint32_t* wm = S.meta + (b ^ 1) * NTP;
+    uint32_t* wp = S.pref + (b ^ 1) * NTP;
+    uint32_t* wa = S.acc + (b ^ 1) * NTP;
+#pragma unroll
+    for (int e = 0; e < NTI; ++e) {
+        if (e < cnt) {
+            const int p = pd(p0 + e);
+            wk[p] = ok[e]; wm[p] = om[e]; wp[p] = op[e]; wa[p] = oa[e];
+        }
+    }
+}
+
+// Plain merge level on (key, slot) pairs in shared memory.
+__device__ __forceinline__ void plain_level_smem(const uint32_t* ik, const uint32_t* ih, uint32_t* wk, uint32_t* wh,
+                                                 int ln, int m) {
+    const int R = 1 << m, R2 = 2 << m;
+    uint32_t ok[NTI], oh[NTI];
+    int cnt = 0;
+    const int p0 = threadIdx.x * NTI;
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+#pragma unroll
+    for (int e = 0; e < NTI; ++e) {
+        const int p = p0 + e;
+        if (p < ln) {
+            if (e == 0 || (p % R2) == 0) {
+                bsl = (p / R2) * R2;
+                cl = min(R, ln - bsl);
+                dl = min(R2, ln - bsl) - cl;
+                SAccP A{ik, bsl}, B{ik, bsl + cl};
+                i = (int)merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+            }
+            const bool takeC = (i < cl) && (j >= dl || ik[pd(bsl + i)] <= ik[pd(bsl + cl + j)]);
+            const int s = takeC ? pd(bsl + i) : pd(bsl + cl + j);
+            ok[e] = ik[s];
+            oh[e] = ih[s];
+            if (takeC) ++i; else ++j;
+            cnt = e + 1;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < NTI; ++e)
+        if (e < cnt) { wk[pd(p0 + e)] = ok[e]; wh[pd(p0 + e)] = oh[e]; }
+}
+
+__global__ void __launch_bounds__(NTN) k_dom_nested(const uint32_t* __restrict__ seq, int64_t n,
+                                                    const uint32_t* __restrict__ P0, const uint32_t* __restrict__ P1,
+                                                    ClassSpecK cs, int levels, Items im,
+                                                    uint32_t* __restrict__ okey_out, uint32_t* __restrict__ oitem_out,
+                                                    uint32_t* __restrict__ C) {
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    uint32_t* s_item = s_dyn;                 // [NTT] items of the tile (slot -> item)
+    uint32_t* s_p0 = s_item + NTT;            // [NTT] P_0 by slot
+    uint32_t* s_cenc = s_p0 + NTT;            // [NTT] enclosing class bits by slot (bits >= 1)
+    uint32_t* s_sum = s_cenc + NTT;           // [NTT] received counts by slot
+    uint32_t* s_okey = s_sum + NTT;           // [2][NTP] outer state: P_1 (padded positions)
+    uint32_t* s_oslot = s_okey + 2 * NTP;     // [2][NTP] outer state: slot
+    DomSmem S{s_oslot + 2 * NTP, s_oslot + 4 * NTP, s_oslot + 6 * NTP, s_oslot + 8 * NTP};
+    const int64_t t0 = (int64_t)blockIdx.x * NTT;
+    const int ln = (int)min((int64_t)NTT, n - t0);
+    {
+        uint32_t it[NTI];
+#pragma unroll
+        for (int e = 0; e < NTI; ++e) {
+            const int i = threadIdx.x + e * NTN;
+            it[e] = (i < ln) ? seq[t0 + i] : 0u;
+        }
+        uint32_t a0[NTI], a1[NTI], ce[NTI];
+#pragma unroll
+        for (int e = 0; e < NTI; ++e) {
+            const int i = threadIdx.x + e * NTN;
+            if (i < ln) {
+                a0[e] = P0[it[e]];
+                a1[e] = P1[it[e]];
+                uint32_t c = 0;
+                for (int q = 1; q < cs.nb; ++q) c |= ((cs.idx[q][it[e]] >> cs.lvl[q]) & 1u) << q;
+                ce[e] = c;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < NTI; ++e) {
+            const int i = threadIdx.x + e * NTN;
+            if (i < ln) {
+                s_item[i] = it[e]; s_p0[i] = a0[e]; s_cenc[i] = ce[e]; s_sum[i] = 0u;
+                s_okey[pd(i)] = a1[e]; s_oslot[pd(i)] = (uint32_t)i;
+            }
+        }
+    }
+    __syncthreads();
+    const int nbt = cs.nb > 1 ? cs.nb : 1;
+    const uint32_t full = (1u << nbt) - 1u;
+    auto src_active = [&](uint32_t mt) {
+        const uint32_t slot = mt & 0xffffu;
+        return (int64_t)s_item[slot] < im.n_src && (mt >> 16) == 0u;
+    };
+    auto tgt_active = [&](uint32_t mt) {
+        const int64_t it = (int64_t)s_item[mt & 0xffffu];
+        return it >= im.tgt_off && it < im.tgt_off + im.n_tgt && (mt >> 16) == full;
+    };
+    int ob = 0;
+    for (int l = 0; l < levels; ++l) {
+        plain_level_smem(s_okey + ob * NTP, s_oslot + ob * NTP, s_okey + (ob ^ 1) * NTP, s_oslot + (ob ^ 1) * NTP, ln, l);
+        __syncthreads();
+        ob ^= 1;
+        // inner sort of level l: nodes of 2^{l+1} sorted by P_1, merged by P_0
+        for (int p = threadIdx.x; p < ln; p += NTN) {
+            const uint32_t sl = s_oslot[ob * NTP + pd(p)];
+            const uint32_t cls = ((sl >> l) & 1u) | s_cenc[sl];
+            S.key[pd(p)] = s_p0[sl];
+            S.meta[pd(p)] = sl | (cls << 16);
+            S.pref[pd(p)] = 0u;
+            S.acc[pd(p)] = 0u;
+        }
+        __syncthreads();
+        int b = 0;
+        for (int m = 0; m <= l; ++m) {
+            dom_level_smem(S, b, ln, m, src_active, tgt_active);
+            __syncthreads();
+            b ^= 1;
+        }
+        for (int p = threadIdx.x; p < ln; p += NTN) {
+            const uint32_t a = S.acc[b * NTP + pd(p)];
+            if (a) s_sum[S.meta[b * NTP + pd(p)] & 0xffffu] += a;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ln; i += NTN) {
+        okey_out[t0 + i] = s_okey[ob * NTP + pd(i)];
+        oitem_out[t0 + i] = s_item[s_oslot[ob * NTP + pd(i)]];
+        const uint32_t a = s_sum[i];
+        if (a) C[(int64_t)s_item[i] - im.tgt_off] += a;
+    }
+}
+
+constexpr int GT = 256, GI = 8, GTILE = GT * GI;
+
+// One global merge level with propagated prefixes.  The last level flushes
+// the received counts instead of writing the state.
+__global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ key_in, const uint32_t* __restrict__ meta_in,
+                                                  const uint32_t* __restrict__ pref_in, const uint32_t* __restrict__ acc_in,
+                                                  uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
+                                                  uint32_t* __restrict__ pref_out, uint32_t* __restrict__ acc_out,
+                                                  int64_t n, int logR, Items im, int last, uint32_t* __restrict__ C) {
+    constexpr int GP = GTILE + GTILE / 32 + 2;   // padded tile
+    __shared__ uint32_t s_key[GP], s_meta[GP], s_pref[GP], s_acc[GP];
+    __shared__ int64_t s_co[6];
+    const int64_t R = (int64_t)1 << logR, R2 = R << 1;
+    const int64_t o0 = (int64_t)blockIdx.x * GTILE;
+    if (o0 >= n) return;
+    const int64_t o1 = min(o0 + (int64_t)GTILE, n);
+    const int ln = (int)(o1 - o0);
+    // Runs are at least one tile long here (R2 > GTILE is not required: when a
+    // tile holds several merged blocks each block is handled from smem).
+    const bool big = R2 > GTILE;
+    int lc = 0, ldd = 0;
+    uint32_t ctot = 0, dtot = 0, cnext = 0, dnext = 0;
+    if (big) {
+        if (threadIdx.x < 64) {
+            const int64_t bs = (o0 / R2) * R2;
+            const int64_t cl = min(R, n - bs);
+            const int64_t dl = max((int64_t)0, min(R2, n - bs) - cl);
+            const int64_t q0 = o0 - bs, q1 = o1 - bs;
+            const int64_t iq = dc::merge_path_warp(key_in + bs, cl, key_in + bs + cl, dl, threadIdx.x < 32 ? q0 : q1);
+            if (threadIdx.x == 0) s_co[0] = iq;
+            if (threadIdx.x == 32) s_co[1] = iq;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int64_t bs = (o0 / R2) * R2;
+            const int64_t cl = min(R, n - bs);
+            const int64_t dl = max((int64_t)0, min(R2, n - bs) - cl);
+            const int64_t q0 = o0 - bs, q1 = o1 - bs;
+            const int64_t i0 = s_co[0], i1 = s_co[1];
+            s_co[0] = bs + i0;
+            s_co[1] = i1 - i0;
+            s_co[2] = bs + cl + (q0 - i0);
+            s_co[3] = (q1 - i1) - (q0 - i0);
+            // prefix just past each loaded range (the next element's, or the run total)
+            const int64_t cend = bs + i1, dend = bs + cl + (q1 - i1);
+            const uint32_t ct = pref_in[bs + cl - 1] + (im.src_active(meta_in[bs + cl - 1]) ? 1u : 0u);
+            const uint32_t dt = dl > 0 ? pref_in[bs + cl + dl - 1] + (im.src_active(meta_in[bs + cl + dl - 1]) ? 1u : 0u) : 0u;
+            s_co[4] = (cend < bs + cl) ? pref_in[cend] : ct;
+            s_co[5] = (dend < bs + cl + dl) ? pref_in[dend] : dt;
+        }
+        __syncthreads();
+        lc = (int)s_co[1];
+        ldd = (int)s_co[3];
+        cnext = (uint32_t)s_co[4];
+        dnext = (uint32_t)s_co[5];
+        const int64_t cs = s_co[0], ds = s_co[2];
+        for (int i = threadIdx.x; i < lc; i += GT) {
+            const int q = pd(i);
+            s_key[q] = key_in[cs + i]; s_meta[q] = meta_in[cs + i]; s_pref[q] = pref_in[cs + i]; s_acc[q] = acc_in[cs + i];
+        }
+        for (int i = threadIdx.x; i < ldd; i += GT) {
+            const int q = pd(lc + i);
+            s_key[q] = key_in[ds + i]; s_meta[q] = meta_in[ds + i];
+            s_pref[q] = pref_in[ds + i]; s_acc[q] = acc_in[ds + i];
+        }
+    } else {
+        for (int i = threadIdx.x; i < ln; i += GT) {
+            const int q = pd(i);
+            s_key[q] = key_in[o0 + i]; s_meta[q] = meta_in[o0 + i]; s_pref[q] = pref_in[o0 + i]; s_acc[q] = acc_in[o0 + i];
+        }
+    }
+    __syncthreads();
+    const int p0 = threadIdx.x * GI;
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+    for (int e = 0; e < GI; ++e) {
+        const int p = p0 + e;
+        if (p >= ln) break;
+        if (e == 0 || (!big && (p % (int)R2) == 0)) {
+            if (big) {
+                bsl = 0; cl = lc; dl = ldd;
+                ctot = cnext; dtot = dnext;
+            } else {
+                bsl = (int)((p / R2) * R2);
+                cl = (int)min(R, (int64_t)(ln - bsl));
+                dl = (int)min(R2, (int64_t)(ln - bsl)) - cl;
+                ctot = s_pref[pd(bsl + cl - 1)] + (im.src_active(s_meta[pd(bsl + cl - 1)]) ? 1u : 0u);
+                dtot = dl > 0 ? s_pref[pd(bsl + cl + dl - 1)] + (im.src_active(s_meta[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
+            }
+            SAccP A{s_key, bsl}, B{s_key, bsl + cl};
+            i = (int)merge_path(A, cl, B, dl, p - bsl);
+            j = (p - bsl) - i;
+        }
+        const bool takeC = (i < cl) && (j >= dl || s_key[pd(bsl + i)] <= s_key[pd(bsl + cl + j)]);
+        uint32_t k, mt, pf, ac;
+        if (takeC) {
+            const int s = pd(bsl + i);
+            const uint32_t other = (j < dl) ? s_pref[pd(bsl + cl + j)] : dtot;
+            k = s_key[s]; mt = s_meta[s]; pf = s_pref[s] + other; ac = s_acc[s];
+            ++i;
+        } else {
+            const int s = pd(bsl + cl + j);
+            const uint32_t other = (i < cl) ? s_pref[pd(bsl + i)] : ctot;
+            k = s_key[s]; mt = s_meta[s]; pf = s_pref[s] + other;
+            ac = s_acc[s] + (im.tgt_active(mt) ? other : 0u);
+            ++j;
+        }
+        const int64_t o = o0 + p;
+        if (last) {
+            if (ac) C[(int64_t)(mt & kItemMask) - im.tgt_off] += ac;
+        } else {
+            key_out[o] = k; meta_out[o] = mt; pref_out[o] = pf; acc_out[o] = ac;
+        }
+    }
+}
+
+// rank counts: C_k(t) = number of sources before target t in the axis-k order
+__global__ void k_src_flags(const uint32_t* __restrict__ P, int64_t n, int64_t n_src, uint32_t* __restrict__ f) {
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it < n) f[P[it]] = (it < n_src) ? 1u : 0u;
+}
+__global__ void k_rank_counts(const uint32_t* __restrict__ P, const uint32_t* __restrict__ scanned, int64_t tgt_off,
+                              int64_t n_tgt, uint32_t* __restrict__ C) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tgt) C[t] = scanned[P[tgt_off + t]];
+}
+__global__ void k_seq_from_pos(const uint32_t* __restrict__ P, int64_t n, uint32_t* __restrict__ seq) {
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it < n) seq[P[it]] = (uint32_t)it;
+}
+
+struct CTab { const uint32_t* c[16]; };   // C_A for every subset A of the d axes (A as a bitmask)
+
+// Orthant o: sum over subsets T of neg(o) of (-1)^|T| C_{pos(o) | T}.
+__global__ void k_combine(CTab ct, int d, int64_t n_tgt, uint32_t n_src, dc::SelMap sel, int64_t* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tgt) return;
+    const uint32_t full = (1u << d) - 1u;
+    for (int r = 0; r < sel.n; ++r) {
+        const uint32_t o = (uint32_t)sel.o[r];
+        const uint32_t pos = full & ~o, neg = o;
+        int64_t s = 0;
+        // enumerate the subsets T of neg
+        uint32_t T = 0;
+        while (true) {
+            const uint32_t A = pos | T;
+            const int64_t v = (A == 0) ? (int64_t)n_src : (int64_t)ct.c[A][t];
+            s += (__popc(T) & 1) ? -v : v;
+            if (T == neg) break;
+            T = (T - neg) & neg;
+        }
+        out[(int64_t)r * n_tgt + t] = s;
+    }
+}
+
+}  // namespace dom
+
+using namespace dom;
+
+// Dominance count C_A for the axes in `axes` (sorted, size k >= 2): the
+// innermost merge sort over the second axis by the first, nested inside merge
+// sorts of the outer axes, as in fk_dc_drv.cuh.
+struct DomBuf {
+    uint32_t* k[2];
+    uint32_t* m[2];
+    uint32_t* p[2];
+    uint32_t* a[2];
+    uint32_t* ok[8][2];
+    uint32_t* om[8][2];
+    uint32_t* idx[8];
+};
+
+static fk_status dom_inner(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, ClassSpecK cs, Items im,
+                           DomBuf& B, uint32_t* C, cudaStream_t st) {
+    int lt = 0;
+    while ((1 << (lt + 1)) <= LT) ++lt;
+    const int L0 = E < lt ? E : lt;
+    {
+        ProfScope ps(PF_LOCAL, 8.0 * n + 8.0 * n * (E > L0 ? 2 : 0) + 8.0 * im.n_tgt, st);
+        constexpr int smem = 8 * (LT + LT / 32) * 4;
+        static bool attr = false;
+        if (!attr) {
+            FK_CUDA(cudaFuncSetAttribute(k_dom_local, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr = true;
+        }
+        k_dom_local<<<grid_for(n, LT), LNT, smem, st>>>(seq, n, P0, cs, L0, im, B.k[0], B.m[0], B.p[0], B.a[0],
+                                                        E > L0 ? 1 : 0, C);
+        FK_LAUNCH_CHECK();
+    }
+    int cur = 0;
+    for (int m = L0; m < E; ++m) {
+        const int last = (m == E - 1);
+        ProfScope ps(PF_MERGE_SWEEP, 16.0 * n + (last ? 8.0 * im.n_tgt : 16.0 * n), st);
+        k_dom_merge<<<grid_for(n, GTILE), GT, 0, st>>>(B.k[cur], B.m[cur], B.p[cur], B.a[cur], B.k[cur ^ 1],
+                                                       B.m[cur ^ 1], B.p[cur ^ 1], B.a[cur ^ 1], n, m, im, last, C);
+        FK_LAUNCH_CHECK();
+        cur ^= 1;
+    }
+    return FK_OK;
+}
+
+static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* const* P, ClassSpecK cs,
+                             Items im, DomBuf& B, uint32_t* C, cudaStream_t st) {
+    if (k == 1) {
+        Items it = im;
+        it.full = (1u << cs.nb) - 1u;
+        return dom_inner(seq, n, E, P[0], cs, it, B, C, st);
+    }
+    const uint32_t* idx = P[k];
+    if (B.idx[k]) {
+        FK_TRY(dc::record_index(seq, n, E, B.idx[k], st));
+        idx = B.idx[k];
+    }
+    int cur = 0;
+    int l0 = 0;
+    if (k == 2) {
+        // outer levels whose nodes fit in a tile: one nested launch
+        int lt = 0;
+        while ((1 << (lt + 1)) <= NTT) ++lt;
+        l0 = E < lt ? E : lt;
+        constexpr int smem = 4 * NTT * 4 + 4 * NTP * 4 + 8 * NTP * 4;
+        static bool attr = false;
+        if (!attr) {
+            FK_CUDA(cudaFuncSetAttribute(k_dom_nested, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr = true;
+        }
+        ProfScope ps(PF_LOCAL, 16.0 * n + 8.0 * im.n_tgt, st);
+        k_dom_nested<<<grid_for(n, NTT), NTN, smem, st>>>(seq, n, P[0], P[1], cs, l0, im, B.ok[k][0], B.om[k][0], C);
+        FK_LAUNCH_CHECK();
+    } else {
+        FK_TRY(dc::gather_outer(seq, n, P[k - 1], B.ok[k][0], B.om[k][0], st));
+    }
+    for (int l = l0; l < E; ++l) {
+        dc::MergeArgs a{B.ok[k][cur], B.om[k][cur], B.ok[k][cur ^ 1], B.om[k][cur ^ 1], n, l};
+        FK_TRY(dc::plain_merge_level(a, st));
+        cur ^= 1;
+        ClassSpecK c2 = cs;
+        c2.idx[k - 2] = idx;
+        c2.lvl[k - 2] = l;
+        if (c2.nb < k - 1) c2.nb = k - 1;
+        FK_TRY(dom_recurse(k - 1, B.om[k][cur], n, l + 1, P, c2, im, B, C, st));
+    }
+    return FK_OK;
+}
+
+// Orthant counts of N sources at the targets from the positions P[0..d-1]
+// (sources before targets on ties), by inclusion-exclusion.
+fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, int64_t n_tgt,
+                             const uint32_t* const* P, const uint32_t* mask, int64_t* out, Arena& ar,
+                             cudaStream_t st) {
+    const int nsub = 1 << d;
+    uint32_t* Cs[16] = {};
+    for (int A = 1; A < nsub; ++A) Cs[A] = ar.take<uint32_t>((size_t)n_tgt);
+    DomBuf B = {};
+    for (int q = 0; q < 2; ++q) {
+        B.k[q] = ar.take<uint32_t>(n); B.m[q] = ar.take<uint32_t>(n);
+        B.p[q] = ar.take<uint32_t>(n); B.a[q] = ar.take<uint32_t>(n);
+    }
+    for (int k = 2; k < d; ++k) {
+        for (int q = 0; q < 2; ++q) { B.ok[k][q] = ar.take<uint32_t>(n); B.om[k][q] = ar.take<uint32_t>(n); }
+        B.idx[k] = ar.take<uint32_t>(n);
+    }
+    uint32_t* flags = ar.take<uint32_t>(n);
+    uint32_t* scanned = ar.take<uint32_t>(n);
+    uint32_t* stmp = ar.take<uint32_t>(scan_u32_tmp_words(n));
+    uint32_t* seq = ar.take<uint32_t>(n);
+    if (ar.sizing) return FK_OK;
+    if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
+    for (int A = 1; A < nsub; ++A) FK_CUDA(cudaMemsetAsync(Cs[A], 0, (size_t)n_tgt * 4, st));
+    const unsigned g = grid_for(n, 256);
+    Items im{n_src, tgt_off, n_tgt, 0u};
+    for (int A = 1; A < nsub; ++A) {
+        const int k = __builtin_popcount((unsigned)A);
+        const uint32_t* PA[8];
+        int q = 0;
+        for (int a = 0; a < d; ++a)
+            if ((A >> a) & 1) PA[q++] = P[a];
+        if (k == 1) {
+            k_src_flags<<<g, 256, 0, st>>>(PA[0], n, n_src, flags);
+            FK_LAUNCH_CHECK();
+            FK_TRY(scan_u32_exclusive(flags, scanned, n, stmp, st));
+            k_rank_counts<<<grid_for(n_tgt, 256), 256, 0, st>>>(PA[0], scanned, tgt_off, n_tgt, Cs[A]);
+            FK_LAUNCH_CHECK();
+            continue;
+        }
+        // items in the order of the outermost axis of A
+        k_seq_from_pos<<<g, 256, 0, st>>>(PA[k - 1], n, seq);
+        FK_LAUNCH_CHECK();
+        DomBuf BB = B;
+        for (int kk = 2; kk < 8; ++kk) BB.idx[kk] = (kk < k - 1) ? B.idx[kk] : nullptr;
+        ClassSpecK cs = {};
+        FK_TRY(dom_recurse(k - 1, seq, n, dc::ceil_log2(n), PA, cs, im, BB, Cs[A], st));
+    }
+    dc::SelMap sel;
+    sel.n = 0;
+    for (int o = 0; o < nsub; ++o)
+        if (!mask || ((mask[o >> 5] >> (o & 31)) & 1u)) sel.o[sel.n++] = o;
+    if (sel.n == 0 || n_tgt == 0) return FK_OK;
+    CTab ct = {};
+    for (int A = 1; A < nsub; ++A) ct.c[A] = Cs[A];
+    k_combine<<<grid_for(n_tgt, 256), 256, 0, st>>>(ct, d, n_tgt, (uint32_t)n_src, sel, out);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
+}  // namespace fk
