@@ -200,6 +200,39 @@ fk_status fk_loo_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const
                          fk_stream_t stream);
 
 /*
+ * ---------------------------------------------------------------- batching
+ * fk_batched -- many independent datasets of uneven size and dimension in one
+ * call (not in the paper, which treats one dataset).  Dataset b has N_b points
+ * x_b [N_b][d_b] (1 <= d_b <= 4) and optional weights y_b [N_b], all DEVICE
+ * pointers in the dtype `xdtype`.
+ *   what & FK_BATCH_ECDF : all 2^d_b orthant counts of every dataset at its own
+ *                          sample points (as fk_ecdf_points with y == NULL);
+ *                          ecdf_out = concatenation over b of [2^d_b][N_b] int64.
+ *   what & FK_BATCH_KDE  : the Laplacian KDE of every dataset at its own sample
+ *                          points with bandwidth h on every axis and weights y_b
+ *                          (1 if NULL), as fk_kde_laplace; kde_out =
+ *                          concatenation over b of [N_b] double.
+ * Datasets are grouped by dimension and padded size; each group runs as one
+ * set of kernel launches covering all its datasets.  No host synchronisation;
+ * with a caller workspace the call can be captured in a CUDA graph.
+ */
+typedef struct {
+    const void* x;   /* [N][d] device */
+    const void* y;   /* [N] device or NULL */
+    int64_t N;
+    int d;
+    int reserved;
+} fk_dataset;
+
+#define FK_BATCH_ECDF 1u
+#define FK_BATCH_KDE 2u
+
+size_t fk_batched_workspace(const fk_dataset* sets, int count, fk_dtype xdtype, unsigned what, fk_path path);
+fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xdtype, unsigned what, double h,
+                     int64_t* ecdf_out, double* kde_out, fk_path path, void* ws, size_t ws_bytes,
+                     fk_stream_t stream);
+
+/*
  * fk_ecdf_grid_counts_noalloc -- the paper has no counterpart to this call; it
  * exists for callers that may not allocate device memory while they run: loops
  * that forbid allocation after start-up (cudaMalloc can synchronise the device

@@ -16,7 +16,7 @@ import numpy as np
 from . import _lib
 from ._lib import FastEcdfError
 
-__all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplace", "kde",
+__all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplace", "kde", "Batched",
            "kde_laplace_backward", "loo_laplace", "select_bandwidth_loo",
            "FastEcdfError", "mask_words"]
 
@@ -355,3 +355,81 @@ def select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, w=None, path="mixed", per_
         else:
             u = u + lr * float(np.sum(h * g))
     return hist
+
+
+# ----------------------------------------------------------------------------- batching
+
+
+class Batched:
+    """Many independent datasets in one call (fk_batched): all orthant counts at
+    each dataset's sample points and/or its Laplacian KDE (bandwidth h on every
+    axis, weights ys[b] or 1).
+
+    xs: list of CUDA tensors [N_b, d_b] of one dtype (1 <= d_b <= 4); ys: list of
+    [N_b] tensors or None.  With graph=True the call is captured once in a CUDA
+    graph and ``run()`` replays it (the input tensors must keep their storage).
+    ``run()`` returns (ecdf, kde): lists of per-dataset views [2^d_b, N_b] int64
+    and [N_b] float64 (None for the part not requested)."""
+
+    def __init__(self, xs, ys=None, h=0.1, ecdf=True, kde=True, path="mixed", graph=True):
+        torch = _torch()
+        lib = _lib.load()
+        if not xs:
+            raise ValueError("no datasets")
+        self.xs = [_prep_points(x) for x in xs]
+        dt = self.xs[0].dtype
+        dev = self.xs[0].device
+        if any(x.dtype != dt for x in self.xs):
+            raise TypeError("all datasets must share one dtype")
+        self.ys = [None if (ys is None or ys[b] is None) else _weights(ys[b], self.xs[b])
+                   for b in range(len(self.xs))]
+        self.what = (_lib.FK_BATCH_ECDF if ecdf else 0) | (_lib.FK_BATCH_KDE if kde else 0)
+        self.h = float(h)
+        self.path = _path_code(path)
+        self.dev = dev
+        n = len(self.xs)
+        self.sets = (_lib.Dataset * n)()
+        ne = nk = 0
+        self.shape_e, self.off_e, self.off_k = [], [], []
+        for b, x in enumerate(self.xs):
+            nb, d = x.shape
+            s = self.sets[b]
+            s.x = x.data_ptr() if nb else None
+            s.y = self.ys[b].data_ptr() if self.ys[b] is not None else None
+            s.N, s.d = nb, d
+            self.off_e.append(ne)
+            self.off_k.append(nk)
+            self.shape_e.append((1 << d, nb))
+            ne += (1 << d) * nb
+            nk += nb
+        self.ecdf_out = torch.empty(max(ne, 1), dtype=torch.int64, device=dev) if ecdf else None
+        self.kde_out = torch.empty(max(nk, 1), dtype=torch.float64, device=dev) if kde else None
+        self.dtype_code = _dtype_code(dt)
+        need = lib.fk_batched_workspace(self.sets, n, self.dtype_code, self.what, self.path)
+        self.ws, self.wsb = _workspace(need, dev)
+        self.graph = None
+        self._call()                         # warm-up (sets kernel attributes, checks errors)
+        torch.cuda.synchronize(dev)
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                self._call()
+            self.graph = g
+
+    def _call(self):
+        lib = _lib.load()
+        rc = lib.fk_batched(self.sets, len(self.xs), self.dtype_code, self.what, self.h, _ptr(self.ecdf_out),
+                            _ptr(self.kde_out), self.path, _ptr(self.ws), self.wsb, _stream_ptr(self.dev))
+        _lib.check(rc, "fk_batched")
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._call()
+        ecdf = kde = None
+        if self.ecdf_out is not None:
+            ecdf = [self.ecdf_out[o:o + a * b].view(a, b) for o, (a, b) in zip(self.off_e, self.shape_e)]
+        if self.kde_out is not None:
+            kde = [self.kde_out[o:o + x.shape[0]] for o, x in zip(self.off_k, self.xs)]
+        return ecdf, kde

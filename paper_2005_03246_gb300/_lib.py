@@ -13,6 +13,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfastecdf.so")
 FK_F32, FK_F64 = 0, 1
 FK_PATH_MIXED, FK_PATH_FP64 = 0, 1
 FK_LOO = 1
+FK_BATCH_ECDF, FK_BATCH_KDE = 1, 2
+
+
+class Dataset(ctypes.Structure):
+    """fk_dataset of include/fastecdf.h."""
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 STATUS = {0: "FK_OK", -1: "FK_ERR_INVALID_ARG", -2: "FK_ERR_UNSUPPORTED", -3: "FK_ERR_WORKSPACE",
           -4: "FK_ERR_NONFINITE", -5: "FK_ERR_CUDA", -6: "FK_ERR_TIMEOUT"}
@@ -36,6 +43,8 @@ SIGNATURES = {
     "fk_kde_laplace_backward": (I, [P, I, I64, I, P, P, I64, P, U, P, P, P, P, I, P, SZ, P]),
     "fk_loo_laplace_workspace": (SZ, [I64, I, I]),
     "fk_loo_laplace": (I, [P, I, I64, I, P, P, P, P, I, P, SZ, P]),
+    "fk_batched_workspace": (SZ, [P, I, I, U, I]),
+    "fk_batched": (I, [P, I, I, U, ctypes.c_double, P, P, I, P, SZ, P]),
     "fk_ecdf_grid_counts_noalloc": (I, [P, I, I64, I, P, P, P, P, P]),
     "fk_kernel_launches": (ctypes.c_uint64, []),
     "fk_profile_enable": (None, [I]),

@@ -17,6 +17,9 @@ fk_status kde_backward_run(const void* x, fk_dtype xd, int64_t N, int d, const v
 fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* h, double* L,
                   double* gh, fk_path path, Arena& ar, cudaStream_t st);
 
+fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
+                      double* kde_out, fk_path path, Arena& ar, cudaStream_t st);
+
 static thread_local char g_msg[512] = "no error";
 
 fk_status set_error(fk_status st, const char* fmt, ...) {
@@ -516,6 +519,48 @@ fk_status fk_loo_laplace(const void* x, fk_dtype xd, int64_t N, int d, const voi
     FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
     FK_TRY(loo_run(xp, xd, N, d, wp, h, (double*)lp, (double*)ghp, path, ar, st));
     return sg.finish();
+}
+
+// ------------------------------------------------------------------ batching
+static fk_status batched_validate(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path) {
+    if (count < 0 || (count > 0 && !sets)) return set_error(FK_ERR_INVALID_ARG, "bad dataset list");
+    if (xd != FK_F32 && xd != FK_F64) return set_error(FK_ERR_INVALID_ARG, "xdtype must be FK_F32 or FK_F64");
+    if (path != FK_PATH_MIXED && path != FK_PATH_FP64) return set_error(FK_ERR_INVALID_ARG, "unknown precision path");
+    if (!(what & (FK_BATCH_ECDF | FK_BATCH_KDE))) return set_error(FK_ERR_INVALID_ARG, "nothing requested");
+    for (int b = 0; b < count; ++b) {
+        if (sets[b].d < 1 || sets[b].d > 4) return set_error(FK_ERR_UNSUPPORTED, "dataset %d: d must be in [1, 4]", b);
+        if (sets[b].N < 0 || 2 * sets[b].N >= ((int64_t)1 << 25))
+            return set_error(FK_ERR_UNSUPPORTED, "dataset %d: N out of range", b);
+        if (sets[b].N > 0 && !sets[b].x) return set_error(FK_ERR_INVALID_ARG, "dataset %d: x is NULL", b);
+    }
+    return FK_OK;
+}
+
+size_t fk_batched_workspace(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path) {
+    if (batched_validate(sets, count, xd, what, path) != FK_OK) return 0;
+    Arena ar;
+    batched_run(sets, count, xd, what, 1.0, nullptr, nullptr, path, ar, 0);
+    return ar.used;
+}
+
+fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
+                     double* kde_out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(batched_validate(sets, count, xd, what, path));
+    if ((what & FK_BATCH_KDE) && !(h > 0.0 && h < 1e300)) return set_error(FK_ERR_INVALID_ARG, "h must be > 0");
+    if ((what & FK_BATCH_ECDF) && !ecdf_out) return set_error(FK_ERR_INVALID_ARG, "ecdf_out is NULL");
+    if ((what & FK_BATCH_KDE) && !kde_out) return set_error(FK_ERR_INVALID_ARG, "kde_out is NULL");
+    for (int b = 0; b < count; ++b)
+        if ((sets[b].x && !is_device_pointer(sets[b].x)) || (sets[b].y && !is_device_pointer(sets[b].y)))
+            return set_error(FK_ERR_INVALID_ARG, "fk_batched needs device pointers (dataset %d)", b);
+    if ((ecdf_out && !is_device_pointer(ecdf_out)) || (kde_out && !is_device_pointer(kde_out)))
+        return set_error(FK_ERR_INVALID_ARG, "fk_batched needs device output pointers");
+    Arena plan;
+    batched_run(sets, count, xd, what, h, nullptr, nullptr, path, plan, st);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    return batched_run(sets, count, xd, what, h, ecdf_out, kde_out, path, ar, st);
 }
 
 }  // extern "C"

@@ -171,6 +171,11 @@ fk_status gather_outer(const uint32_t* seq, int64_t n, const uint32_t* Pkey, uin
     FK_LAUNCH_CHECK();
     return FK_OK;
 }
+fk_status iota_u32(uint32_t* a, int64_t n, cudaStream_t st) {
+    k_iota<<<grid_for(n, 256), 256, 0, st>>>(a, n);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
 fk_status record_index(const uint32_t* seq, int64_t n, int E, uint32_t* idx, cudaStream_t st) {
     const uint32_t mask = (E >= 32) ? 0xffffffffu : ((1u << E) - 1u);
     k_record_index<<<grid_for(n, 256), 256, 0, st>>>(seq, n, mask, idx);

@@ -12,11 +12,29 @@ namespace dc {
 //   sample points, kernel sums  : items [0,N) are both (the self pair is added
 //                                 separately, or dropped for leave-one-out)
 //   explicit targets            : items [0,N) sources, [N,N+M) targets
+//   batched layout (seg != nullptr): the items form segments of 2^segE slots,
+//                                 one dataset per segment; seg[4s..4s+3] =
+//                                 {sources, first target slot, targets,
+//                                 global index of the first target}; the other
+//                                 slots are padding (neither role).
 struct ItemMap {
     int64_t n_src, tgt_off, n_tgt;
-    __device__ __forceinline__ bool is_src(uint32_t it) const { return (int64_t)it < n_src; }
+    const int64_t* seg;
+    int segE;
+    __device__ __forceinline__ bool is_src(uint32_t it) const {
+        if (!seg) return (int64_t)it < n_src;
+        const int64_t loc = it & ((1u << segE) - 1u);
+        return loc < seg[4 * (int64_t)(it >> segE)];
+    }
     __device__ __forceinline__ bool is_tgt(uint32_t it) const {
-        return (int64_t)it >= tgt_off && (int64_t)it < tgt_off + n_tgt;
+        if (!seg) return (int64_t)it >= tgt_off && (int64_t)it < tgt_off + n_tgt;
+        const int64_t s = it >> segE, loc = it & ((1u << segE) - 1u);
+        return loc >= seg[4 * s + 1] && loc < seg[4 * s + 1] + seg[4 * s + 2];
+    }
+    __device__ __forceinline__ int64_t tgt_index(uint32_t it) const {
+        if (!seg) return (int64_t)it - tgt_off;
+        const int64_t s = it >> segE, loc = it & ((1u << segE) - 1u);
+        return seg[4 * s + 3] + loc - seg[4 * s + 1];
     }
 };
 
@@ -43,7 +61,7 @@ struct PolCount : ItemMap {
     __device__ static V add(V a, V b) { return a + b; }
     __device__ void local_weights(uint32_t, uint32_t, LW*) const {}
     __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!loc[j]) continue;
@@ -54,7 +72,7 @@ struct PolCount : ItemMap {
     __device__ void src_weights(uint32_t, int, V& f, V& b) const { f = 1u; b = 1u; }
     __device__ void prep_item(uint32_t, uint32_t) const {}
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const uint32_t o = fwd_orthant(pb, pbmask);
         acc[(int64_t)o * n_tgt + t] += f;
         acc[(int64_t)(o | 1u) * n_tgt + t] += b;
@@ -79,7 +97,7 @@ struct PolW64 : ItemMap {
         o[0] = o[1] = o[2] = o[3] = v;
     }
     __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const uint32_t o = fwd_orthant((uint32_t)(j >> 1) | (cls << 1), pbmask) | (uint32_t)(j & 1);
@@ -89,7 +107,7 @@ struct PolW64 : ItemMap {
     __device__ void src_weights(uint32_t item, int, V& f, V& b) const { f = b = w[item]; }
     __device__ void prep_item(uint32_t, uint32_t) const {}
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const uint32_t o = fwd_orthant(pb, pbmask);
         acc[(int64_t)o * n_tgt + t] += f;
         acc[(int64_t)(o | 1u) * n_tgt + t] += b;
@@ -114,7 +132,7 @@ struct PolWFF : ItemMap {
         o[0] = o[1] = o[2] = o[3] = v;
     }
     __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const uint32_t o = fwd_orthant((uint32_t)(j >> 1) | (cls << 1), pbmask) | (uint32_t)(j & 1);
@@ -124,7 +142,7 @@ struct PolWFF : ItemMap {
     __device__ void src_weights(uint32_t item, int, V& f, V& b) const { f = b = w[item]; }
     __device__ void prep_item(uint32_t, uint32_t) const {}
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const uint32_t o = fwd_orthant(pb, pbmask);
         acc[(int64_t)o * n_tgt + t] = ff_add(acc[(int64_t)o * n_tgt + t], f);
         acc[(int64_t)(o | 1u) * n_tgt + t] = ff_add(acc[(int64_t)(o | 1u) * n_tgt + t], b);
@@ -218,7 +236,7 @@ struct PolKF : ItemMap {
     }
     // target factors B E1^{+-} E0^{-+} applied once to the four local sums
     __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const BaseF B = base_of(item, cls);
         const FacF e1 = fac[(int64_t)1 * n_items + item];
         const FacF e0 = fac[item];
@@ -259,7 +277,7 @@ struct PolKF : ItemMap {
         }
     }
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const FacF e1 = fac[(int64_t)1 * n_items + item];
         const FacF e0 = fac[item];
         const BaseF B = base[item];
@@ -356,7 +374,7 @@ struct PolKD : ItemMap {
         }
     }
     __device__ void flush(uint32_t item, uint32_t cls, const V* loc) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const BaseD B = base_of(item, cls);
         const FacD e1 = fac[(int64_t)1 * n_items + item];
         const FacD e0 = fac[item];
@@ -392,7 +410,7 @@ struct PolKD : ItemMap {
         }
     }
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
-        const int64_t t = (int64_t)item - tgt_off;
+        const int64_t t = tgt_index(item);
         const FacD e1 = fac[(int64_t)1 * n_items + item];
         const FacD e0 = fac[item];
         const BaseD B = base[item];
@@ -433,6 +451,7 @@ fk_status plain_merge_level(const MergeArgs& a, cudaStream_t st);
 fk_status gather_outer(const uint32_t* seq, int64_t n, const uint32_t* Pkey, uint32_t* key,
                        uint32_t* meta, cudaStream_t st);
 fk_status record_index(const uint32_t* seq, int64_t n, int E, uint32_t* idx, cudaStream_t st);
+fk_status iota_u32(uint32_t* a, int64_t n, cudaStream_t st);
 inline int ceil_log2(int64_t n) {
     int e = 0;
     while (((int64_t)1 << e) < n) ++e;
@@ -538,7 +557,7 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
 // are the per-axis positions, seq_top the items sorted by P[d_eff-1].
 template <class Pol, int CLSB>
 fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,
-                   const Pol& pol, Arena& ar, cudaStream_t st) {
+                   const Pol& pol, Arena& ar, cudaStream_t st, int levels = -1) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
     OuterBuffers ob[8] = {};
@@ -555,7 +574,7 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (dominance sweep)");
     if (n <= 1) return FK_OK;
     ClassSpec cs = {};
-    const int E = ceil_log2(n);
+    const int E = levels >= 0 ? levels : ceil_log2(n);
     // for k == d_eff-1 the axis index is P[d_eff-1] itself (idx == nullptr above)
     if (d_eff - 1 >= 2) ob[d_eff - 1].idx = nullptr;
     return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, st);

@@ -41,15 +41,32 @@ struct SAccP {
     __device__ uint32_t operator()(int64_t i) const { return p[pd(base + (int)i)]; }
 };
 
+// Item roles: flat (sources [0, n_src), targets [tgt_off, tgt_off + n_tgt)) or
+// batched segments as in dc::ItemMap.
 struct Items {
     int64_t n_src, tgt_off, n_tgt;
     uint32_t full;      // class value of a receiving target (all enclosing bits set)
+    const int64_t* seg;
+    int segE;
+    __device__ __forceinline__ bool is_src(uint32_t it) const {
+        if (!seg) return (int64_t)it < n_src;
+        return (int64_t)(it & ((1u << segE) - 1u)) < seg[4 * (int64_t)(it >> segE)];
+    }
+    __device__ __forceinline__ bool is_tgt(uint32_t it) const {
+        if (!seg) return (int64_t)it >= tgt_off && (int64_t)it < tgt_off + n_tgt;
+        const int64_t s = it >> segE, loc = it & ((1u << segE) - 1u);
+        return loc >= seg[4 * s + 1] && loc < seg[4 * s + 1] + seg[4 * s + 2];
+    }
+    __device__ __forceinline__ int64_t tgt_index(uint32_t it) const {
+        if (!seg) return (int64_t)it - tgt_off;
+        const int64_t s = it >> segE, loc = it & ((1u << segE) - 1u);
+        return seg[4 * s + 3] + loc - seg[4 * s + 1];
+    }
     __device__ __forceinline__ bool src_active(uint32_t meta) const {
-        return (int64_t)(meta & kItemMask) < n_src && (meta >> kItemBits) == 0u;
+        return (meta >> kItemBits) == 0u && is_src(meta & kItemMask);
     }
     __device__ __forceinline__ bool tgt_active(uint32_t meta) const {
-        const int64_t it = (int64_t)(meta & kItemMask);
-        return it >= tgt_off && it < tgt_off + n_tgt && (meta >> kItemBits) == full;
+        return (meta >> kItemBits) == full && is_tgt(meta & kItemMask);
     }
 };
 
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(LNT) k_dom_local(const uint32_t* __restrict__ 
             pref_out[t0 + i] = s_pref[b][pd(i)];
             acc_out[t0 + i] = s_acc[b][pd(i)];
         } else if (s_acc[b][pd(i)]) {
-            C[(int64_t)(m & kItemMask) - im.tgt_off] += s_acc[b][pd(i)];
+            C[im.tgt_index(m & kItemMask)] += s_acc[b][pd(i)];
         }
     }
 }
@@ -325,14 +342,8 @@ __global__ void __launch_bounds__(NTN) k_dom_nested(const uint32_t* __restrict__
     __syncthreads();
     const int nbt = cs.nb > 1 ? cs.nb : 1;
     const uint32_t full = (1u << nbt) - 1u;
-    auto src_active = [&](uint32_t mt) {
-        const uint32_t slot = mt & 0xffffu;
-        return (int64_t)s_item[slot] < im.n_src && (mt >> 16) == 0u;
-    };
-    auto tgt_active = [&](uint32_t mt) {
-        const int64_t it = (int64_t)s_item[mt & 0xffffu];
-        return it >= im.tgt_off && it < im.tgt_off + im.n_tgt && (mt >> 16) == full;
-    };
+    auto src_active = [&](uint32_t mt) { return (mt >> 16) == 0u && im.is_src(s_item[mt & 0xffffu]); };
+    auto tgt_active = [&](uint32_t mt) { return (mt >> 16) == full && im.is_tgt(s_item[mt & 0xffffu]); };
     int ob = 0;
     for (int l = 0; l < levels; ++l) {
         plain_level_smem(s_okey + ob * NTP, s_oslot + ob * NTP, s_okey + (ob ^ 1) * NTP, s_oslot + (ob ^ 1) * NTP, ln, l);
@@ -364,7 +375,7 @@ __global__ void __launch_bounds__(NTN) k_dom_nested(const uint32_t* __restrict__
         okey_out[t0 + i] = s_okey[ob * NTP + pd(i)];
         oitem_out[t0 + i] = s_item[s_oslot[ob * NTP + pd(i)]];
         const uint32_t a = s_sum[i];
-        if (a) C[(int64_t)s_item[i] - im.tgt_off] += a;
+        if (a) C[im.tgt_index(s_item[i])] += a;
     }
 }
 
@@ -476,7 +487,7 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
         }
         const int64_t o = o0 + p;
         if (last) {
-            if (ac) C[(int64_t)(mt & kItemMask) - im.tgt_off] += ac;
+            if (ac) C[im.tgt_index(mt & kItemMask)] += ac;
         } else {
             key_out[o] = k; meta_out[o] = mt; pref_out[o] = pf; acc_out[o] = ac;
         }
@@ -484,14 +495,18 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
 }
 
 // rank counts: C_k(t) = number of sources before target t in the axis-k order
-__global__ void k_src_flags(const uint32_t* __restrict__ P, int64_t n, int64_t n_src, uint32_t* __restrict__ f) {
+__global__ void k_src_flags(const uint32_t* __restrict__ P, int64_t n, Items im, uint32_t* __restrict__ f) {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (it < n) f[P[it]] = (it < n_src) ? 1u : 0u;
+    if (it < n) f[P[it]] = im.is_src((uint32_t)it) ? 1u : 0u;
 }
-__global__ void k_rank_counts(const uint32_t* __restrict__ P, const uint32_t* __restrict__ scanned, int64_t tgt_off,
-                              int64_t n_tgt, uint32_t* __restrict__ C) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_tgt) C[t] = scanned[P[tgt_off + t]];
+// (the count restarts at every segment of 2^E positions in the batched layout)
+__global__ void k_rank_counts(const uint32_t* __restrict__ P, const uint32_t* __restrict__ scanned, int64_t n,
+                              Items im, int E, uint32_t* __restrict__ C) {
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n || !im.is_tgt((uint32_t)it)) return;
+    const uint32_t p = P[it];
+    const uint32_t s0 = (E >= 32) ? 0u : ((p >> E) << E);
+    C[im.tgt_index((uint32_t)it)] = scanned[p] - scanned[s0];
 }
 __global__ void k_seq_from_pos(const uint32_t* __restrict__ P, int64_t n, uint32_t* __restrict__ seq) {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -519,6 +534,37 @@ __global__ void k_combine(CTab ct, int d, int64_t n_tgt, uint32_t n_src, dc::Sel
             T = (T - neg) & neg;
         }
         out[(int64_t)r * n_tgt + t] = s;
+    }
+}
+
+// Batched combine: target t of dataset b (tbase[b] <= t < tbase[b+1]) writes
+// orthant o to out[obase[b] + o * n_b + (t - tbase[b])].
+__global__ void k_combine_seg(CTab ct, int d, int64_t n_tgt, const int64_t* __restrict__ seg, int segE,
+                              BatchOut bo, int64_t* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tgt) return;
+    int lo = 0, hi = bo.nb;                 // dataset of t: last b with tbase[b] <= t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bo.tbase[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int b = lo;
+    const int64_t nb = bo.tbase[b + 1] - bo.tbase[b];
+    const int64_t loc = t - bo.tbase[b];
+    const int64_t nsrc = seg[4 * (int64_t)b];
+    const uint32_t full = (1u << d) - 1u;
+    for (uint32_t o = 0; o <= full; ++o) {
+        const uint32_t pos = full & ~o, neg = o;
+        int64_t s = 0;
+        uint32_t T = 0;
+        while (true) {
+            const uint32_t A = pos | T;
+            const int64_t v = (A == 0) ? nsrc : (int64_t)ct.c[A][t];
+            s += (__popc(T) & 1) ? -v : v;
+            if (T == neg) break;
+            T = (T - neg) & neg;
+        }
+        out[bo.obase[b] + (int64_t)o * nb + loc] = s;
     }
 }
 
@@ -614,11 +660,12 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
 
 // Orthant counts of N sources at the targets from the positions P[0..d-1]
 // (sources before targets on ties), by inclusion-exclusion.
-fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, int64_t n_tgt,
-                             const uint32_t* const* P, const uint32_t* mask, int64_t* out, Arena& ar,
-                             cudaStream_t st) {
+// C_A for every non-empty subset A of the d axes (rank counts for |A| = 1,
+// nested dominance for |A| >= 2); E levels of the outermost merge sort.
+static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32_t* const* P, uint32_t** Cs,
+                                 Arena& ar, cudaStream_t st) {
     const int nsub = 1 << d;
-    uint32_t* Cs[16] = {};
+    const int64_t n_tgt = im.n_tgt;
     for (int A = 1; A < nsub; ++A) Cs[A] = ar.take<uint32_t>((size_t)n_tgt);
     DomBuf B = {};
     for (int q = 0; q < 2; ++q) {
@@ -637,7 +684,6 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
     for (int A = 1; A < nsub; ++A) FK_CUDA(cudaMemsetAsync(Cs[A], 0, (size_t)n_tgt * 4, st));
     const unsigned g = grid_for(n, 256);
-    Items im{n_src, tgt_off, n_tgt, 0u};
     for (int A = 1; A < nsub; ++A) {
         const int k = __builtin_popcount((unsigned)A);
         const uint32_t* PA[8];
@@ -645,10 +691,10 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
         for (int a = 0; a < d; ++a)
             if ((A >> a) & 1) PA[q++] = P[a];
         if (k == 1) {
-            k_src_flags<<<g, 256, 0, st>>>(PA[0], n, n_src, flags);
+            k_src_flags<<<g, 256, 0, st>>>(PA[0], n, im, flags);
             FK_LAUNCH_CHECK();
             FK_TRY(scan_u32_exclusive(flags, scanned, n, stmp, st));
-            k_rank_counts<<<grid_for(n_tgt, 256), 256, 0, st>>>(PA[0], scanned, tgt_off, n_tgt, Cs[A]);
+            k_rank_counts<<<g, 256, 0, st>>>(PA[0], scanned, n, im, E, Cs[A]);
             FK_LAUNCH_CHECK();
             continue;
         }
@@ -658,8 +704,19 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
         DomBuf BB = B;
         for (int kk = 2; kk < 8; ++kk) BB.idx[kk] = (kk < k - 1) ? B.idx[kk] : nullptr;
         ClassSpecK cs = {};
-        FK_TRY(dom_recurse(k - 1, seq, n, dc::ceil_log2(n), PA, cs, im, BB, Cs[A], st));
+        FK_TRY(dom_recurse(k - 1, seq, n, E, PA, cs, im, BB, Cs[A], st));
     }
+    return FK_OK;
+}
+
+fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, int64_t n_tgt,
+                             const uint32_t* const* P, const uint32_t* mask, int64_t* out, Arena& ar,
+                             cudaStream_t st) {
+    const int nsub = 1 << d;
+    uint32_t* Cs[16] = {};
+    Items im{n_src, tgt_off, n_tgt, 0u, nullptr, 0};
+    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st));
+    if (ar.sizing) return FK_OK;
     dc::SelMap sel;
     sel.n = 0;
     for (int o = 0; o < nsub; ++o)
@@ -668,6 +725,21 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
     CTab ct = {};
     for (int A = 1; A < nsub; ++A) ct.c[A] = Cs[A];
     k_combine<<<grid_for(n_tgt, 256), 256, 0, st>>>(ct, d, n_tgt, (uint32_t)n_src, sel, out);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
+fk_status dom_orthant_counts_seg(int d, int64_t n, const int64_t* seg, int segE, int64_t n_tgt,
+                                 const uint32_t* const* P, BatchOut bo, int64_t* out, Arena& ar,
+                                 cudaStream_t st) {
+    const int nsub = 1 << d;
+    uint32_t* Cs[16] = {};
+    Items im{0, 0, n_tgt, 0u, seg, segE};
+    FK_TRY(dom_counts_core(d, n, im, segE, P, Cs, ar, st));
+    if (ar.sizing || n_tgt == 0) return FK_OK;
+    CTab ct = {};
+    for (int A = 1; A < nsub; ++A) ct.c[A] = Cs[A];
+    k_combine_seg<<<grid_for(n_tgt, 256), 256, 0, st>>>(ct, d, n_tgt, seg, segE, bo, out);
     FK_LAUNCH_CHECK();
     return FK_OK;
 }

@@ -173,6 +173,9 @@ __device__ __forceinline__ FF shfl_idx_any(FF v, int l) {
     return FF{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
 }
 
+__device__ __forceinline__ double dc_as_f64(double v) { return v; }
+__device__ __forceinline__ double dc_as_f64(FF v) { return ff_to_double(v); }
+
 // Per-item, per-axis exponent factor e^{+-v/h} = m_plus * 2^s, m_minus * 2^-s.
 struct FacF { float mp, mm; int s; };
 struct FacD { double mp, mm; int s; int pad; };
