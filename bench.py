@@ -58,6 +58,7 @@ def _args():
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
                     help="run one operation per step (profiling of a single kernel family)")
     return ap.parse_args()
@@ -328,6 +329,11 @@ def run_ours(args):
     fp64 = {"kde_fp64_ms": kde64, "kde_mixed_ms": split["kde_mixed_ms"],
             "mixed_speedup": kde64 / split["kde_mixed_ms"]}
 
+    # ---- other hot-path rows on their own workloads (reported beside the step)
+    extras = {}
+    if not args.no_extras:
+        extras = _extras(fk, torch, dev, x, stream, flush, timed)
+
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -345,11 +351,35 @@ def run_ours(args):
                            "h": H, "kde_path": "mixed", "l2": "flushed (256 MB write) between steps",
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roofline, "kernel_families": breakdown,
-                "split": split, "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+                "split": split, "fp64_path": fp64, "extras": extras, "e2e": e2e, "cpu_baseline": cpu,
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _extras(fk, torch, dev, x, stream, flush, timed):
+    """Batched 512-dataset workload (graph replay; mixed vs FP64 path) and the
+    KDE adjoint (grad w, grad h) at N=1e6, d=3."""
+    from paper_2005_03246_gb300 import datagen
+    out = {}
+    sets = datagen.batched()
+    xs = [torch.as_tensor(s["x"], device=dev) for s in sets]
+    ys = [torch.as_tensor(s["y"], device=dev) for s in sets]
+    pts = int(sum(s["n"] for s in sets))
+    bm = fk.Batched(xs, ys, h=H, path="mixed", graph=True)
+    bd = fk.Batched(xs, ys, h=H, path="fp64", graph=True)
+    tm = timed(lambda: bm.run(), reps=5)
+    td = timed(lambda: bd.run(), reps=5)
+    out["batched"] = {"workload": "512 datasets, N log-uniform [1e3,1e5], d 2/3, U[0,1] FP32; all orthant "
+                                  "counts + Laplacian KDE h=0.1 weighted by y; CUDA-graph replay",
+                      "points": pts, "mixed_ms": tm, "fp64_ms": td, "points_per_s": pts / (tm / 1e3),
+                      "mixed_speedup": td / tm}
+    g = torch.ones(x.shape[0], dtype=torch.float64, device=dev)
+    out["kde_backward_ms"] = timed(lambda: fk.kde_laplace_backward(x, H, g, need_w=True, need_z=False,
+                                                                   need_h=True, path="mixed"), reps=3)
+    return out
 
 
 def _traffic(kernel, alg_bytes):
