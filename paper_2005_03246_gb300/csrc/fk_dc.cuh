@@ -134,6 +134,13 @@ __device__ __forceinline__ uint32_t class_of_k(const ClassSpecK& cs, uint32_t it
     return c;
 }
 
+__device__ __forceinline__ int64_t mpd(int64_t p) { return p + (p >> 5); }
+struct MAccP {
+    const uint32_t* p;
+    int base;
+    __device__ uint32_t operator()(int64_t i) const { return p[mpd(base + i)]; }
+};
+
 // Phases of k_merge.
 enum { PH_PLAIN = 0, PH_TOTALS = 1, PH_SWEEP = 2 };
 
@@ -203,8 +210,9 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
     constexpr uint32_t CMASK = (1u << CLSB) - 1u;
-    __shared__ uint32_t s_key[MTILE];
-    __shared__ uint32_t s_meta[MTILE];
+    constexpr int MP = MTILE + MTILE / 32;   // padded tile (bank conflicts)
+    __shared__ uint32_t s_key[MP];
+    __shared__ uint32_t s_meta[MP];
     __shared__ int64_t s_co[6];
     __shared__ V s_scan[(PHASE == PH_PLAIN) ? 1 : 2 * NCH * (MT / 32)];
 
@@ -239,10 +247,13 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
         __syncthreads();
         lc = s_co[1];
         const int64_t cs = s_co[0], ds = s_co[2], ldd = s_co[3];
-        for (int64_t i = threadIdx.x; i < lc; i += MT) { s_key[i] = a.key_in[cs + i]; s_meta[i] = a.meta_in[cs + i]; }
-        for (int64_t i = threadIdx.x; i < ldd; i += MT) { s_key[lc + i] = a.key_in[ds + i]; s_meta[lc + i] = a.meta_in[ds + i]; }
+        for (int64_t i = threadIdx.x; i < lc; i += MT) { s_key[mpd(i)] = a.key_in[cs + i]; s_meta[mpd(i)] = a.meta_in[cs + i]; }
+        for (int64_t i = threadIdx.x; i < ldd; i += MT) {
+            s_key[mpd(lc + i)] = a.key_in[ds + i];
+            s_meta[mpd(lc + i)] = a.meta_in[ds + i];
+        }
     } else {
-        for (int64_t i = threadIdx.x; i < ln; i += MT) { s_key[i] = a.key_in[o0 + i]; s_meta[i] = a.meta_in[o0 + i]; }
+        for (int64_t i = threadIdx.x; i < ln; i += MT) { s_key[mpd(i)] = a.key_in[o0 + i]; s_meta[mpd(i)] = a.meta_in[o0 + i]; }
     }
     __syncthreads();
 
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
 #pragma unroll
         for (int c = 0; c < NCH; ++c) { tf[c] = Pol::zero(); tb[c] = Pol::zero(); }
         for (int64_t i = threadIdx.x; i < ln; i += MT) {
-            const uint32_t m = s_meta[i];
+            const uint32_t m = s_meta[mpd(i)];
             const int half = (i >= lc) ? 1 : 0;
             const uint32_t item = m & kItemMask;
             if (pol.is_src(item)) {
@@ -293,13 +304,13 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
             if (e == 0 || (!big && (p % R2) == 0)) {
                 if (big) { bsl = 0; cl = lc; dl = ln - lc; }
                 else { bsl = (p / R2) * R2; cl = min(R, ln - bsl); dl = min(R2, ln - bsl) - cl; }
-                SAcc A{s_key + bsl}, B{s_key + bsl + cl};
+                MAccP A{s_key, (int)bsl}, B{s_key, (int)(bsl + cl)};
                 i = merge_path(A, cl, B, dl, p - bsl);
                 j = (p - bsl) - i;
             }
-            bool takeC = (i < cl) && (j >= dl || s_key[bsl + i] <= s_key[bsl + cl + j]);
-            if (takeC) { ek[e] = s_key[bsl + i]; em[e] = s_meta[bsl + i]; eh[e] = 0; ++i; }
-            else { ek[e] = s_key[bsl + cl + j]; em[e] = s_meta[bsl + cl + j]; eh[e] = 1; ++j; }
+            bool takeC = (i < cl) && (j >= dl || s_key[mpd(bsl + i)] <= s_key[mpd(bsl + cl + j)]);
+            if (takeC) { ek[e] = s_key[mpd(bsl + i)]; em[e] = s_meta[mpd(bsl + i)]; eh[e] = 0; ++i; }
+            else { ek[e] = s_key[mpd(bsl + cl + j)]; em[e] = s_meta[mpd(bsl + cl + j)]; eh[e] = 1; ++j; }
             cnt = e + 1;
         }
     }
@@ -426,6 +437,13 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
 // inside one innermost sort the side bits of the enclosing axes are fixed, so
 // those four sums are all a target receives; they are flushed to the global
 // accumulators once (Pol::flush) after the last local level.
+__device__ __forceinline__ int lpd(int p) { return p + (p >> 5); }
+struct LAccP {
+    const uint32_t* p;
+    int base;
+    __device__ uint32_t operator()(int64_t i) const { return p[lpd(base + (int)i)]; }
+};
+
 template <class Pol>
 struct LocalCfg {
     static constexpr int T = Pol::kLocalT;     // items per tile
@@ -444,10 +462,11 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
     constexpr int NCH = 2 << CLSB;
     constexpr uint32_t CMASK = (1u << CLSB) - 1u;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw);             // [2][T]
-    uint32_t* s_meta = s_key + 2 * T;                                   // [2][T]
-    uint16_t* s_home = reinterpret_cast<uint16_t*>(s_meta + 2 * T);     // [2][T]
-    V* s_acc = reinterpret_cast<V*>(s_home + 2 * T);                    // [T][4]
+    constexpr int TP = T + T / 32;                                      // padded row (bank conflicts)
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw);             // [2][TP]
+    uint32_t* s_meta = s_key + 2 * TP;                                  // [2][TP]
+    uint16_t* s_home = reinterpret_cast<uint16_t*>(s_meta + 2 * TP);    // [2][TP]
+    V* s_acc = reinterpret_cast<V*>(s_home + 2 * TP + (TP & 1) * 2);    // [T][4]
     LW* s_w = reinterpret_cast<LW*>(s_acc + 4 * T);                     // [T][4]
     V* s_scan = reinterpret_cast<V*>(s_w + (Pol::kUnitWeights ? 0 : 4 * T));   // [2][NCH][NT/32]
 
@@ -457,9 +476,9 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
         if (i < ln) {
             const uint32_t item = seq[t0 + i];
             const uint32_t c = class_of_k(cs, item);
-            s_key[i] = P0[item];
-            s_meta[i] = item | (c << kItemBits);
-            s_home[i] = (uint16_t)i;
+            s_key[lpd(i)] = P0[item];
+            s_meta[lpd(i)] = item | (c << kItemBits);
+            s_home[lpd(i)] = (uint16_t)i;
             pol.prep_item(item, c);
             if constexpr (!Pol::kUnitWeights) {
                 if (pol.is_src(item)) pol.local_weights(item, c, &s_w[4 * i]);
@@ -472,9 +491,9 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
     int buf = 0;
     for (int m = 0; m < levels; ++m) {
         const int R = 1 << m, R2 = 2 << m;
-        const uint32_t* ik = s_key + buf * T;
-        const uint32_t* im = s_meta + buf * T;
-        const uint16_t* ih = s_home + buf * T;
+        const uint32_t* ik = s_key + buf * TP;
+        const uint32_t* im = s_meta + buf * TP;
+        const uint16_t* ih = s_home + buf * TP;
         uint32_t em[IT];
         uint16_t eh2[IT];
         uint32_t ek[IT];
@@ -491,12 +510,12 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
                         bsl = (p / R2) * R2;
                         cl = min(R, ln - bsl);
                         dl = min(R2, ln - bsl) - cl;
-                        SAcc A{ik + bsl}, B{ik + bsl + cl};
+                        LAccP A{ik, bsl}, B{ik, bsl + cl};
                         i = (int)merge_path(A, cl, B, dl, p - bsl);
                         j = (p - bsl) - i;
                     }
-                    const bool takeC = (i < cl) && (j >= dl || ik[bsl + i] <= ik[bsl + cl + j]);
-                    const int src = takeC ? bsl + i : bsl + cl + j;
+                    const bool takeC = (i < cl) && (j >= dl || ik[lpd(bsl + i)] <= ik[lpd(bsl + cl + j)]);
+                    const int src = takeC ? lpd(bsl + i) : lpd(bsl + cl + j);
                     ek[e] = ik[src];
                     em[e] = im[src];
                     eh2[e] = ih[src];
@@ -597,13 +616,13 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
             }
         }
         // write the merged level into the other buffer
-        uint32_t* ok = s_key + (buf ^ 1) * T;
-        uint32_t* om = s_meta + (buf ^ 1) * T;
-        uint16_t* oh = s_home + (buf ^ 1) * T;
+        uint32_t* ok = s_key + (buf ^ 1) * TP;
+        uint32_t* om = s_meta + (buf ^ 1) * TP;
+        uint16_t* oh = s_home + (buf ^ 1) * TP;
 #pragma unroll
         for (int e = 0; e < IT; ++e) {
             if (e < cnt) {
-                const int p = threadIdx.x * IT + e;
+                const int p = lpd(threadIdx.x * IT + e);
                 ok[p] = ek[e];
                 om[p] = em[e];
                 oh[p] = eh2[e];
@@ -614,14 +633,14 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
     }
     // flush the per-target sums and write the tile out for the global levels
     for (int i = threadIdx.x; i < ln; i += NT) {
-        const uint32_t m = s_meta[buf * T + i];
+        const uint32_t m = s_meta[buf * TP + lpd(i)];
         const uint32_t item = m & kItemMask;
         if (write_out) {
-            key_out[t0 + i] = s_key[buf * T + i];
+            key_out[t0 + i] = s_key[buf * TP + lpd(i)];
             meta_out[t0 + i] = m;
         }
         if (pol.is_tgt(item)) {
-            const int h = s_home[buf * T + i];
+            const int h = s_home[buf * TP + lpd(i)];
             pol.flush(item, m >> kItemBits, s_acc + 4 * h);
         }
     }
@@ -631,7 +650,8 @@ template <class Pol, int CLSB>
 constexpr size_t local_smem_bytes() {
     constexpr int T = LocalCfg<Pol>::T, NT = LocalCfg<Pol>::NT;
     constexpr int NCH = 2 << CLSB;
-    return (size_t)T * (2 * 4 + 2 * 4 + 2 * 2) + (size_t)T * 4 * sizeof(typename Pol::V) +
+    constexpr int TP = T + T / 32;
+    return (size_t)TP * (2 * 4 + 2 * 4 + 2 * 2) + 16 + (size_t)T * 4 * sizeof(typename Pol::V) +
            (Pol::kUnitWeights ? 0 : (size_t)T * 4 * sizeof(typename Pol::LW)) +
            (size_t)2 * NCH * (NT / 32) * sizeof(typename Pol::V) + 64;
 }

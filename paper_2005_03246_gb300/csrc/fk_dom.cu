@@ -453,6 +453,9 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
     __syncthreads();
     const int p0 = threadIdx.x * GI;
     int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+    uint32_t rk[GI], rm[GI], rp[GI], ra[GI];
+    int cnt = 0;
+#pragma unroll
     for (int e = 0; e < GI; ++e) {
         const int p = p0 + e;
         if (p >= ln) break;
@@ -485,11 +488,27 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
             ac = s_acc[s] + (im.tgt_active(mt) ? other : 0u);
             ++j;
         }
-        const int64_t o = o0 + p;
         if (last) {
             if (ac) C[im.tgt_index(mt & kItemMask)] += ac;
-        } else {
-            key_out[o] = k; meta_out[o] = mt; pref_out[o] = pf; acc_out[o] = ac;
+        }
+        rk[e] = k; rm[e] = mt; rp[e] = pf; ra[e] = ac;
+        cnt = e + 1;
+    }
+    if (last) return;
+    const int64_t ob = o0 + p0;
+    if (cnt == GI) {
+        // eight consecutive outputs per thread: two 16-byte stores per array
+        uint4* a = reinterpret_cast<uint4*>(key_out + ob);
+        uint4* b = reinterpret_cast<uint4*>(meta_out + ob);
+        uint4* c = reinterpret_cast<uint4*>(pref_out + ob);
+        uint4* dd = reinterpret_cast<uint4*>(acc_out + ob);
+        a[0] = make_uint4(rk[0], rk[1], rk[2], rk[3]); a[1] = make_uint4(rk[4], rk[5], rk[6], rk[7]);
+        b[0] = make_uint4(rm[0], rm[1], rm[2], rm[3]); b[1] = make_uint4(rm[4], rm[5], rm[6], rm[7]);
+        c[0] = make_uint4(rp[0], rp[1], rp[2], rp[3]); c[1] = make_uint4(rp[4], rp[5], rp[6], rp[7]);
+        dd[0] = make_uint4(ra[0], ra[1], ra[2], ra[3]); dd[1] = make_uint4(ra[4], ra[5], ra[6], ra[7]);
+    } else {
+        for (int e = 0; e < cnt; ++e) {
+            key_out[ob + e] = rk[e]; meta_out[ob + e] = rm[e]; pref_out[ob + e] = rp[e]; acc_out[ob + e] = ra[e];
         }
     }
 }
