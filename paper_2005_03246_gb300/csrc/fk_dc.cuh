@@ -70,6 +70,33 @@ __device__ __forceinline__ T shfl_down_t(const T& v, int o, int width) {
     return r;
 }
 
+// Word-wise select between two accumulator values (no branches).
+template <class T>
+__device__ __forceinline__ T sel_t(bool p, const T& a, const T& b) {
+    T r;
+    const uint32_t* x = reinterpret_cast<const uint32_t*>(&a);
+    const uint32_t* y = reinterpret_cast<const uint32_t*>(&b);
+    uint32_t* q = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) q[i] = p ? x[i] : y[i];
+    return r;
+}
+// Channel c of a register array (selects instead of dynamic indexing).
+template <class T, int N>
+__device__ __forceinline__ T pick(const T (&a)[N], int c) {
+    T r = a[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) r = sel_t(c == k, a[k], r);
+    return r;
+}
+// a[c] += w with one addition whatever c is.
+template <class Pol, int N>
+__device__ __forceinline__ void add_at(typename Pol::V (&a)[N], int c, const typename Pol::V& w) {
+    const typename Pol::V s = Pol::add(pick(a, c), w);
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k] = sel_t(c == k, s, a[k]);
+}
+
 // Merge path: number of elements taken from A among the first q outputs of a
 // stable merge (A first on ties) of sorted A[0,la) and B[0,lb).
 template <class Acc>
@@ -130,7 +157,9 @@ struct ClassSpecK {
 };
 __device__ __forceinline__ uint32_t class_of_k(const ClassSpecK& cs, uint32_t item) {
     uint32_t c = 0;
-    for (int j = 0; j < cs.nb; ++j) c |= ((cs.idx[j][item] >> cs.lvl[j]) & 1u) << j;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)      // static indices keep cs out of local memory
+        if (j < cs.nb) c |= ((cs.idx[j][item] >> cs.lvl[j]) & 1u) << j;
     return c;
 }
 
@@ -178,25 +207,41 @@ __device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Po
         be[c] = (lw == w - 1) ? Pol::zero() : eb;
     }
     if (ts <= 32) return;
-    // segments spanning several warps: add the totals of earlier / later warps
+    // segments spanning several warps: exclusive scans of the warp totals
+    // inside each segment, one (direction, channel) row per warp
+    constexpr int NW = NT / 32;
     const int wps = ts >> 5;                 // warps per segment
     if (lane == 31) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) sh[(0 * NCH + c) * (NT / 32) + warp] = fi[c];
+        for (int c = 0; c < NCH; ++c) sh[(0 * NCH + c) * NW + warp] = fi[c];
     }
     if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) sh[(1 * NCH + c) * (NT / 32) + warp] = bi[c];
+        for (int c = 0; c < NCH; ++c) sh[(1 * NCH + c) * NW + warp] = bi[c];
     }
     __syncthreads();
-    const int seg0 = warp & ~(wps - 1);
+    for (int row = warp; row < 2 * NCH; row += NW) {
+        const bool fw = row < NCH;
+        V v = (lane < NW) ? sh[row * NW + lane] : Pol::zero();
+        const int lq = lane & (wps - 1);
+        for (int o = 1; o < wps; o <<= 1) {
+            if (fw) {
+                const V y = shfl_up_t(v, o, wps);
+                if (lq >= o) v = Pol::add(y, v);
+            } else {
+                const V y = shfl_down_t(v, o, wps);
+                if (lq + o < wps) v = Pol::add(v, y);
+            }
+        }
+        V x = fw ? shfl_up_t(v, 1, wps) : shfl_down_t(v, 1, wps);
+        if (fw ? (lq == 0) : (lq == wps - 1)) x = Pol::zero();
+        if (lane < NW) sh[row * NW + lane] = x;
+    }
+    __syncthreads();
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        V accf = Pol::zero(), accb = Pol::zero();
-        for (int q = seg0; q < warp; ++q) accf = Pol::add(accf, sh[(0 * NCH + c) * (NT / 32) + q]);
-        for (int q = warp + 1; q < seg0 + wps; ++q) accb = Pol::add(accb, sh[(1 * NCH + c) * (NT / 32) + q]);
-        fe[c] = Pol::add(accf, fe[c]);
-        be[c] = Pol::add(be[c], accb);
+        fe[c] = Pol::add(sh[(0 * NCH + c) * NW + warp], fe[c]);
+        be[c] = Pol::add(be[c], sh[(1 * NCH + c) * NW + warp]);
     }
     __syncthreads();
 }
@@ -270,9 +315,8 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
                 V wf, wb;
                 pol.src_weights(item, half, wf, wb);
                 const int ch = (half << CLSB) | (int)(m >> kItemBits);
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (c == ch) { tf[c] = Pol::add(tf[c], wf); tb[c] = Pol::add(tb[c], wb); }
+                add_at<Pol>(tf, ch, wf);
+                add_at<Pol>(tb, ch, wb);
             }
         }
         // CTA reduction through the scan helper: inclusive total = excl + own
@@ -352,9 +396,8 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
         for (int e = 0; e < MI; ++e) {
             if (e < cnt) {
                 const int ch = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (c == ch) { fe[c] = Pol::add(fe[c], wf[e]); be[c] = Pol::add(be[c], wb[e]); }
+                add_at<Pol>(fe, ch, wf[e]);
+                add_at<Pol>(be, ch, wb[e]);
             }
         }
         seg_scan<Pol, NCH>(fe, be, ts, s_scan);
@@ -384,12 +427,8 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
                 const int cls = (int)(em[e] >> kItemBits);
                 const int own = (eh[e] << CLSB) | cls;
                 const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (c == opp) fwd[e] = run[c];
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (c == own) run[c] = Pol::add(run[c], wf[e]);
+                fwd[e] = pick(run, opp);
+                add_at<Pol>(run, own, wf[e]);
             }
         }
     }
@@ -409,19 +448,14 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
                 const int cls = (int)(em[e] >> kItemBits);
                 const int own = (eh[e] << CLSB) | cls;
                 const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
-                V bwd = Pol::zero();
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (c == opp) bwd = run[c];
+                const V bwd = pick(run, opp);
                 const uint32_t item = em[e] & kItemMask;
                 if (pol.is_tgt(item)) {
                     // position bits: bit 0 = half on axis 1, bit j = class bit of axis j+1
                     const uint32_t pb = (uint32_t)eh[e] | ((uint32_t)cls << 1);
                     pol.target(item, pb, fwd[e], bwd);
                 }
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (c == own) run[c] = Pol::add(run[c], wb[e]);
+                add_at<Pol>(run, own, wb[e]);
             }
         }
     }
@@ -429,14 +463,26 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
 
 
 // ------------------------------------------------------------------ tile-local levels
-// All merge levels whose merged runs fit in one tile of LT items run in shared
+// All merge levels whose merged runs fit in one tile of T items run in shared
 // memory in one launch.  The tile is gathered straight from the enclosing
 // state (items sorted by P_1 inside their nodes): key = P_0[item], class bits,
-// and the policy's per-item weights.  Targets accumulate their sums in shared
-// memory, indexed by the item's slot in the tile and by (half, direction):
-// inside one innermost sort the side bits of the enclosing axes are fixed, so
-// those four sums are all a target receives; they are flushed to the global
-// accumulators once (Pol::flush) after the last local level.
+// and the policy's per-item weights.  Inside one innermost sort the side bits
+// of the enclosing axes are fixed, so what a target receives depends only on
+// its half on axis 1 and the direction on axis 0 at each level:
+//
+//  * plain form: four sums per target, indexed by (half, direction), flushed
+//    to the global accumulators once (Pol::flush) after the last level, which
+//    keeps the orthants apart (orthant sums, per-orthant kernel terms);
+//  * folded form (kernel sums without per-orthant terms): a source in half h
+//    carries w F(h, dir), F(h, dir) = B E1^{h} E0^{dir} (the factor products
+//    of eq. Laplacian decomposition nD, mantissa and power-of-two shift), and
+//    a target in half h turns its forward and backward sums into kernel values
+//    with F(h, -) and F(h, +): the same per-item products read with the other
+//    direction.  The values are bounded by the sum of the weights, so one
+//    compensated accumulator per target and weight channel holds them.
+//
+// The key, meta and home (slot of the item's per-item data) arrays are
+// single-buffered: each level merges into registers, then writes back.
 __device__ __forceinline__ int lpd(int p) { return p + (p >> 5); }
 struct LAccP {
     const uint32_t* p;
@@ -444,31 +490,112 @@ struct LAccP {
     __device__ uint32_t operator()(int64_t i) const { return p[lpd(base + (int)i)]; }
 };
 
-template <class Pol>
+template <class Pol, int CLSB, bool FOLD>
 struct LocalCfg {
-    static constexpr int T = Pol::kLocalT;     // items per tile
-    static constexpr int NT = 512;             // threads
-    static constexpr int IT = T / NT;          // items per thread
-};
-
-template <class Pol, int CLSB>
-__global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict__ seq, int64_t n,
-                                                     const uint32_t* __restrict__ P0, ClassSpecK cs, int levels,
-                                                     Pol pol, uint32_t* __restrict__ key_out,
-                                                     uint32_t* __restrict__ meta_out, int write_out) {
+    // items per tile (the folded form halves it at d = 4 to keep its
+    // per-thread state in registers)
+    static constexpr int T = FOLD ? (CLSB >= 2 ? Pol::kFoldT / 2 : Pol::kFoldT) : Pol::kLocalT;
+    // threads: 512, or 256 when the per-thread channel sums alone would take
+    // more than 32 registers (so that they stay in registers)
+    static constexpr int NT = sizeof(typename Pol::V) * (2 << CLSB) > 128 ? 256 : 512;
+    static constexpr int IT = T / NT;                              // items per thread
+    static constexpr int TP = T + T / 32;                          // padded rows (bank conflicts)
     typedef typename Pol::V V;
     typedef typename Pol::LW LW;
-    constexpr int T = LocalCfg<Pol>::T, NT = LocalCfg<Pol>::NT, IT = LocalCfg<Pol>::IT;
+    typedef typename Pol::M M;
+    typedef typename Pol::FA FA;
+    // shared memory layout (byte offsets)
+    static constexpr size_t o_key = 0;
+    static constexpr size_t o_meta = o_key + 4 * (size_t)TP;
+    static constexpr size_t o_home = o_meta + 4 * (size_t)TP;
+    static constexpr size_t o_data = (o_home + 2 * (size_t)TP + 15) / 16 * 16;
+    // plain form: sums [T][4] and weights [T][4]
+    static constexpr size_t o_acc = o_data;
+    static constexpr size_t o_w = o_acc + (FOLD ? 0 : (size_t)T * 4 * sizeof(V));
+    // folded form: factors [T][4] (mantissa, shift), weights [T], sums [T][NW]
+    static constexpr size_t o_fm = o_data;
+    static constexpr size_t o_fs = o_fm + (FOLD ? (size_t)T * 4 * sizeof(M) : 0);
+    static constexpr size_t o_wt = o_fs + (FOLD ? (size_t)T * 4 * 4 : 0);
+    static constexpr size_t o_fa = o_wt + (FOLD ? ((size_t)T * sizeof(M) + 15) / 16 * 16 : 0);
+    static constexpr size_t o_end_data =
+        FOLD ? o_fa + (size_t)T * Pol::kNW * sizeof(FA)
+             : o_w + (Pol::kUnitWeights ? 0 : (size_t)T * 4 * sizeof(LW));
+    static constexpr size_t o_scan = (o_end_data + 15) / 16 * 16;
+    static constexpr size_t bytes = o_scan + (size_t)2 * (2 << CLSB) * (NT / 32) * sizeof(V);
+};
+
+// One tile-local merge level: each thread takes IT consecutive outputs of
+// the merge of the runs of length R (read from the single-buffered arrays);
+// eh packs the item's home slot (low 16 bits) and its half (bit 16).
+// Returns the number of outputs taken.
+template <int IT>
+__device__ __forceinline__ int local_merge(const uint32_t* s_key, const uint32_t* s_meta, const uint16_t* s_home,
+                                           int ln, int R, uint32_t (&ek)[IT], uint32_t (&em)[IT],
+                                           uint32_t (&eh)[IT]) {
+    const int R2 = 2 * R;
+    const int p0 = threadIdx.x * IT;
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0, cnt = 0;
+#pragma unroll
+    for (int e = 0; e < IT; ++e) {
+        const int p = p0 + e;
+        if (p < ln) {
+            if (e == 0 || (p % R2) == 0) {
+                bsl = (p / R2) * R2;
+                cl = min(R, ln - bsl);
+                dl = min(R2, ln - bsl) - cl;
+                LAccP A{s_key, bsl}, B{s_key, bsl + cl};
+                i = (int)merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+            }
+            const bool takeC = (i < cl) && (j >= dl || s_key[lpd(bsl + i)] <= s_key[lpd(bsl + cl + j)]);
+            const int src = takeC ? lpd(bsl + i) : lpd(bsl + cl + j);
+            ek[e] = s_key[src];
+            em[e] = s_meta[src];
+            eh[e] = (uint32_t)s_home[src] | (takeC ? 0u : 0x10000u);
+            if (takeC) ++i; else ++j;
+            cnt = e + 1;
+        }
+    }
+    return cnt;
+}
+
+// Writes a merged level back into the single-buffered arrays.
+template <int IT>
+__device__ __forceinline__ void local_store(uint32_t* s_key, uint32_t* s_meta, uint16_t* s_home, int cnt,
+                                            const uint32_t (&ek)[IT], const uint32_t (&em)[IT],
+                                            const uint32_t (&eh)[IT]) {
+    __syncthreads();   // every read of this level is done
+#pragma unroll
+    for (int e = 0; e < IT; ++e) {
+        if (e < cnt) {
+            const int p = lpd(threadIdx.x * IT + e);
+            s_key[p] = ek[e];
+            s_meta[p] = em[e];
+            s_home[p] = (uint16_t)(eh[e] & 0xffffu);
+        }
+    }
+    __syncthreads();
+}
+
+// Plain form: four sums per target, flushed with the target factors.
+template <class Pol, int CLSB>
+__global__ void __launch_bounds__(LocalCfg<Pol, CLSB, false>::NT)
+    k_local_sweep(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0, ClassSpecK cs,
+                  int levels, Pol pol, uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
+                  int write_out) {
+    typedef LocalCfg<Pol, CLSB, false> Cfg;
+    typedef typename Pol::V V;
+    typedef typename Pol::LW LW;
+    constexpr int T = Cfg::T, NT = Cfg::NT, IT = Cfg::IT;
     constexpr int NCH = 2 << CLSB;
     constexpr uint32_t CMASK = (1u << CLSB) - 1u;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TP = T + T / 32;                                      // padded row (bank conflicts)
-    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw);             // [2][TP]
-    uint32_t* s_meta = s_key + 2 * TP;                                  // [2][TP]
-    uint16_t* s_home = reinterpret_cast<uint16_t*>(s_meta + 2 * TP);    // [2][TP]
-    V* s_acc = reinterpret_cast<V*>(s_home + 2 * TP + (TP & 1) * 2);    // [T][4]
-    LW* s_w = reinterpret_cast<LW*>(s_acc + 4 * T);                     // [T][4]
-    V* s_scan = reinterpret_cast<V*>(s_w + (Pol::kUnitWeights ? 0 : 4 * T));   // [2][NCH][NT/32]
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_key);
+    uint32_t* s_meta = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_meta);
+    uint16_t* s_home = reinterpret_cast<uint16_t*>(smem_raw + Cfg::o_home);
+    V* s_acc = reinterpret_cast<V*>(smem_raw + Cfg::o_acc);
+    LW* s_w = reinterpret_cast<LW*>(smem_raw + Cfg::o_w);
+    V* s_scan = reinterpret_cast<V*>(smem_raw + Cfg::o_scan);
 
     const int64_t t0 = (int64_t)blockIdx.x * T;
     const int ln = (int)min((int64_t)T, n - t0);
@@ -488,57 +615,21 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
         for (int j = 0; j < 4; ++j) s_acc[4 * i + j] = Pol::zero();
     }
     __syncthreads();
-    int buf = 0;
     for (int m = 0; m < levels; ++m) {
-        const int R = 1 << m, R2 = 2 << m;
-        const uint32_t* ik = s_key + buf * TP;
-        const uint32_t* im = s_meta + buf * TP;
-        const uint16_t* ih = s_home + buf * TP;
-        uint32_t em[IT];
-        uint16_t eh2[IT];
-        uint32_t ek[IT];
-        int eh[IT];
-        int cnt = 0;
-        {
-            const int p0 = threadIdx.x * IT;
-            int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
-#pragma unroll
-            for (int e = 0; e < IT; ++e) {
-                const int p = p0 + e;
-                if (p < ln) {
-                    if (e == 0 || (p % R2) == 0) {
-                        bsl = (p / R2) * R2;
-                        cl = min(R, ln - bsl);
-                        dl = min(R2, ln - bsl) - cl;
-                        LAccP A{ik, bsl}, B{ik, bsl + cl};
-                        i = (int)merge_path(A, cl, B, dl, p - bsl);
-                        j = (p - bsl) - i;
-                    }
-                    const bool takeC = (i < cl) && (j >= dl || ik[lpd(bsl + i)] <= ik[lpd(bsl + cl + j)]);
-                    const int src = takeC ? lpd(bsl + i) : lpd(bsl + cl + j);
-                    ek[e] = ik[src];
-                    em[e] = im[src];
-                    eh2[e] = ih[src];
-                    eh[e] = takeC ? 0 : 1;
-                    if (takeC) ++i; else ++j;
-                    cnt = e + 1;
-                }
-            }
-        }
-        // sweep over the merged blocks of length R2
+        const int R2 = 2 << m;
+        uint32_t ek[IT], em[IT], eh[IT];
+        const int cnt = local_merge<IT>(s_key, s_meta, s_home, ln, 1 << m, ek, em, eh);
         V wf[IT], wb[IT];
 #pragma unroll
         for (int e = 0; e < IT; ++e) {
             wf[e] = Pol::zero();
             wb[e] = Pol::zero();
-            if (e < cnt) {
-                const uint32_t item = em[e] & kItemMask;
-                if (pol.is_src(item)) {
-                    if constexpr (Pol::kUnitWeights) { wf[e] = Pol::one(); wb[e] = Pol::one(); }
-                    else {
-                        wf[e] = Pol::from_lw(s_w[4 * eh2[e] + eh[e] * 2 + 0]);
-                        wb[e] = Pol::from_lw(s_w[4 * eh2[e] + eh[e] * 2 + 1]);
-                    }
+            if (e < cnt && pol.is_src(em[e] & kItemMask)) {
+                if constexpr (Pol::kUnitWeights) { wf[e] = Pol::one(); wb[e] = Pol::one(); }
+                else {
+                    const LW* l = s_w + 4 * (eh[e] & 0xffffu) + 2 * (eh[e] >> 16);
+                    wf[e] = Pol::from_lw(l[0]);
+                    wb[e] = Pol::from_lw(l[1]);
                 }
             }
         }
@@ -550,10 +641,9 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
 #pragma unroll
             for (int e = 0; e < IT; ++e) {
                 if (e < cnt) {
-                    const int ch = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        if (c == ch) { fe[c] = Pol::add(fe[c], wf[e]); be[c] = Pol::add(be[c], wb[e]); }
+                    const int ch = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                    add_at<Pol>(fe, ch, wf[e]);
+                    add_at<Pol>(be, ch, wb[e]);
                 }
             }
             seg_scan<Pol, NCH, NT>(fe, be, ts, s_scan);
@@ -572,15 +662,11 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
 #pragma unroll
                         for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
                     }
-                    const int cls = (int)(em[e] >> kItemBits);
-                    const int own = (eh[e] << CLSB) | cls;
-                    const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        if (c == opp) fwd[e] = run[c];
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        if (c == own) run[c] = Pol::add(run[c], wf[e]);
+                    const int half = (int)(eh[e] >> 16), cls = (int)(em[e] >> kItemBits);
+                    const int own = (half << CLSB) | cls;
+                    const int opp = ((1 - half) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+                    fwd[e] = pick(run, opp);
+                    add_at<Pol>(run, own, wf[e]);
                 }
             }
         }
@@ -596,64 +682,170 @@ __global__ void __launch_bounds__(512) k_local_sweep(const uint32_t* __restrict_
 #pragma unroll
                         for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
                     }
-                    const int cls = (int)(em[e] >> kItemBits);
-                    const int own = (eh[e] << CLSB) | cls;
-                    const int opp = ((1 - eh[e]) << CLSB) | (int)(~(uint32_t)cls & CMASK);
-                    V bwd = Pol::zero();
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        if (c == opp) bwd = run[c];
-                    const uint32_t item = em[e] & kItemMask;
-                    if (pol.is_tgt(item)) {
-                        V* a = s_acc + 4 * eh2[e] + 2 * eh[e];
+                    const int half = (int)(eh[e] >> 16), cls = (int)(em[e] >> kItemBits);
+                    const int own = (half << CLSB) | cls;
+                    const int opp = ((1 - half) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+                    const V bwd = pick(run, opp);
+                    if (pol.is_tgt(em[e] & kItemMask)) {
+                        V* a = s_acc + 4 * (eh[e] & 0xffffu) + 2 * half;
                         a[0] = Pol::add(a[0], fwd[e]);
                         a[1] = Pol::add(a[1], bwd);
                     }
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        if (c == own) run[c] = Pol::add(run[c], wb[e]);
+                    add_at<Pol>(run, own, wb[e]);
                 }
             }
         }
-        // write the merged level into the other buffer
-        uint32_t* ok = s_key + (buf ^ 1) * TP;
-        uint32_t* om = s_meta + (buf ^ 1) * TP;
-        uint16_t* oh = s_home + (buf ^ 1) * TP;
-#pragma unroll
-        for (int e = 0; e < IT; ++e) {
-            if (e < cnt) {
-                const int p = lpd(threadIdx.x * IT + e);
-                ok[p] = ek[e];
-                om[p] = em[e];
-                oh[p] = eh2[e];
-            }
-        }
-        __syncthreads();
-        buf ^= 1;
+        local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
     }
     // flush the per-target sums and write the tile out for the global levels
     for (int i = threadIdx.x; i < ln; i += NT) {
-        const uint32_t m = s_meta[buf * TP + lpd(i)];
+        const uint32_t m = s_meta[lpd(i)];
         const uint32_t item = m & kItemMask;
         if (write_out) {
-            key_out[t0 + i] = s_key[buf * TP + lpd(i)];
+            key_out[t0 + i] = s_key[lpd(i)];
             meta_out[t0 + i] = m;
         }
-        if (pol.is_tgt(item)) {
-            const int h = s_home[buf * TP + lpd(i)];
-            pol.flush(item, m >> kItemBits, s_acc + 4 * h);
-        }
+        if (pol.is_tgt(item)) pol.flush(item, m >> kItemBits, s_acc + 4 * s_home[lpd(i)]);
     }
 }
 
+// Folded form (kernel policies without per-orthant terms).  Source weights
+// are rebuilt from the per-item factors when needed instead of being held.
 template <class Pol, int CLSB>
-constexpr size_t local_smem_bytes() {
-    constexpr int T = LocalCfg<Pol>::T, NT = LocalCfg<Pol>::NT;
+__global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
+    k_local_fold(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0, ClassSpecK cs,
+                 int levels, Pol pol, uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
+                 int write_out) {
+    typedef LocalCfg<Pol, CLSB, true> Cfg;
+    typedef typename Pol::V V;
+    typedef typename Pol::M M;
+    typedef typename Pol::FA FA;
+    constexpr int T = Cfg::T, NT = Cfg::NT, IT = Cfg::IT;
+    constexpr int NW = Pol::kNW;
     constexpr int NCH = 2 << CLSB;
-    constexpr int TP = T + T / 32;
-    return (size_t)TP * (2 * 4 + 2 * 4 + 2 * 2) + 16 + (size_t)T * 4 * sizeof(typename Pol::V) +
-           (Pol::kUnitWeights ? 0 : (size_t)T * 4 * sizeof(typename Pol::LW)) +
-           (size_t)2 * NCH * (NT / 32) * sizeof(typename Pol::V) + 64;
+    constexpr uint32_t CMASK = (1u << CLSB) - 1u;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_key);
+    uint32_t* s_meta = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_meta);
+    uint16_t* s_home = reinterpret_cast<uint16_t*>(smem_raw + Cfg::o_home);
+    M* s_fm = reinterpret_cast<M*>(smem_raw + Cfg::o_fm);
+    int* s_fs = reinterpret_cast<int*>(smem_raw + Cfg::o_fs);
+    M* s_wt = reinterpret_cast<M*>(smem_raw + Cfg::o_wt);
+    FA* s_fa = reinterpret_cast<FA*>(smem_raw + Cfg::o_fa);
+    V* s_scan = reinterpret_cast<V*>(smem_raw + Cfg::o_scan);
+
+    const int64_t t0 = (int64_t)blockIdx.x * T;
+    const int ln = (int)min((int64_t)T, n - t0);
+    for (int i = threadIdx.x; i < T; i += NT) {
+        if (i < ln) {
+            const uint32_t item = seq[t0 + i];
+            const uint32_t c = class_of_k(cs, item);
+            s_key[lpd(i)] = P0[item];
+            s_meta[lpd(i)] = item | (c << kItemBits);
+            s_home[lpd(i)] = (uint16_t)i;
+            pol.prep_item(item, c);
+            M wt;
+            pol.fold_item(item, c, &s_fm[4 * i], &s_fs[4 * i], wt);
+            s_wt[i] = pol.is_src(item) ? wt : (M)0;   // 0: no source role
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) s_fa[NW * i + q] = Pol::fa_zero();
+    }
+    __syncthreads();
+    for (int m = 0; m < levels; ++m) {
+        const int R2 = 2 << m;
+        uint32_t ek[IT], em[IT], eh[IT];
+        const int cnt = local_merge<IT>(s_key, s_meta, s_home, ln, 1 << m, ek, em, eh);
+        // factors F(h, +) (index 0) and F(h, -) (index 1) of each element
+        M f0[IT], f1[IT], wt[IT];
+        int g0[IT], g1[IT];
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+            f0[e] = f1[e] = wt[e] = (M)0;
+            g0[e] = g1[e] = 0;
+            if (e < cnt) {
+                const int b = 4 * (int)(eh[e] & 0xffffu) + 2 * (int)(eh[e] >> 16);
+                f0[e] = s_fm[b];
+                f1[e] = s_fm[b + 1];
+                g0[e] = s_fs[b];
+                g1[e] = s_fs[b + 1];
+                wt[e] = s_wt[eh[e] & 0xffffu];
+            }
+        }
+        const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
+        V fe[NCH], be[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { fe[c] = Pol::zero(); be[c] = Pol::zero(); }
+        if (ts > 1) {
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+                if (e < cnt) {
+                    const int ch = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                    add_at<Pol>(fe, ch, Pol::fold_src(f0[e], g0[e], wt[e]));
+                    add_at<Pol>(be, ch, Pol::fold_src(f1[e], g1[e], wt[e]));
+                }
+            }
+            seg_scan<Pol, NCH, NT>(fe, be, ts, s_scan);
+        }
+        // forward walk: kernel value of the forward sum, F(h, -) of the target
+        M cf[IT][NW];
+        {
+            V run[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) run[c] = fe[c];
+            const int p0 = threadIdx.x * IT;
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+#pragma unroll
+                for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
+                if (e < cnt) {
+                    if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
+                    }
+                    const int half = (int)(eh[e] >> 16), cls = (int)(em[e] >> kItemBits);
+                    const int own = (half << CLSB) | cls;
+                    const int opp = ((1 - half) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+                    Pol::fold_value(pick(run, opp), f1[e], g1[e], cf[e]);
+                    add_at<Pol>(run, own, Pol::fold_src(f0[e], g0[e], wt[e]));
+                }
+            }
+        }
+        {
+            V run[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) run[c] = be[c];
+            const int p0 = threadIdx.x * IT;
+#pragma unroll
+            for (int e = IT - 1; e >= 0; --e) {
+                if (e < cnt) {
+                    if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
+                    }
+                    const int half = (int)(eh[e] >> 16), cls = (int)(em[e] >> kItemBits);
+                    const int own = (half << CLSB) | cls;
+                    const int opp = ((1 - half) << CLSB) | (int)(~(uint32_t)cls & CMASK);
+                    if (pol.is_tgt(em[e] & kItemMask)) {
+                        M cb[NW];
+                        Pol::fold_value(pick(run, opp), f0[e], g0[e], cb);
+                        Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb);
+                    }
+                    add_at<Pol>(run, own, Pol::fold_src(f1[e], g1[e], wt[e]));
+                }
+            }
+        }
+        local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
+    }
+    for (int i = threadIdx.x; i < ln; i += NT) {
+        const uint32_t m = s_meta[lpd(i)];
+        const uint32_t item = m & kItemMask;
+        if (write_out) {
+            key_out[t0 + i] = s_key[lpd(i)];
+            meta_out[t0 + i] = m;
+        }
+        if (pol.is_tgt(item)) pol.fold_flush(item, s_fa + NW * s_home[lpd(i)]);
+    }
 }
 
 // Carries for merged blocks that span several CTAs: exclusive prefix of the

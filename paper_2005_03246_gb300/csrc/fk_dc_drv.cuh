@@ -52,6 +52,10 @@ struct PolCount : ItemMap {
     static constexpr int kSrcBytes = 0, kTgtBytes = 16, kTgtFacBytes = 0;
     static constexpr int kLocalT = 4096;
     static constexpr bool kUnitWeights = true;
+    static constexpr bool kCanFold = false;      // sums stay per orthant
+    static constexpr int kFoldT = kLocalT, kNW = 1;
+    typedef float M;
+    typedef float FA;
     struct LW { uint32_t unused; };
     uint32_t* acc;        // [2^d][n_tgt]
     uint32_t pbmask;
@@ -84,6 +88,10 @@ struct PolW64 : ItemMap {
     static constexpr int kSrcBytes = 8, kTgtBytes = 32, kTgtFacBytes = 0;
     static constexpr int kLocalT = 2048;
     static constexpr bool kUnitWeights = false;
+    static constexpr bool kCanFold = false;      // sums stay per orthant
+    static constexpr int kFoldT = kLocalT, kNW = 1;
+    typedef float M;
+    typedef float FA;
     typedef double LW;
     const double* w;      // [n_src]
     double* acc;          // [2^d][n_tgt]
@@ -119,6 +127,10 @@ struct PolWFF : ItemMap {
     static constexpr int kSrcBytes = 8, kTgtBytes = 32, kTgtFacBytes = 0;
     static constexpr int kLocalT = 2048;
     static constexpr bool kUnitWeights = false;
+    static constexpr bool kCanFold = false;      // sums stay per orthant
+    static constexpr int kFoldT = kLocalT, kNW = 1;
+    typedef float M;
+    typedef float FA;
     typedef FF LW;
     const FF* w;          // [n_src] weights split into hi + lo
     FF* acc;              // [2^d][n_tgt]
@@ -202,8 +214,47 @@ struct PolKF : ItemMap {
     __device__ static V from_lw(const LW& l) {
         V r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r.v[i] = SFF{l.m[i], 0.f, l.s};
+        for (int i = 0; i < NW; ++i) r.v[i] = sff_term(l.m[i], l.s);
         return r;
+    }
+    // folded local form (targets turn their sums into kernel values)
+    static constexpr bool kCanFold = true;
+    static constexpr int kFoldT = NW == 1 ? 4096 : 2048, kNW = NW;
+    typedef float M;
+    typedef FF FA;
+    __device__ static FA fa_zero() { return ff_zero(); }
+    __device__ static V fold_src(float m, int s, float wt) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sff_term(((NW == 2 && i == 1) ? 1.f : wt) * m, s);
+        return r;
+    }
+    // kernel values v * (m 2^s) per weight channel, and a += cf + cb
+    __device__ static void fold_value(const V& v, float m, int s, float* c) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) c[i] = (v.v[i].hi + v.v[i].lo) * m * pow2f_any(v.v[i].e + s);
+    }
+    __device__ static void fold_add(FA* a, const float* cf, const float* cb) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) a[i] = ff_add_f(ff_add_f(a[i], cf[i]), cb[i]);
+    }
+    // the four products B E1^{h} E0^{dir} (index 2h + dir) and the weight
+    __device__ void fold_item(uint32_t item, uint32_t cls, float* fm, int* fs, float& wt) const {
+        const BaseF B = base_of(item, cls);
+        const FacF e1 = fac[(int64_t)1 * n_items + item];
+        const FacF e0 = fac[item];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int h = j >> 1, dir = j & 1;
+            fm[j] = B.m * (h ? e1.mm : e1.mp) * (dir ? e0.mm : e0.mp);
+            fs[j] = B.s + (h ? -e1.s : e1.s) + (dir ? -e0.s : e0.s);
+        }
+        wt = (w && is_src(item)) ? w[item] : 1.f;   // the caller zeroes it for non-sources
+    }
+    __device__ void fold_flush(uint32_t item, const FA* a) const {
+        const int64_t t = tgt_index(item);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] = ff_add(acc[(int64_t)i * n_tgt + t], a[i]);
     }
     __device__ BaseF base_of(uint32_t item, uint32_t cls) const {
         float m = 1.f;
@@ -272,8 +323,8 @@ struct PolKF : ItemMap {
 #pragma unroll
         for (int i = 0; i < NW; ++i) {
             const float wi = (NW == 2 && i == 1) ? 1.f : w0;
-            f.v[i] = SFF{wi * mb * e0.mp, 0.f, B.s + s1 + e0.s};
-            b.v[i] = SFF{wi * mb * e0.mm, 0.f, B.s + s1 - e0.s};
+            f.v[i] = sff_term(wi * mb * e0.mp, B.s + s1 + e0.s);
+            b.v[i] = sff_term(wi * mb * e0.mm, B.s + s1 - e0.s);
         }
     }
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
@@ -341,8 +392,45 @@ struct PolKD : ItemMap {
     __device__ static V from_lw(const LW& l) {
         V r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r.v[i] = SD{l.m[i], l.s};
+        for (int i = 0; i < NW; ++i) r.v[i] = sd_term(l.m[i], l.s);
         return r;
+    }
+    // folded local form (targets turn their sums into kernel values)
+    static constexpr bool kCanFold = true;
+    static constexpr int kFoldT = NW == 1 ? 2048 : 1024, kNW = NW;
+    typedef double M;
+    typedef double FA;
+    __device__ static FA fa_zero() { return 0.0; }
+    __device__ static V fold_src(double m, int s, double wt) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sd_term(((NW == 2 && i == 1) ? 1.0 : wt) * m, s);
+        return r;
+    }
+    __device__ static void fold_value(const V& v, double m, int s, double* c) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) c[i] = ldexp_i(v.v[i].m * m, max(v.v[i].e + s, -4096));
+    }
+    __device__ static void fold_add(FA* a, const double* cf, const double* cb) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) a[i] += cf[i] + cb[i];
+    }
+    __device__ void fold_item(uint32_t item, uint32_t cls, double* fm, int* fs, double& wt) const {
+        const BaseD B = base_of(item, cls);
+        const FacD e1 = fac[(int64_t)1 * n_items + item];
+        const FacD e0 = fac[item];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int h = j >> 1, dir = j & 1;
+            fm[j] = B.m * (h ? e1.mm : e1.mp) * (dir ? e0.mm : e0.mp);
+            fs[j] = B.s + (h ? -e1.s : e1.s) + (dir ? -e0.s : e0.s);
+        }
+        wt = (w && is_src(item)) ? w[item] : 1.0;
+    }
+    __device__ void fold_flush(uint32_t item, const FA* a) const {
+        const int64_t t = tgt_index(item);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] += a[i];
     }
     __device__ BaseD base_of(uint32_t item, uint32_t cls) const {
         double m = 1.0;
@@ -385,7 +473,7 @@ struct PolKD : ItemMap {
             const int ts = B.s + (h ? -e1.s : e1.s) + (dir ? e0.s : -e0.s);
 #pragma unroll
             for (int i = 0; i < NW; ++i) {
-                const double c = loc[j].v[i].m * tf * pow2d_any(loc[j].v[i].e + ts);
+                const double c = ldexp_i(loc[j].v[i].m * tf, max(loc[j].v[i].e + ts, -4096));
                 acc[(int64_t)i * n_tgt + t] += c;
                 if (i == 0 && terms) {
                     const uint32_t o = fwd_orthant((uint32_t)h | (cls << 1), pbmask) | (uint32_t)dir;
@@ -405,8 +493,8 @@ struct PolKD : ItemMap {
 #pragma unroll
         for (int i = 0; i < NW; ++i) {
             const double wi = (NW == 2 && i == 1) ? 1.0 : w0;
-            f.v[i] = SD{wi * mb * e0.mp, B.s + s1 + e0.s};
-            b.v[i] = SD{wi * mb * e0.mm, B.s + s1 - e0.s};
+            f.v[i] = sd_term(wi * mb * e0.mp, B.s + s1 + e0.s);
+            b.v[i] = sd_term(wi * mb * e0.mm, B.s + s1 - e0.s);
         }
     }
     __device__ void target(uint32_t item, uint32_t pb, V f, V b) const {
@@ -424,8 +512,8 @@ struct PolKD : ItemMap {
         const uint32_t o = fwd_orthant(pb, pbmask);
 #pragma unroll
         for (int i = 0; i < NW; ++i) {
-            const double cf = f.v[i].m * tf * pow2d_any(f.v[i].e + sf);
-            const double cb = b.v[i].m * tb * pow2d_any(b.v[i].e + sb);
+            const double cf = ldexp_i(f.v[i].m * tf, max(f.v[i].e + sf, -4096));
+            const double cb = ldexp_i(b.v[i].m * tb, max(b.v[i].e + sb, -4096));
             acc[(int64_t)i * n_tgt + t] += cf + cb;
             if (i == 0 && terms) {
                 terms[(int64_t)o * n_tgt + t] += cf;
@@ -458,30 +546,43 @@ inline int ceil_log2(int64_t n) {
     return e;
 }
 
+template <class Pol, int CLSB, bool FOLD>
+fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
+                       const Pol& pol, DCBuffers& b, int& L0, cudaStream_t st) {
+    typedef LocalCfg<Pol, CLSB, FOLD> Cfg;
+    int lt = 0;
+    while ((1 << (lt + 1)) <= Cfg::T) ++lt;
+    L0 = E < lt ? E : lt;
+    constexpr size_t smem = Cfg::bytes;
+    static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
+    void (*kern)(const uint32_t*, int64_t, const uint32_t*, ClassSpecK, int, Pol, uint32_t*, uint32_t*, int);
+    if constexpr (FOLD) kern = k_local_fold<Pol, CLSB>;
+    else kern = k_local_sweep<Pol, CLSB>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
+                          (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes) + (E > L0 ? 8.0 * n : 0.0);
+    ProfScope ps(PF_LOCAL, lbytes, st);
+    kern<<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(seq, n, P0, cs, L0, pol, b.k[0], b.m[0], E > L0 ? 1 : 0);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
 template <class Pol, int CLSB>
 fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
                      const Pol& pol, DCBuffers& b, cudaStream_t st) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
     // tile-local levels (gather fused into the tile load)
-    constexpr int T = LocalCfg<Pol>::T;
-    int lt = 0;
-    while ((1 << (lt + 1)) <= T) ++lt;
-    const int L0 = E < lt ? E : lt;
-    {
-        constexpr size_t smem = local_smem_bytes<Pol, CLSB>();
-        static bool attr_set = false;
-        if (!attr_set) {
-            FK_CUDA(cudaFuncSetAttribute(k_local_sweep<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-            attr_set = true;
-        }
-        const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
-                              (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes) + (E > L0 ? 8.0 * n : 0.0);
-        ProfScope ps(PF_LOCAL, lbytes, st);
-        k_local_sweep<Pol, CLSB><<<grid_for(n, T), LocalCfg<Pol>::NT, smem, st>>>(seq, n, P0, cs, L0, pol, b.k[0],
-                                                                                 b.m[0], E > L0 ? 1 : 0);
-        FK_LAUNCH_CHECK();
+    int L0 = 0;
+    if constexpr (Pol::kCanFold) {
+        if (!pol.terms) FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, st)));
+        else FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
+    } else {
+        FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
     }
     int cur = 0;
     const unsigned ctas = grid_for(n, MTILE);

@@ -142,18 +142,43 @@ __device__ __forceinline__ double pow2d_any(int k) {
 constexpr int kEmin = -(1 << 28);
 struct SFF { float hi, lo; int e; };
 __device__ __forceinline__ SFF sff_zero() { return SFF{0.f, 0.f, kEmin}; }
+// A zero value always carries kEmin: a zero with a large shift would
+// otherwise raise the shift of every sum it joins and flush the sum.
+__device__ __forceinline__ SFF sff_term(float m, int s) { return SFF{m, 0.f, m != 0.f ? s : kEmin}; }
 __device__ __forceinline__ SFF sff_add(SFF a, SFF b) {
     int e = max(a.e, b.e);
     float sa = pow2f_le0(a.e - e), sb = pow2f_le0(b.e - e);
     FF r = ff_add(FF{a.hi * sa, a.lo * sa}, FF{b.hi * sb, b.lo * sb});
-    return SFF{r.hi, r.lo, e};
+    return SFF{r.hi, r.lo, r.hi != 0.f ? e : kEmin};
 }
 // Shifted FP64 value m * 2^e.
 struct SD { double m; int e; };
 __device__ __forceinline__ SD sd_zero() { return SD{0.0, kEmin}; }
+// Zero test on the two 32-bit halves: integer instructions only (an FP64
+// compare would take the FP64 pipe, the scarce one on this part).
+__device__ __forceinline__ bool f64_nonzero(double v) {
+    return ((__double2hiint(v) & 0x7fffffff) | __double2loint(v)) != 0;
+}
+__device__ __forceinline__ SD sd_term(double m, int s) { return SD{m, f64_nonzero(m) ? s : kEmin}; }
+// m * 2^k by an integer add to the exponent field (no FP64 instruction):
+// m normal or zero; results below the normal range flush to zero, above it
+// saturate to infinity.
+__device__ __forceinline__ double ldexp_i(double m, int k) {
+    const int hi = __double2hiint(m), lo = __double2loint(m);
+    const int eb = (hi >> 20) & 0x7ff;
+    const int nb = eb + k;
+    if (eb == 0 || nb <= 0) return 0.0;
+    if (nb >= 0x7ff) return __hiloint2double((hi & (int)0x80000000) | 0x7ff00000, 0);
+    return __hiloint2double((int)((unsigned)hi + ((unsigned)k << 20)), lo);
+}
+// One FP64 addition: the operand with the smaller shift is rescaled by an
+// exponent add.  (No zero test on the result: a sum that cancels to exactly
+// zero keeps its shift, which only matters if far smaller values follow.)
 __device__ __forceinline__ SD sd_add(SD a, SD b) {
-    int e = max(a.e, b.e);
-    return SD{a.m * pow2d_le0(a.e - e) + b.m * pow2d_le0(b.e - e), e};
+    const bool ag = a.e >= b.e;
+    const double big = ag ? a.m : b.m, small = ag ? b.m : a.m;
+    const int eb = ag ? a.e : b.e, es = ag ? b.e : a.e;
+    return SD{big + ldexp_i(small, max(es - eb, -4096)), eb};
 }
 
 // Full-warp shuffles for every accumulator type.
