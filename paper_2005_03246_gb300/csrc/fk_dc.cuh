@@ -82,12 +82,19 @@ __device__ __forceinline__ T sel_t(bool p, const T& a, const T& b) {
     return r;
 }
 // Channel c of a register array (selects instead of dynamic indexing).
+// A multiplexer tree on the bits of c (N a power of two).
 template <class T, int N>
 __device__ __forceinline__ T pick(const T (&a)[N], int c) {
-    T r = a[0];
+    static_assert((N & (N - 1)) == 0, "channel count must be a power of two");
+    if constexpr (N == 1) {
+        return a[0];
+    } else {
+        T h[N / 2];
+        const bool b = (c & 1) != 0;
 #pragma unroll
-    for (int k = 1; k < N; ++k) r = sel_t(c == k, a[k], r);
-    return r;
+        for (int k = 0; k < N / 2; ++k) h[k] = sel_t(b, a[2 * k + 1], a[2 * k]);
+        return pick(h, c >> 1);
+    }
 }
 // a[c] += w with one addition whatever c is.
 template <class Pol, int N>
@@ -773,68 +780,62 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
             }
         }
         const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
+        const int p0 = threadIdx.x * IT;
+        // Walks from zero over the thread's elements (a thread's elements lie
+        // in one merged block when ts > 1): kernel values of the thread-local
+        // prefix (forward, with F(h, -) of the target) and suffix (backward,
+        // F(h, +)); the walks end with the thread's channel totals.
+        M cf[IT][NW], cb[IT][NW];
         V fe[NCH], be[NCH];
 #pragma unroll
         for (int c = 0; c < NCH; ++c) { fe[c] = Pol::zero(); be[c] = Pol::zero(); }
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
+            if (e < cnt) {
+                if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) fe[c] = Pol::zero();
+                }
+                const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                Pol::fold_value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
+                add_at<Pol>(fe, own, Pol::fold_src(f0[e], g0[e], wt[e]));
+            }
+        }
+#pragma unroll
+        for (int e = IT - 1; e >= 0; --e) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) cb[e][q] = (M)0;
+            if (e < cnt) {
+                if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) be[c] = Pol::zero();
+                }
+                const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                Pol::fold_value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
+                add_at<Pol>(be, own, Pol::fold_src(f1[e], g1[e], wt[e]));
+            }
+        }
+        // blocks spanning several threads: the exclusive prefix / suffix of
+        // the thread totals joins every element (the fold is linear)
         if (ts > 1) {
-#pragma unroll
-            for (int e = 0; e < IT; ++e) {
-                if (e < cnt) {
-                    const int ch = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
-                    add_at<Pol>(fe, ch, Pol::fold_src(f0[e], g0[e], wt[e]));
-                    add_at<Pol>(be, ch, Pol::fold_src(f1[e], g1[e], wt[e]));
-                }
-            }
             seg_scan<Pol, NCH, NT>(fe, be, ts, s_scan);
-        }
-        // forward walk: kernel value of the forward sum, F(h, -) of the target
-        M cf[IT][NW];
-        {
-            V run[NCH];
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) run[c] = fe[c];
-            const int p0 = threadIdx.x * IT;
 #pragma unroll
             for (int e = 0; e < IT; ++e) {
-#pragma unroll
-                for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
                 if (e < cnt) {
-                    if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+                    const int opp = ((int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits)) ^ (NCH - 1);
+                    M xf[NW], xb[NW];
+                    Pol::fold_value(pick(fe, opp), f1[e], g1[e], xf);
+                    Pol::fold_value(pick(be, opp), f0[e], g0[e], xb);
 #pragma unroll
-                        for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
-                    }
-                    const int half = (int)(eh[e] >> 16), cls = (int)(em[e] >> kItemBits);
-                    const int own = (half << CLSB) | cls;
-                    const int opp = ((1 - half) << CLSB) | (int)(~(uint32_t)cls & CMASK);
-                    Pol::fold_value(pick(run, opp), f1[e], g1[e], cf[e]);
-                    add_at<Pol>(run, own, Pol::fold_src(f0[e], g0[e], wt[e]));
+                    for (int q = 0; q < NW; ++q) { cf[e][q] += xf[q]; cb[e][q] += xb[q]; }
                 }
             }
         }
-        {
-            V run[NCH];
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) run[c] = be[c];
-            const int p0 = threadIdx.x * IT;
-#pragma unroll
-            for (int e = IT - 1; e >= 0; --e) {
-                if (e < cnt) {
-                    if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
-#pragma unroll
-                        for (int c = 0; c < NCH; ++c) run[c] = Pol::zero();
-                    }
-                    const int half = (int)(eh[e] >> 16), cls = (int)(em[e] >> kItemBits);
-                    const int own = (half << CLSB) | cls;
-                    const int opp = ((1 - half) << CLSB) | (int)(~(uint32_t)cls & CMASK);
-                    if (pol.is_tgt(em[e] & kItemMask)) {
-                        M cb[NW];
-                        Pol::fold_value(pick(run, opp), f0[e], g0[e], cb);
-                        Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb);
-                    }
-                    add_at<Pol>(run, own, Pol::fold_src(f1[e], g1[e], wt[e]));
-                }
-            }
-        }
+        for (int e = 0; e < IT; ++e)
+            if (e < cnt && pol.is_tgt(em[e] & kItemMask)) Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e]);
         local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
     }
     for (int i = threadIdx.x; i < ln; i += NT) {

@@ -217,3 +217,26 @@ def test_kde_full_size_d3_sampled():
     for path in ("mixed", "fp64"):
         got = _fk().kde_laplace(_t(x), 0.1, path=path).cpu().numpy()
         assert _rel_kde(got[idx], ref) <= TOL[path], path
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+def test_kernel_sums_with_zero_weights_and_wide_spread(path):
+    """Weights and responses with many exact zeros, points spread over 30
+    bandwidth-scaled units per axis (shifts of the factors differ by far more
+    than the FP32 exponent range): a zero term must not disturb the sums."""
+    r = np.random.default_rng(41)
+    n = 4000
+    x = (r.random((n, 3)) * 30.0).astype(np.float32)
+    x[: n // 2] = (r.standard_normal((n // 2, 3)) * 0.3 + 15.0).astype(np.float32)
+    h = [0.05, 0.08, 0.06]
+    w = r.random(n).astype(np.float32)
+    w[r.random(n) < 0.4] = 0.0
+    got = _fk().kde_laplace(_t(x), h, w=_t(w), path=path).cpu().numpy()
+    ref = oracle.kde_laplace(x, h, w=w)
+    assert _rel_kde(got, ref) <= TOL[path]
+    y = r.standard_normal(n).astype(np.float32)
+    y[r.random(n) < 0.4] = 0.0
+    gk = _fk().kreg_laplace(_t(x), _t(y), h, path=path).cpu().numpy()
+    rk = oracle.kreg_laplace(x, y, h)
+    ok = np.isfinite(rk)
+    assert np.max(np.abs(gk[ok] - rk[ok])) <= TOL[path] * 10 * np.abs(y).max()
