@@ -71,6 +71,15 @@ def _dist():
     return ws, rank, local
 
 
+# Families whose work is counted in floating-point operations (the tile-local
+# kernel-sum sweep is bound by instruction issue, not by HBM), and the FP32
+# peak they are held against: 152 SMs x 128 FP32 lanes x 2.07 GHz, one
+# non-fused operation per lane and clock.
+ALU_FAMILIES = ("kernel_local",)
+FP32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 1e12
+FP32_PEAK_SOURCE = "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -295,14 +304,29 @@ def run_ours(args):
     roofline = None
     if dom:
         name, (tms, cnt, by) = dom
-        achieved = (by / cnt) / ((tms / cnt) / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                    "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": _traffic(name, by / cnt), "launches": cnt,
-                    "avg_launch_us": tms / cnt * 1e3, "alg_bytes_per_launch": by / cnt,
-                    "share_of_step": tms / total_ms}
+        per_launch_s = (tms / cnt) / 1e3
+        if name in ALU_FAMILIES:
+            # arithmetic-bound family: work = floating-point operations
+            roofline = {"bound": "alu", "kernel": name, "achieved": (by / cnt) / per_launch_s / 1e12,
+                        "peak": FP32_PEAK_TFLOPS, "peak_source": FP32_PEAK_SOURCE, "unit": "TFLOP/s"}
+            roofline["frac"] = roofline["achieved"] / FP32_PEAK_TFLOPS
+            roofline["alg_flop_per_launch"] = by / cnt
+        else:
+            roofline = {"bound": "hbm", "kernel": name, "achieved": (by / cnt) / per_launch_s / 1e9,
+                        "peak": peak, "peak_source": peak_kind, "unit": "GB/s"}
+            roofline["frac"] = roofline["achieved"] / peak
+            roofline["alg_bytes_per_launch"] = by / cnt
+        roofline.update({"traffic": _traffic(name, by / cnt), "launches": cnt,
+                         "avg_launch_us": tms / cnt * 1e3, "share_of_step": tms / total_ms})
+
+    def _rate(name, v):
+        if v[0] <= 0:
+            return None
+        return v[2] / (v[0] / 1e3) / (1e12 if name in ALU_FAMILIES else 1e9)
+
     breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
-                     "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None} for k, v in fams.items()}
+                     "rate": _rate(k, v), "rate_unit": "TFLOP/s" if k in ALU_FAMILIES else "GB/s"}
+                 for k, v in fams.items()}
 
     # ---- per-call split and the FP64 GPU path on the same inputs
     def timed(fn, reps=3):

@@ -269,12 +269,18 @@ fk_status fk_device_status(fk_stream_t stream);
  * performance.  fk_kernel_launches returns the number of CUDA kernels this
  * library has launched in the calling process.  When profiling is enabled,
  * the main kernel families are bracketed by CUDA events recorded on the
- * stream each kernel is launched on, together with the algorithmic bytes the
- * launch moves (inputs read once, outputs written once); fk_profile_read
- * synchronises on those events and sums them for one family:
+ * stream each kernel is launched on, together with the launch's algorithmic
+ * work; fk_profile_read synchronises on those events and sums them for one
+ * family:
  *   0 divide-and-conquer merge with sweep, 1 its per-tile totals pass,
  *   2 plain merge (tree construction), 3 grid orthant pass, 4 grid histogram,
- *   5 radix-sort pass, 6 gathers, 7 tile-local merge levels with sweep.
+ *   5 radix-sort pass, 6 gathers, 7 tile-local merge levels (counts and
+ *   orthant sums), 8 tile-local merge levels of the kernel sums.
+ * The work (alg_bytes) is the bytes the launch must move (inputs read once,
+ * outputs written once) for families 0-7, and for family 8 the arithmetic
+ * operations of the sweep: 44 floating-point operations per item and merge
+ * level (two compensated additions into the running sums, two scaled
+ * compensated additions into the target's sum).
  */
 uint64_t fk_kernel_launches(void);
 void fk_profile_enable(int on);

@@ -53,7 +53,7 @@ SIGNATURES = {
 }
 
 PROFILE_FAMILIES = {"merge_sweep": 0, "merge_totals": 1, "merge_plain": 2, "grid_pass": 3,
-                    "grid_hist": 4, "radix": 5, "gather": 6, "local_sweep": 7}
+                    "grid_hist": 4, "radix": 5, "gather": 6, "local_sweep": 7, "kernel_local": 8}
 
 _lib = None
 

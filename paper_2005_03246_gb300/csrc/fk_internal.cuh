@@ -35,7 +35,12 @@ void note_launch();
 
 // Optional CUDA-event timing of kernel families (fk_profile_*).
 enum ProfFamily : int { PF_MERGE_SWEEP = 0, PF_MERGE_TOTALS = 1, PF_MERGE_PLAIN = 2, PF_GRID_PASS = 3,
-                        PF_GRID_HIST = 4, PF_RADIX = 5, PF_GATHER = 6, PF_LOCAL = 7, PF_COUNT = 8 };
+                        PF_GRID_HIST = 4, PF_RADIX = 5, PF_GATHER = 6, PF_LOCAL = 7, PF_KLOCAL = 8,
+                        PF_COUNT = 9 };
+// Arithmetic of the kernel-sum sweep per item and merge level (family PF_KLOCAL):
+// two compensated additions into the running sums and two scaled compensated
+// additions into the target's sum, 10 + 1 operations each.
+constexpr double kKernelOpsPerItemLevel = 44.0;
 bool profiling_on();
 void prof_record(int family, double bytes, cudaEvent_t a, cudaEvent_t b);
 cudaEvent_t prof_event();
