@@ -724,7 +724,8 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
                  int levels, Pol pol, uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
                  int write_out) {
     typedef LocalCfg<Pol, CLSB, true> Cfg;
-    typedef typename Pol::V V;
+    typedef typename Pol::LOps LO;
+    typedef typename LO::V V;          // tile-local sums
     typedef typename Pol::M M;
     typedef typename Pol::FA FA;
     constexpr int T = Cfg::T, NT = Cfg::NT, IT = Cfg::IT;
@@ -788,7 +789,7 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
         M cf[IT][NW], cb[IT][NW];
         V fe[NCH], be[NCH];
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) { fe[c] = Pol::zero(); be[c] = Pol::zero(); }
+        for (int c = 0; c < NCH; ++c) { fe[c] = LO::zero(); be[c] = LO::zero(); }
 #pragma unroll
         for (int e = 0; e < IT; ++e) {
 #pragma unroll
@@ -796,11 +797,11 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
             if (e < cnt) {
                 if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) fe[c] = Pol::zero();
+                    for (int c = 0; c < NCH; ++c) fe[c] = LO::zero();
                 }
                 const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
                 Pol::fold_value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
-                add_at<Pol>(fe, own, Pol::fold_src(f0[e], g0[e], wt[e]));
+                add_at<LO>(fe, own, Pol::fold_src(f0[e], g0[e], wt[e]));
             }
         }
 #pragma unroll
@@ -810,17 +811,17 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
             if (e < cnt) {
                 if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) be[c] = Pol::zero();
+                    for (int c = 0; c < NCH; ++c) be[c] = LO::zero();
                 }
                 const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
                 Pol::fold_value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
-                add_at<Pol>(be, own, Pol::fold_src(f1[e], g1[e], wt[e]));
+                add_at<LO>(be, own, Pol::fold_src(f1[e], g1[e], wt[e]));
             }
         }
         // blocks spanning several threads: the exclusive prefix / suffix of
         // the thread totals joins every element (the fold is linear)
         if (ts > 1) {
-            seg_scan<Pol, NCH, NT>(fe, be, ts, s_scan);
+            seg_scan<LO, NCH, NT>(fe, be, ts, s_scan);
 #pragma unroll
             for (int e = 0; e < IT; ++e) {
                 if (e < cnt) {

@@ -175,6 +175,8 @@ struct BaseD { double m; int s; int pad; };
 template <int NW>
 struct SFFn { SFF v[NW]; };
 template <int NW>
+struct SFn_ { SF v[NW]; };
+template <int NW>
 struct SDn { SD v[NW]; };
 
 // Mixed path: FP32 compensated bulk sums, FP64 exponent arithmetic.
@@ -222,17 +224,36 @@ struct PolKF : ItemMap {
     static constexpr int kFoldT = NW == 1 ? 4096 : 2048, kNW = NW;
     typedef float M;
     typedef FF FA;
-    __device__ static FA fa_zero() { return ff_zero(); }
-    __device__ static V fold_src(float m, int s, float wt) {
-        V r;
+    // Tile-local running sums and scans: plain FP32 mantissa with a shift.
+    // A tile-local sum has at most 8 serial terms plus a scan tree of at most
+    // 12 levels, so its relative rounding error stays near 1e-6; the target's
+    // sum over all levels is compensated.
+    struct LOps {
+        typedef SFn_<NW> V;
+        __device__ static V zero() {
+            V r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r.v[i] = sff_term(((NW == 2 && i == 1) ? 1.f : wt) * m, s);
+            for (int i = 0; i < NW; ++i) r.v[i] = sf_zero();
+            return r;
+        }
+        __device__ static V add(V a, V b) {
+            V r;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) r.v[i] = sf_add(a.v[i], b.v[i]);
+            return r;
+        }
+    };
+    __device__ static FA fa_zero() { return ff_zero(); }
+    __device__ static typename LOps::V fold_src(float m, int s, float wt) {
+        typename LOps::V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sf_term(((NW == 2 && i == 1) ? 1.f : wt) * m, s);
         return r;
     }
     // kernel values v * (m 2^s) per weight channel, and a += cf + cb
-    __device__ static void fold_value(const V& v, float m, int s, float* c) {
+    __device__ static void fold_value(const typename LOps::V& v, float m, int s, float* c) {
 #pragma unroll
-        for (int i = 0; i < NW; ++i) c[i] = (v.v[i].hi + v.v[i].lo) * m * pow2f_any(v.v[i].e + s);
+        for (int i = 0; i < NW; ++i) c[i] = v.v[i].m * m * pow2f_any(v.v[i].e + s);
     }
     __device__ static void fold_add(FA* a, const float* cf, const float* cb) {
 #pragma unroll
@@ -400,6 +421,11 @@ struct PolKD : ItemMap {
     static constexpr int kFoldT = NW == 1 ? 2048 : 1024, kNW = NW;
     typedef double M;
     typedef double FA;
+    struct LOps {   // tile-local sums: the same shifted FP64 values
+        typedef SDn<NW> V;
+        __device__ static V zero() { return PolKD::zero(); }
+        __device__ static V add(V a, V b) { return PolKD::add(a, b); }
+    };
     __device__ static FA fa_zero() { return 0.0; }
     __device__ static V fold_src(double m, int s, double wt) {
         V r;

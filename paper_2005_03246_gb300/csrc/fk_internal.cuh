@@ -127,20 +127,16 @@ __device__ __forceinline__ FF ff_from_double(double v) {
 }
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
 
-// Exact powers of two for k <= 0 (flush below the normal range).
-__device__ __forceinline__ float pow2f_le0(int k) {
-    return (k >= -126) ? __int_as_float((k + 127) << 23) : 0.0f;
-}
+// Exact powers of two built from the exponent field: k <= 0 flushes below
+// the normal range to zero; the _any forms saturate above it to infinity.
+// (A clamp and a shift: no compare-and-select.)
+__device__ __forceinline__ float pow2f_le0(int k) { return __int_as_float((max(k, -127) + 127) << 23); }
 __device__ __forceinline__ double pow2d_le0(int k) {
-    return (k >= -1022) ? __longlong_as_double((long long)(k + 1023) << 52) : 0.0;
+    return __longlong_as_double((long long)(max(k, -1023) + 1023) << 52);
 }
-__device__ __forceinline__ float pow2f_any(int k) {
-    if (k > 127) return __int_as_float(0x7f800000);
-    return (k >= -126) ? __int_as_float((k + 127) << 23) : 0.0f;
-}
+__device__ __forceinline__ float pow2f_any(int k) { return __int_as_float((min(max(k, -127), 128) + 127) << 23); }
 __device__ __forceinline__ double pow2d_any(int k) {
-    if (k > 1023) return __longlong_as_double(0x7ff0000000000000LL);
-    return (k >= -1022) ? __longlong_as_double((long long)(k + 1023) << 52) : 0.0;
+    return __longlong_as_double((long long)(min(max(k, -1023), 1024) + 1023) << 52);
 }
 
 // Shifted compensated value (hi + lo) * 2^e; the zero value has e = kEmin.
@@ -155,6 +151,14 @@ __device__ __forceinline__ SFF sff_add(SFF a, SFF b) {
     float sa = pow2f_le0(a.e - e), sb = pow2f_le0(b.e - e);
     FF r = ff_add(FF{a.hi * sa, a.lo * sa}, FF{b.hi * sb, b.lo * sb});
     return SFF{r.hi, r.lo, r.hi != 0.f ? e : kEmin};
+}
+// Shifted plain FP32 value m * 2^e (short sums: tile-local walks and scans).
+struct SF { float m; int e; };
+__device__ __forceinline__ SF sf_zero() { return SF{0.f, kEmin}; }
+__device__ __forceinline__ SF sf_term(float m, int s) { return SF{m, m != 0.f ? s : kEmin}; }
+__device__ __forceinline__ SF sf_add(SF a, SF b) {
+    const int e = max(a.e, b.e);
+    return SF{a.m * pow2f_le0(a.e - e) + b.m * pow2f_le0(b.e - e), e};
 }
 // Shifted FP64 value m * 2^e.
 struct SD { double m; int e; };
