@@ -253,31 +253,27 @@ __device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Po
     __syncthreads();
 }
 
-// The merge kernel.  PH_PLAIN: merge only.  PH_TOTALS: per-CTA channel totals
-// of the source weights (CTAs inside a merged block longer than a tile).
-// PH_SWEEP: merge plus the Merge1D sweep contributions to the targets.
-template <class Pol, int CLSB, int PHASE>
-__global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol::V* __restrict__ totals,
-                                              const typename Pol::V* __restrict__ carries) {
-    typedef typename Pol::V V;
-    constexpr int NCH = 2 << CLSB;
-    constexpr uint32_t CMASK = (1u << CLSB) - 1u;
-    constexpr int MP = MTILE + MTILE / 32;   // padded tile (bank conflicts)
-    __shared__ uint32_t s_key[MP];
-    __shared__ uint32_t s_meta[MP];
-    __shared__ int64_t s_co[6];
-    __shared__ V s_scan[(PHASE == PH_PLAIN) ? 1 : 2 * NCH * (MT / 32)];
-
+// The inputs of one CTA of a merge level in shared memory (padded rows).
+// Runs of 2R longer than a tile (big): the CTA's co-ranks are found by a
+// warp-cooperative merge-path search and its C part [cs, cs+lc) and D part
+// [ds, ds+ldd) are loaded one after the other; otherwise the tile
+// [o0, o0+ln) holds whole runs.
+struct MergeTile {
+    int64_t ln, lc, cs, ds, ldd;
+    bool big;
+};
+__device__ __forceinline__ MergeTile merge_tile_load(const MergeArgs& a, uint32_t* s_key, uint32_t* s_meta,
+                                                     int64_t* s_co) {
     const int64_t n = a.n;
     const int64_t R = (int64_t)1 << a.logR;
     const int64_t R2 = R << 1;
     const int64_t o0 = (int64_t)blockIdx.x * MTILE;
-    if (o0 >= n) return;
     const int64_t o1 = min(o0 + (int64_t)MTILE, n);
-    const int64_t ln = o1 - o0;                 // outputs of this CTA
-    const bool big = R2 > MTILE;
-    int64_t lc = 0;                              // big: local length of the C part
-    if (big) {
+    MergeTile t;
+    t.ln = o1 - o0;
+    t.big = R2 > MTILE;
+    t.lc = t.cs = t.ds = t.ldd = 0;
+    if (t.big) {
         if (threadIdx.x < 64) {
             const int64_t bs = (o0 / R2) * R2;
             const int64_t cl = min(R, n - bs);
@@ -297,18 +293,50 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
             s_co[3] = (q1 - i1) - (q0 - i0);   // D range length
         }
         __syncthreads();
-        lc = s_co[1];
-        const int64_t cs = s_co[0], ds = s_co[2], ldd = s_co[3];
-        for (int64_t i = threadIdx.x; i < lc; i += MT) { s_key[mpd(i)] = a.key_in[cs + i]; s_meta[mpd(i)] = a.meta_in[cs + i]; }
-        for (int64_t i = threadIdx.x; i < ldd; i += MT) {
-            s_key[mpd(lc + i)] = a.key_in[ds + i];
-            s_meta[mpd(lc + i)] = a.meta_in[ds + i];
+        t.lc = s_co[1];
+        t.cs = s_co[0];
+        t.ds = s_co[2];
+        t.ldd = s_co[3];
+        for (int64_t i = threadIdx.x; i < t.lc; i += MT) {
+            s_key[mpd(i)] = a.key_in[t.cs + i];
+            s_meta[mpd(i)] = a.meta_in[t.cs + i];
+        }
+        for (int64_t i = threadIdx.x; i < t.ldd; i += MT) {
+            s_key[mpd(t.lc + i)] = a.key_in[t.ds + i];
+            s_meta[mpd(t.lc + i)] = a.meta_in[t.ds + i];
         }
     } else {
-        for (int64_t i = threadIdx.x; i < ln; i += MT) { s_key[mpd(i)] = a.key_in[o0 + i]; s_meta[mpd(i)] = a.meta_in[o0 + i]; }
+        for (int64_t i = threadIdx.x; i < t.ln; i += MT) {
+            s_key[mpd(i)] = a.key_in[o0 + i];
+            s_meta[mpd(i)] = a.meta_in[o0 + i];
+        }
     }
     __syncthreads();
+    return t;
+}
 
+// The merge kernel.  PH_PLAIN: merge only.  PH_TOTALS: per-CTA channel totals
+// of the source weights (CTAs inside a merged block longer than a tile).
+// PH_SWEEP: merge plus the Merge1D sweep contributions to the targets.
+template <class Pol, int CLSB, int PHASE>
+__global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol::V* __restrict__ totals,
+                                              const typename Pol::V* __restrict__ carries) {
+    typedef typename Pol::V V;
+    constexpr int NCH = 2 << CLSB;
+    constexpr uint32_t CMASK = (1u << CLSB) - 1u;
+    constexpr int MP = MTILE + MTILE / 32;   // padded tile (bank conflicts)
+    __shared__ uint32_t s_key[MP];
+    __shared__ uint32_t s_meta[MP];
+    __shared__ int64_t s_co[6];
+    __shared__ V s_scan[(PHASE == PH_PLAIN) ? 1 : 2 * NCH * (MT / 32)];
+
+    const int64_t n = a.n;
+    const int64_t R2 = (int64_t)2 << a.logR;
+    const int64_t o0 = (int64_t)blockIdx.x * MTILE;
+    if (o0 >= n) return;
+    const MergeTile mt = merge_tile_load(a, s_key, s_meta, s_co);
+    const int64_t ln = mt.ln, lc = mt.lc;
+    const bool big = mt.big;
     if (PHASE == PH_TOTALS) {
         // channel totals of this CTA's inputs (order does not matter)
         V tf[NCH], tb[NCH];
@@ -354,7 +382,7 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
             if (p >= ln) break;
             if (e == 0 || (!big && (p % R2) == 0)) {
                 if (big) { bsl = 0; cl = lc; dl = ln - lc; }
-                else { bsl = (p / R2) * R2; cl = min(R, ln - bsl); dl = min(R2, ln - bsl) - cl; }
+                else { bsl = (p / R2) * R2; cl = min(R2 / 2, ln - bsl); dl = min(R2, ln - bsl) - cl; }
                 MAccP A{s_key, (int)bsl}, B{s_key, (int)(bsl + cl)};
                 i = merge_path(A, cl, B, dl, p - bsl);
                 j = (p - bsl) - i;
@@ -468,6 +496,21 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     }
 }
 
+
+// ------------------------------------------------------------------ folded records
+// Records of the folded kernel sums for the merge levels longer than a tile
+// (structure of arrays, ping-pong): the four factor products F(h, dir)
+// (mantissa, shift; index 2h + dir), the source weight (0: no source role)
+// and the target's sum so far travel with every element, so a level streams
+// its payload instead of gathering it per item, and a target's sum is
+// flushed once, after the last level.
+template <class Pol>
+struct FoldRecs {
+    typename Pol::M* fm;    // [n][4]
+    int* fs;                // [n][4]
+    typename Pol::M* wt;    // [n]
+    typename Pol::FA* fa;   // [n][NW]
+};
 
 // ------------------------------------------------------------------ tile-local levels
 // All merge levels whose merged runs fit in one tile of T items run in shared
@@ -722,7 +765,7 @@ template <class Pol, int CLSB>
 __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
     k_local_fold(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0, ClassSpecK cs,
                  int levels, Pol pol, uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
-                 int write_out) {
+                 int write_out, int rec_out, FoldRecs<Pol> rout) {
     typedef LocalCfg<Pol, CLSB, true> Cfg;
     typedef typename Pol::LOps LO;
     typedef typename LO::V V;          // tile-local sums
@@ -839,14 +882,256 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
             if (e < cnt && pol.is_tgt(em[e] & kItemMask)) Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e]);
         local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
     }
+    // write the tile out for the longer merge levels (as records when they
+    // run on records); targets not handed on as records are flushed
     for (int i = threadIdx.x; i < ln; i += NT) {
         const uint32_t m = s_meta[lpd(i)];
         const uint32_t item = m & kItemMask;
+        const int h = s_home[lpd(i)];
+        const int64_t d = t0 + i;
         if (write_out) {
-            key_out[t0 + i] = s_key[lpd(i)];
-            meta_out[t0 + i] = m;
+            key_out[d] = s_key[lpd(i)];
+            meta_out[d] = m;
         }
-        if (pol.is_tgt(item)) pol.fold_flush(item, s_fa + NW * s_home[lpd(i)]);
+        if (rec_out) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                rout.fm[4 * d + j] = s_fm[4 * h + j];
+                rout.fs[4 * d + j] = s_fs[4 * h + j];
+            }
+            rout.wt[d] = s_wt[h];
+#pragma unroll
+            for (int q = 0; q < NW; ++q) rout.fa[d * NW + q] = s_fa[NW * h + q];
+        } else if (pol.is_tgt(item)) {
+            pol.fold_flush(item, s_fa + NW * h);
+        }
+    }
+}
+
+// Reads element s (factors of half h, weight) and, if d >= 0, copies its
+// factors and weight to slot d of `out`.
+template <class Pol>
+__device__ __forceinline__ void rec_move(const FoldRecs<Pol>& in, int64_t s, const FoldRecs<Pol>& out, int64_t d,
+                                         int h, typename Pol::M& f0, typename Pol::M& f1, int& g0, int& g1,
+                                         typename Pol::M& wt) {
+    if constexpr (sizeof(typename Pol::M) == 4) {
+        const float4 f = reinterpret_cast<const float4*>(in.fm)[s];
+        if (d >= 0) reinterpret_cast<float4*>(out.fm)[d] = f;
+        f0 = h ? f.z : f.x;
+        f1 = h ? f.w : f.y;
+    } else {
+        const double2 fa = reinterpret_cast<const double2*>(in.fm)[2 * s];
+        const double2 fb = reinterpret_cast<const double2*>(in.fm)[2 * s + 1];
+        if (d >= 0) {
+            reinterpret_cast<double2*>(out.fm)[2 * d] = fa;
+            reinterpret_cast<double2*>(out.fm)[2 * d + 1] = fb;
+        }
+        f0 = h ? fb.x : fa.x;
+        f1 = h ? fb.y : fa.y;
+    }
+    const int4 g = reinterpret_cast<const int4*>(in.fs)[s];
+    if (d >= 0) reinterpret_cast<int4*>(out.fs)[d] = g;
+    g0 = h ? g.z : g.x;
+    g1 = h ? g.w : g.y;
+    wt = in.wt[s];
+    if (d >= 0) out.wt[d] = wt;
+}
+
+// Merge level of the folded records.  PH_TOTALS: per-CTA channel totals of
+// the source weights (runs longer than a tile).  PH_SWEEP: merge, payload
+// move and the sweep; each thread walks its elements from zero, the
+// segmented scan over threads and the inter-CTA carries give the prefix /
+// suffix before them, and every target adds the kernel values of its
+// forward and backward sums to its record (flushed on the last level).
+// Resident CTAs per SM asked of the compiler: small channel sums leave room
+// for two (sweep) or three (totals) CTAs without spilling.
+template <class Pol, int CLSB, int PHASE>
+struct FoldOcc {
+    static constexpr size_t bytes = sizeof(typename Pol::V) * (2 << CLSB);
+    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= 64 ? 2 : 1) : (bytes <= 48 ? 2 : 1);
+};
+
+template <class Pol, int CLSB, int PHASE>
+__global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merge_fold(MergeArgs a, FoldRecs<Pol> rin, FoldRecs<Pol> rout, Pol pol,
+                                                   typename Pol::V* __restrict__ totals,
+                                                   const typename Pol::V* __restrict__ carries, int last) {
+    typedef typename Pol::V V;
+    typedef typename Pol::M M;
+    typedef typename Pol::FA FA;
+    constexpr int NW = Pol::kNW;
+    constexpr int NCH = 2 << CLSB;
+    constexpr int MP = MTILE + MTILE / 32;
+    __shared__ uint32_t s_key[MP];
+    __shared__ uint32_t s_meta[MP];
+    __shared__ int64_t s_co[6];
+    __shared__ V s_scan[2 * NCH * (MT / 32)];
+
+    const int64_t n = a.n;
+    const int64_t R2 = (int64_t)2 << a.logR;
+    const int64_t o0 = (int64_t)blockIdx.x * MTILE;
+    if (o0 >= n) return;
+    const MergeTile mt = merge_tile_load(a, s_key, s_meta, s_co);
+    const int64_t ln = mt.ln, lc = mt.lc;
+    const bool big = mt.big;
+
+    if (PHASE == PH_TOTALS) {
+        V tf[NCH], tb[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { tf[c] = Pol::zero(); tb[c] = Pol::zero(); }
+        for (int64_t i = threadIdx.x; i < ln; i += MT) {
+            const uint32_t m = s_meta[mpd(i)];
+            if (pol.is_src(m & kItemMask)) {
+                const int half = (i >= lc) ? 1 : 0;
+                const int64_t g = half ? mt.ds + (i - lc) : mt.cs + i;
+                M f0, f1, wt;
+                int g0, g1;
+                rec_move<Pol>(rin, g, rin, -1, half, f0, f1, g0, g1, wt);
+                const int ch = (half << CLSB) | (int)(m >> kItemBits);
+                add_at<Pol>(tf, ch, Pol::fold_src_g(f0, g0, wt));
+                add_at<Pol>(tb, ch, Pol::fold_src_g(f1, g1, wt));
+            }
+        }
+        V fe[NCH], be[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { fe[c] = tf[c]; be[c] = tb[c]; }
+        seg_scan<Pol, NCH>(fe, be, MT, s_scan);
+        if (threadIdx.x == MT - 1) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) totals[((int64_t)blockIdx.x * 2 + 0) * NCH + c] = Pol::add(fe[c], tf[c]);
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) totals[((int64_t)blockIdx.x * 2 + 1) * NCH + c] = Pol::add(be[c], tb[c]);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- merge
+    uint32_t ek[MI], em[MI];
+    int eh[MI], es[MI];      // half, and the shared-memory slot the element came from
+    int cnt = 0;
+    const int64_t p0 = (int64_t)threadIdx.x * MI;
+    {
+        int64_t bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
+        for (int e = 0; e < MI; ++e) {
+            const int64_t p = p0 + e;
+            if (p >= ln) break;
+            if (e == 0 || (!big && (p % R2) == 0)) {
+                if (big) { bsl = 0; cl = lc; dl = ln - lc; }
+                else { bsl = (p / R2) * R2; cl = min(R2 / 2, ln - bsl); dl = min(R2, ln - bsl) - cl; }
+                MAccP A{s_key, (int)bsl}, B{s_key, (int)(bsl + cl)};
+                i = merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+            }
+            const bool takeC = (i < cl) && (j >= dl || s_key[mpd(bsl + i)] <= s_key[mpd(bsl + cl + j)]);
+            const int slot = (int)(takeC ? bsl + i : bsl + cl + j);
+            ek[e] = s_key[mpd(slot)];
+            em[e] = s_meta[mpd(slot)];
+            eh[e] = takeC ? 0 : 1;
+            es[e] = slot;
+            if (takeC) ++i; else ++j;
+            cnt = e + 1;
+        }
+    }
+    if (!last) {
+        const int64_t q0 = o0 + p0;
+        if (cnt == MI) {
+            uint4* kk = reinterpret_cast<uint4*>(a.key_out + q0);
+            uint4* mm = reinterpret_cast<uint4*>(a.meta_out + q0);
+            kk[0] = make_uint4(ek[0], ek[1], ek[2], ek[3]);
+            kk[1] = make_uint4(ek[4], ek[5], ek[6], ek[7]);
+            mm[0] = make_uint4(em[0], em[1], em[2], em[3]);
+            mm[1] = make_uint4(em[4], em[5], em[6], em[7]);
+        } else {
+            for (int e = 0; e < cnt; ++e) { a.key_out[q0 + e] = ek[e]; a.meta_out[q0 + e] = em[e]; }
+        }
+    }
+    // global position of the element held in shared-memory slot q
+    auto gpos = [&](int q) -> int64_t {
+        return big ? (q < lc ? mt.cs + q : mt.ds + (q - lc)) : o0 + q;
+    };
+    // payload move; the factors of the element's half stay in registers
+    M f0[MI], f1[MI], wt[MI];
+    int g0[MI], g1[MI];
+#pragma unroll
+    for (int e = 0; e < MI; ++e) {
+        f0[e] = f1[e] = wt[e] = (M)0;
+        g0[e] = g1[e] = 0;
+        if (e < cnt)
+            rec_move<Pol>(rin, gpos(es[e]), rout, last ? -1 : o0 + p0 + e, eh[e], f0[e], f1[e], g0[e], g1[e], wt[e]);
+    }
+    // walks from zero over the thread's elements
+    const int ts = big ? MT : (int)(R2 / MI);   // threads per merged block (0/1: thread-local)
+    M cf[MI][NW], cb[MI][NW];
+    V fe[NCH], be[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) { fe[c] = Pol::zero(); be[c] = Pol::zero(); }
+#pragma unroll
+    for (int e = 0; e < MI; ++e) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
+        if (e < cnt) {
+            if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) fe[c] = Pol::zero();
+            }
+            const int own = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
+            Pol::fold_value_g(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
+            add_at<Pol>(fe, own, Pol::fold_src_g(f0[e], g0[e], wt[e]));
+        }
+    }
+#pragma unroll
+    for (int e = MI - 1; e >= 0; --e) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) cb[e][q] = (M)0;
+        if (e < cnt) {
+            if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) be[c] = Pol::zero();
+            }
+            const int own = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
+            Pol::fold_value_g(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
+            add_at<Pol>(be, own, Pol::fold_src_g(f1[e], g1[e], wt[e]));
+        }
+    }
+    if (ts > 1) {
+        seg_scan<Pol, NCH>(fe, be, ts, s_scan);
+        if (big && carries) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                fe[c] = Pol::add(carries[((int64_t)blockIdx.x * 2 + 0) * NCH + c], fe[c]);
+                be[c] = Pol::add(be[c], carries[((int64_t)blockIdx.x * 2 + 1) * NCH + c]);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < MI; ++e) {
+            if (e < cnt) {
+                const int opp = ((eh[e] << CLSB) | (int)(em[e] >> kItemBits)) ^ (NCH - 1);
+                M xf[NW], xb[NW];
+                Pol::fold_value_g(pick(fe, opp), f1[e], g1[e], xf);
+                Pol::fold_value_g(pick(be, opp), f0[e], g0[e], xb);
+#pragma unroll
+                for (int q = 0; q < NW; ++q) { cf[e][q] += xf[q]; cb[e][q] += xb[q]; }
+            }
+        }
+    }
+    // target sums: read, add this level's kernel values, write on (or flush)
+#pragma unroll
+    for (int e = 0; e < MI; ++e) {
+        if (e < cnt) {
+            const uint32_t item = em[e] & kItemMask;
+            const int64_t src = gpos(es[e]);
+            FA acc[NW];
+#pragma unroll
+            for (int q = 0; q < NW; ++q) acc[q] = rin.fa[src * NW + q];
+            if (pol.is_tgt(item)) Pol::fold_add(acc, cf[e], cb[e]);
+            if (!last) {
+#pragma unroll
+                for (int q = 0; q < NW; ++q) rout.fa[(o0 + p0 + e) * NW + q] = acc[q];
+            } else if (pol.is_tgt(item)) {
+                pol.fold_flush(item, acc);
+            }
+        }
     }
 }
 

@@ -53,6 +53,7 @@ struct PolCount : ItemMap {
     static constexpr int kLocalT = 4096;
     static constexpr bool kUnitWeights = true;
     static constexpr bool kCanFold = false;      // sums stay per orthant
+    static constexpr bool kRecords = false;
     static constexpr int kFoldT = kLocalT, kNW = 1;
     typedef float M;
     typedef float FA;
@@ -89,6 +90,7 @@ struct PolW64 : ItemMap {
     static constexpr int kLocalT = 2048;
     static constexpr bool kUnitWeights = false;
     static constexpr bool kCanFold = false;      // sums stay per orthant
+    static constexpr bool kRecords = false;
     static constexpr int kFoldT = kLocalT, kNW = 1;
     typedef float M;
     typedef float FA;
@@ -128,6 +130,7 @@ struct PolWFF : ItemMap {
     static constexpr int kLocalT = 2048;
     static constexpr bool kUnitWeights = false;
     static constexpr bool kCanFold = false;      // sums stay per orthant
+    static constexpr bool kRecords = false;
     static constexpr int kFoldT = kLocalT, kNW = 1;
     typedef float M;
     typedef float FA;
@@ -222,6 +225,7 @@ struct PolKF : ItemMap {
     // folded local form (targets turn their sums into kernel values)
     static constexpr bool kCanFold = true;
     static constexpr int kFoldT = NW == 1 ? 4096 : 2048, kNW = NW;
+    static constexpr bool kRecords = true;    // longer levels on streamed records
     typedef float M;
     typedef FF FA;
     // Tile-local running sums and scans: plain FP32 mantissa with a shift.
@@ -258,6 +262,17 @@ struct PolKF : ItemMap {
     __device__ static void fold_add(FA* a, const float* cf, const float* cb) {
 #pragma unroll
         for (int i = 0; i < NW; ++i) a[i] = ff_add_f(ff_add_f(a[i], cf[i]), cb[i]);
+    }
+    // the same for the compensated sums of the longer merge levels
+    __device__ static V fold_src_g(float m, int s, float wt) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = sff_term(((NW == 2 && i == 1) ? 1.f : wt) * m, s);
+        return r;
+    }
+    __device__ static void fold_value_g(const V& v, float m, int s, float* c) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) c[i] = (v.v[i].hi + v.v[i].lo) * m * pow2f_any(v.v[i].e + s);
     }
     // the four products B E1^{h} E0^{dir} (index 2h + dir) and the weight
     __device__ void fold_item(uint32_t item, uint32_t cls, float* fm, int* fs, float& wt) const {
@@ -419,6 +434,9 @@ struct PolKD : ItemMap {
     // folded local form (targets turn their sums into kernel values)
     static constexpr bool kCanFold = true;
     static constexpr int kFoldT = NW == 1 ? 2048 : 1024, kNW = NW;
+    // longer levels gather the factors per item (measured faster on the FP64
+    // path, whose cost is FP64 arithmetic rather than memory latency)
+    static constexpr bool kRecords = false;
     typedef double M;
     typedef double FA;
     struct LOps {   // tile-local sums: the same shifted FP64 values
@@ -441,6 +459,8 @@ struct PolKD : ItemMap {
 #pragma unroll
         for (int i = 0; i < NW; ++i) a[i] += cf[i] + cb[i];
     }
+    __device__ static V fold_src_g(double m, int s, double wt) { return fold_src(m, s, wt); }
+    __device__ static void fold_value_g(const V& v, double m, int s, double* c) { fold_value(v, m, s, c); }
     __device__ void fold_item(uint32_t item, uint32_t cls, double* fm, int* fs, double& wt) const {
         const BaseD B = base_of(item, cls);
         const FacD e1 = fac[(int64_t)1 * n_items + item];
@@ -558,7 +578,14 @@ struct DCBuffers {
     uint32_t* m[2];   // inner sort ping-pong metas
     void* totals;
     void* carries;
+    // folded kernel sums: record arrays (fm, fs, wt, fa) of each ping-pong side
+    void* rec[2][4];
 };
+template <class Pol>
+FoldRecs<Pol> fold_recs(const DCBuffers& b, int q) {
+    return FoldRecs<Pol>{(typename Pol::M*)b.rec[q][0], (int*)b.rec[q][1], (typename Pol::M*)b.rec[q][2],
+                         (typename Pol::FA*)b.rec[q][3]};
+}
 
 // host-side common pieces (fk_dc_common.cu)
 fk_status plain_merge_level(const MergeArgs& a, cudaStream_t st);
@@ -581,20 +608,65 @@ fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0
     L0 = E < lt ? E : lt;
     constexpr size_t smem = Cfg::bytes;
     static_assert(smem <= 227 * 1024, "tile does not fit in shared memory");
-    void (*kern)(const uint32_t*, int64_t, const uint32_t*, ClassSpecK, int, Pol, uint32_t*, uint32_t*, int);
-    if constexpr (FOLD) kern = k_local_fold<Pol, CLSB>;
-    else kern = k_local_sweep<Pol, CLSB>;
     static bool attr_set = false;
     if (!attr_set) {
-        FK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if constexpr (FOLD)
+            FK_CUDA(cudaFuncSetAttribute(k_local_fold<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        else
+            FK_CUDA(cudaFuncSetAttribute(k_local_sweep<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
         attr_set = true;
     }
     const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
                           (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes) + (E > L0 ? 8.0 * n : 0.0);
     ProfScope ps(Pol::kCanFold ? PF_KLOCAL : PF_LOCAL,
                  Pol::kCanFold ? (double)n * L0 * kKernelOpsPerItemLevel : lbytes, st);
-    kern<<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(seq, n, P0, cs, L0, pol, b.k[0], b.m[0], E > L0 ? 1 : 0);
+    if constexpr (FOLD)
+        k_local_fold<Pol, CLSB><<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(
+            seq, n, P0, cs, L0, pol, b.k[0], b.m[0], E > L0 ? 1 : 0, (E > L0 && Pol::kRecords) ? 1 : 0,
+            fold_recs<Pol>(b, 0));
+    else
+        k_local_sweep<Pol, CLSB><<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(seq, n, P0, cs, L0, pol, b.k[0], b.m[0],
+                                                                           E > L0 ? 1 : 0);
     FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
+// Merge levels L0..E-1 of the folded kernel sums on records.
+template <class Pol, int CLSB>
+fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cudaStream_t st) {
+    typedef typename Pol::V V;
+    constexpr int NCH = 2 << CLSB;
+    const unsigned ctas = grid_for(n, MTILE);
+    // algorithmic bytes of one level: key, meta and the record in and out
+    const double rec_bytes = 8.0 + 8.0 * sizeof(typename Pol::M) + 16.0 + Pol::kNW * sizeof(typename Pol::FA);
+    int cur = 0;
+    for (int m = L0; m < E; ++m) {
+        MergeArgs a{b.k[cur], b.m[cur], b.k[cur ^ 1], b.m[cur ^ 1], n, m};
+        const FoldRecs<Pol> rin = fold_recs<Pol>(b, cur), rout = fold_recs<Pol>(b, cur ^ 1);
+        const int last = (m == E - 1) ? 1 : 0;
+        const int64_t R2 = (int64_t)2 << m;
+        const V* carries = nullptr;
+        if (R2 > MTILE) {
+            {
+                ProfScope ps(PF_MERGE_TOTALS, (rec_bytes - Pol::kNW * sizeof(typename Pol::FA)) * n, st);
+                k_merge_fold<Pol, CLSB, PH_TOTALS><<<ctas, MT, 0, st>>>(a, rin, rout, pol, (V*)b.totals, nullptr,
+                                                                       last);
+                FK_LAUNCH_CHECK();
+            }
+            const int64_t per = R2 / MTILE;
+            const int64_t nblk = ((int64_t)ctas + per - 1) / per;
+            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2, 128), 128, 0, st>>>((const V*)b.totals,
+                                                                              (V*)b.carries, n, m);
+            FK_LAUNCH_CHECK();
+            carries = (const V*)b.carries;
+        }
+        ProfScope ps(PF_MERGE_SWEEP, rec_bytes * n * (last ? 0.5 : 1.0) + (last ? 8.0 * pol.n_tgt : 0.0), st);
+        k_merge_fold<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, rin, rout, pol, nullptr, carries, last);
+        FK_LAUNCH_CHECK();
+        cur ^= 1;
+    }
     return FK_OK;
 }
 
@@ -606,8 +678,12 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
     // tile-local levels (gather fused into the tile load)
     int L0 = 0;
     if constexpr (Pol::kCanFold) {
-        if (!pol.terms) FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, st)));
-        else FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
+        if (!pol.terms) {
+            FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, st)));
+            if constexpr (Pol::kRecords) return fold_levels<Pol, CLSB>(n, E, L0, pol, b, st);
+        } else {
+            FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
+        }
     } else {
         FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
     }
@@ -698,6 +774,16 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
     const int64_t ctas = (n + MTILE - 1) / MTILE;
     ib.totals = ar.take<V>((size_t)ctas * 2 * NCH);
     ib.carries = ar.take<V>((size_t)ctas * 2 * NCH);
+    for (int q = 0; q < 2; ++q)
+        for (int j = 0; j < 4; ++j) ib.rec[q][j] = nullptr;
+    if constexpr (Pol::kCanFold && Pol::kRecords) {
+        for (int q = 0; q < 2; ++q) {
+            ib.rec[q][0] = ar.take<typename Pol::M>((size_t)4 * n);
+            ib.rec[q][1] = ar.take<int>((size_t)4 * n);
+            ib.rec[q][2] = ar.take<typename Pol::M>((size_t)n);
+            ib.rec[q][3] = ar.take<typename Pol::FA>((size_t)Pol::kNW * n);
+        }
+    }
     if (ar.sizing) return FK_OK;
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (dominance sweep)");
     if (n <= 1) return FK_OK;
