@@ -63,10 +63,11 @@ def _load():
     lib.fko_kreg.argtypes = [P, I64, I, P, P, I64, P, I, P, I]
     lib.fko_kde_grad.argtypes = [P, I64, I, P, P, I64, P, I, P, P, P, P, I]
     lib.fko_loo_loglik.argtypes = [P, I64, I, P, P, P, P, I]
+    lib.fko_kde_at.argtypes = [P, I64, I, P, P, I64, P, I, P, I]
     lib.fko_fenwick2d.argtypes = [P, I64, P, I64, P]
     lib.fko_max_threads.argtypes = []
     for f in (lib.fko_orthant_sums, lib.fko_kde, lib.fko_kreg, lib.fko_kde_grad,
-              lib.fko_loo_loglik, lib.fko_fenwick2d, lib.fko_max_threads):
+              lib.fko_loo_loglik, lib.fko_fenwick2d, lib.fko_max_threads, lib.fko_kde_at):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -173,6 +174,23 @@ def kde_laplace(x, h, w=None, z=None, loo=False, terms=False, threads=0):
                          int(bool(loo)), _ptr(out), _ptr(tt), int(threads))
     _check(rc)
     return (out, tt) if terms else out
+
+
+def kde_at_points(x, h, idx, w=None, loo=False, threads=0):
+    """eq. (Laplacian kde nD) at the sample points x[idx]; with ``loo`` the
+    leave-one-out density f_{-j} (drops exactly source idx[j], normalises by
+    N-1)."""
+    x = np.asarray(x)
+    d = x.shape[1] if x.ndim == 2 else 1
+    x = _f64(x, d)
+    hh = _f64(np.broadcast_to(np.asarray(h, dtype=np.float64), (d,)))
+    ii = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).reshape(-1))
+    out = np.zeros(ii.shape[0], dtype=np.float64)
+    ww = None if w is None else _f64(w).reshape(-1)
+    rc = _load().fko_kde_at(_ptr(x), x.shape[0], d, _ptr(ww), _ptr(ii), ii.shape[0], _ptr(hh),
+                            int(bool(loo)), _ptr(out), int(threads))
+    _check(rc)
+    return out
 
 
 def kreg_laplace(x, y, h, z=None, loo=False, threads=0):

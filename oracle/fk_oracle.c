@@ -198,6 +198,34 @@ int fko_kde(const double* x, int64_t n, int d, const double* w, const double* z,
 }
 
 /*
+ * The same KDE at a subset of the sample points: target j is x[idx[j]]; with
+ * loo != 0 exactly the source i == idx[j] is dropped and the normalisation is
+ * N-1 (the leave-one-out density f_{-j} of the bandwidth likelihood), so that
+ * large-N checks can sample targets instead of evaluating all N.
+ */
+int fko_kde_at(const double* x, int64_t n, int d, const double* w, const int64_t* idx,
+               int64_t m, const double* h, int loo, double* out, int nthreads) {
+    if (d < 1 || d > 12 || n < 0 || m < 0) return FKO_EINVAL;
+    for (int k = 0; k < d; ++k) if (!(h[k] > 0.0)) return FKO_EINVAL;
+    for (int64_t j = 0; j < m; ++j) if (idx[j] < 0 || idx[j] >= n) return FKO_EINVAL;
+    int64_t nn = loo ? n - 1 : n;
+    if (nn <= 0) { for (int64_t j = 0; j < m; ++j) out[j] = 0.0; return FKO_OK; }
+    const double cst = kde_const(nn, d, h);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        const double* zj = x + idx[j] * d;
+        neum_t acc = {0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) {
+            if (loo && i == idx[j]) continue;
+            neum_add(&acc, (w ? w[i] : 1.0) * exp(-l1h(x + i * d, zj, h, d)));
+        }
+        out[j] = cst * neum_get(&acc);
+    }
+    return FKO_OK;
+}
+
+/*
  * Nadaraya-Watson regression with the Laplacian kernel:
  *   m(z_j) = sum_i y_i K_ij / sum_i K_ij,  K_ij = exp(-(a_ij - min_i a_ij)),
  *   a_ij = sum_k |x_ik - z_jk| / h_k.

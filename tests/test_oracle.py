@@ -269,6 +269,28 @@ def test_kde_loo_drops_exactly_self():
     np.testing.assert_allclose(f, [c * (1 + e(-3)), c * (1 + e(-3)), c * 2 * e(-3)], rtol=1e-15)
 
 
+def test_kde_at_sampled_points_closed_form():
+    """KDE at a subset of the sample points, with and without leave-one-out,
+    on the five tie points (h = (0.5, 1)), expanded by hand: the LOO constant
+    is 1/(4*(5-1)*0.5*1) = 1/8 and only index idx[j] itself is dropped (the
+    duplicate (1,1) stays); weights w = 1..5 scale each term."""
+    g = _read_tie_golden()
+    x = np.array(g["points"])
+    e = math.exp
+    h = [0.5, 1.0]
+    idx = [3, 0, 3, 4]
+    loo = oracle.kde_at_points(x, h, idx, loo=True)
+    np.testing.assert_allclose(loo, [(e(-3) + e(-1) + e(-2) + 1) / 8, (e(-2) + e(-1) + 2 * e(-3)) / 8,
+                                     (e(-3) + e(-1) + e(-2) + 1) / 8, (e(-3) + e(-1) + e(-2) + 1) / 8],
+                               rtol=1e-15)
+    full = oracle.kde_at_points(x, h, [0, 2])
+    np.testing.assert_allclose(full, [(1 + e(-2) + e(-1) + 2 * e(-3)) / 10, (e(-1) + e(-3) + 1 + 2 * e(-2)) / 10],
+                               rtol=1e-15)
+    w = np.arange(1.0, 6.0)
+    lw = oracle.kde_at_points(x, h, [3], w=w, loo=True)
+    assert lw[0] == pytest.approx((1 * e(-3) + 2 * e(-1) + 3 * e(-2) + 5 * 1) / 8, rel=1e-15)
+
+
 def test_kreg_constant_and_ratio():
     """NW: constant y gives that constant; in general m = kde(w=y) / kde(w=1)."""
     r = np.random.default_rng(9)
