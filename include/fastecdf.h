@@ -233,6 +233,56 @@ fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xdtype, unsigne
                      fk_stream_t stream);
 
 /*
+ * Launch configuration of fk_batched (a tuning knob, not part of the paper's
+ * problem; results agree across configurations within the stated tolerances,
+ * counts exactly):
+ *   streams     groups run concurrently on this many streams (1..8): the
+ *               caller's stream and library-owned streams forked from it and
+ *               joined back to it with events (so the call stays capturable in
+ *               a CUDA graph); each stream gets its own workspace slot.
+ *               Overlapping calls from several host threads are serialised
+ *               while they enqueue.
+ *   coarsen     datasets are grouped by dimension and padded size 2^E with E
+ *               rounded up to a multiple of coarsen + 1 (0..2): fewer, larger
+ *               launches against more padding.
+ *   kernel_tile 0: default tile of the tile-local kernel-sum levels (4096
+ *               items mixed, 2048 FP64), 1: half of it.
+ *   count_tile  tile of the tile-local counting levels: 0: 2048, 1: 1024,
+ *               2: 4096 items.
+ * fk_batched uses fk_batched_config_default (1, 0, 0, 0).
+ */
+typedef struct {
+    int streams;
+    int coarsen;
+    int kernel_tile;
+    int count_tile;
+} fk_batch_config;
+
+void fk_batched_config_default(fk_batch_config* cfg);
+size_t fk_batched_workspace_ex(const fk_dataset* sets, int count, fk_dtype xdtype, unsigned what, fk_path path,
+                               const fk_batch_config* cfg);
+fk_status fk_batched_ex(const fk_dataset* sets, int count, fk_dtype xdtype, unsigned what, double h,
+                        int64_t* ecdf_out, double* kde_out, fk_path path, const fk_batch_config* cfg, void* ws,
+                        size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_batched_autotune -- picks the configuration by measurement on the
+ * caller's own datasets: coordinate descent over streams {1, 2, 4, 8},
+ * coarsen {0, 1, 2}, count_tile {0, 1, 2} (with FK_BATCH_ECDF) and
+ * kernel_tile {0, 1} (with FK_BATCH_KDE), each candidate run once to warm up
+ * and timed as the best of two runs with CUDA events on `stream`.  The call
+ * synchronises the stream (it cannot be captured) and leaves the outputs of
+ * the last run in ecdf_out / kde_out.  ws: NULL (allocated per trial) or at
+ * least fk_batched_autotune_workspace bytes (the largest candidate's need).
+ * best receives the fastest configuration, best_ms (optional) its time.
+ */
+size_t fk_batched_autotune_workspace(const fk_dataset* sets, int count, fk_dtype xdtype, unsigned what,
+                                     fk_path path);
+fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xdtype, unsigned what, double h,
+                              int64_t* ecdf_out, double* kde_out, fk_path path, void* ws, size_t ws_bytes,
+                              fk_stream_t stream, fk_batch_config* best, double* best_ms);
+
+/*
  * fk_ecdf_grid_counts_noalloc -- the paper has no counterpart to this call; it
  * exists for callers that may not allocate device memory while they run: loops
  * that forbid allocation after start-up (cudaMalloc can synchronise the device

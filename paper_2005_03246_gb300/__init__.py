@@ -369,9 +369,14 @@ class Batched:
     [N_b] tensors or None.  With graph=True the call is captured once in a CUDA
     graph and ``run()`` replays it (the input tensors must keep their storage).
     ``run()`` returns (ecdf, kde): lists of per-dataset views [2^d_b, N_b] int64
-    and [N_b] float64 (None for the part not requested)."""
+    and [N_b] float64 (None for the part not requested).
 
-    def __init__(self, xs, ys=None, h=0.1, ecdf=True, kde=True, path="mixed", graph=True):
+    config: a dict of fk_batch_config fields (streams, coarsen, kernel_tile,
+    count_tile), "tune" to let fk_batched_autotune choose it by measurement on
+    these datasets, or None for the default; ``self.config`` holds the one
+    used (and ``self.tune_ms`` the tuned time)."""
+
+    def __init__(self, xs, ys=None, h=0.1, ecdf=True, kde=True, path="mixed", graph=True, config=None):
         torch = _torch()
         lib = _lib.load()
         if not xs:
@@ -405,7 +410,26 @@ class Batched:
         self.ecdf_out = torch.empty(max(ne, 1), dtype=torch.int64, device=dev) if ecdf else None
         self.kde_out = torch.empty(max(nk, 1), dtype=torch.float64, device=dev) if kde else None
         self.dtype_code = _dtype_code(dt)
-        need = lib.fk_batched_workspace(self.sets, n, self.dtype_code, self.what, self.path)
+        self.cfg = _lib.BatchConfig()
+        lib.fk_batched_config_default(ctypes.byref(self.cfg))
+        self.tune_ms = None
+        if config == "tune":
+            need = lib.fk_batched_autotune_workspace(self.sets, n, self.dtype_code, self.what, self.path)
+            tws, twsb = _workspace(need, dev)
+            ms = ctypes.c_double(0.0)
+            rc = lib.fk_batched_autotune(self.sets, n, self.dtype_code, self.what, self.h, _ptr(self.ecdf_out),
+                                         _ptr(self.kde_out), self.path, _ptr(tws), twsb, _stream_ptr(dev),
+                                         ctypes.byref(self.cfg), ctypes.byref(ms))
+            _lib.check(rc, "fk_batched_autotune")
+            self.tune_ms = ms.value
+            del tws
+        elif config is not None:
+            for k, v in dict(config).items():
+                setattr(self.cfg, k, int(v))
+        self.config = self.cfg.as_dict()
+        need = lib.fk_batched_workspace_ex(self.sets, n, self.dtype_code, self.what, self.path, ctypes.byref(self.cfg))
+        if need == 0 and n > 0:
+            _lib.check(-1, "fk_batched_workspace_ex")
         self.ws, self.wsb = _workspace(need, dev)
         self.graph = None
         self._call()                         # warm-up (sets kernel attributes, checks errors)
@@ -418,9 +442,10 @@ class Batched:
 
     def _call(self):
         lib = _lib.load()
-        rc = lib.fk_batched(self.sets, len(self.xs), self.dtype_code, self.what, self.h, _ptr(self.ecdf_out),
-                            _ptr(self.kde_out), self.path, _ptr(self.ws), self.wsb, _stream_ptr(self.dev))
-        _lib.check(rc, "fk_batched")
+        rc = lib.fk_batched_ex(self.sets, len(self.xs), self.dtype_code, self.what, self.h, _ptr(self.ecdf_out),
+                               _ptr(self.kde_out), self.path, ctypes.byref(self.cfg), _ptr(self.ws), self.wsb,
+                               _stream_ptr(self.dev))
+        _lib.check(rc, "fk_batched_ex")
 
     def run(self):
         if self.graph is not None:

@@ -21,6 +21,15 @@ class Dataset(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int),
                 ("reserved", ctypes.c_int)]
 
+class BatchConfig(ctypes.Structure):
+    """fk_batch_config of include/fastecdf.h."""
+    _fields_ = [("streams", ctypes.c_int), ("coarsen", ctypes.c_int), ("kernel_tile", ctypes.c_int),
+                ("count_tile", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 STATUS = {0: "FK_OK", -1: "FK_ERR_INVALID_ARG", -2: "FK_ERR_UNSUPPORTED", -3: "FK_ERR_WORKSPACE",
           -4: "FK_ERR_NONFINITE", -5: "FK_ERR_CUDA", -6: "FK_ERR_TIMEOUT"}
 
@@ -45,6 +54,11 @@ SIGNATURES = {
     "fk_loo_laplace": (I, [P, I, I64, I, P, P, P, P, I, P, SZ, P]),
     "fk_batched_workspace": (SZ, [P, I, I, U, I]),
     "fk_batched": (I, [P, I, I, U, ctypes.c_double, P, P, I, P, SZ, P]),
+    "fk_batched_config_default": (None, [P]),
+    "fk_batched_workspace_ex": (SZ, [P, I, I, U, I, P]),
+    "fk_batched_ex": (I, [P, I, I, U, ctypes.c_double, P, P, I, P, P, SZ, P]),
+    "fk_batched_autotune_workspace": (SZ, [P, I, I, U, I]),
+    "fk_batched_autotune": (I, [P, I, I, U, ctypes.c_double, P, P, I, P, SZ, P, P, P]),
     "fk_ecdf_grid_counts_noalloc": (I, [P, I, I64, I, P, P, P, P, P]),
     "fk_kernel_launches": (ctypes.c_uint64, []),
     "fk_profile_enable": (None, [I]),

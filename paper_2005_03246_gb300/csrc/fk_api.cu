@@ -1,5 +1,6 @@
 // fk_api.cu -- extern "C" entry points of fastecdf.h: argument validation,
 // host/device staging of the caller's arrays, workspace handling, dispatch.
+#include <algorithm>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -18,7 +19,7 @@ fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, c
                   double* gh, fk_path path, Arena& ar, cudaStream_t st);
 
 fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
-                      double* kde_out, fk_path path, Arena& ar, cudaStream_t st);
+                      double* kde_out, fk_path path, const BatchCfg& cfg, Arena& ar, cudaStream_t st);
 
 static thread_local char g_msg[512] = "no error";
 
@@ -536,16 +537,50 @@ static fk_status batched_validate(const fk_dataset* sets, int count, fk_dtype xd
     return FK_OK;
 }
 
-size_t fk_batched_workspace(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path) {
-    if (batched_validate(sets, count, xd, what, path) != FK_OK) return 0;
+static fk_status batch_cfg(const fk_batch_config* c, BatchCfg& out) {
+    out = BatchCfg{};
+    if (!c) return FK_OK;
+    if (c->streams < 1 || c->streams > 8) return set_error(FK_ERR_INVALID_ARG, "streams must be 1..8");
+    if (c->coarsen < 0 || c->coarsen > 2) return set_error(FK_ERR_INVALID_ARG, "coarsen must be 0..2");
+    if (c->kernel_tile < 0 || c->kernel_tile > 1) return set_error(FK_ERR_INVALID_ARG, "kernel_tile must be 0 or 1");
+    if (c->count_tile < 0 || c->count_tile > 2) return set_error(FK_ERR_INVALID_ARG, "count_tile must be 0..2");
+    out.streams = c->streams;
+    out.coarsen = c->coarsen;
+    out.kernel_tile = c->kernel_tile;
+    out.count_tile = c->count_tile;
+    return FK_OK;
+}
+
+static size_t batched_plan(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path,
+                           const BatchCfg& c) {
     Arena ar;
-    batched_run(sets, count, xd, what, 1.0, nullptr, nullptr, path, ar, 0);
+    batched_run(sets, count, xd, what, 1.0, nullptr, nullptr, path, c, ar, 0);
     return ar.used;
 }
 
-fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
-                     double* kde_out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
-    cudaStream_t st = (cudaStream_t)stream;
+void fk_batched_config_default(fk_batch_config* cfg) {
+    if (!cfg) return;
+    const BatchCfg d;
+    cfg->streams = d.streams;
+    cfg->coarsen = d.coarsen;
+    cfg->kernel_tile = d.kernel_tile;
+    cfg->count_tile = d.count_tile;
+}
+
+size_t fk_batched_workspace_ex(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path,
+                               const fk_batch_config* cfg) {
+    BatchCfg c;
+    if (batch_cfg(cfg, c) != FK_OK) return 0;
+    if (batched_validate(sets, count, xd, what, path) != FK_OK) return 0;
+    return batched_plan(sets, count, xd, what, path, c);
+}
+
+size_t fk_batched_workspace(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path) {
+    return fk_batched_workspace_ex(sets, count, xd, what, path, nullptr);
+}
+
+static fk_status batched_check(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h,
+                               int64_t* ecdf_out, double* kde_out, fk_path path) {
     FK_TRY(batched_validate(sets, count, xd, what, path));
     if ((what & FK_BATCH_KDE) && !(h > 0.0 && h < 1e300)) return set_error(FK_ERR_INVALID_ARG, "h must be > 0");
     if ((what & FK_BATCH_ECDF) && !ecdf_out) return set_error(FK_ERR_INVALID_ARG, "ecdf_out is NULL");
@@ -555,12 +590,112 @@ fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xd, unsigned wh
             return set_error(FK_ERR_INVALID_ARG, "fk_batched needs device pointers (dataset %d)", b);
     if ((ecdf_out && !is_device_pointer(ecdf_out)) || (kde_out && !is_device_pointer(kde_out)))
         return set_error(FK_ERR_INVALID_ARG, "fk_batched needs device output pointers");
-    Arena plan;
-    batched_run(sets, count, xd, what, h, nullptr, nullptr, path, plan, st);
+    return FK_OK;
+}
+
+fk_status fk_batched_ex(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
+                        double* kde_out, fk_path path, const fk_batch_config* cfg, void* ws, size_t ws_bytes,
+                        fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchCfg c;
+    FK_TRY(batch_cfg(cfg, c));
+    FK_TRY(batched_check(sets, count, xd, what, h, ecdf_out, kde_out, path));
+    const size_t need = batched_plan(sets, count, xd, what, path, c);
     Workspace wsp(st);
     Arena ar;
-    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
-    return batched_run(sets, count, xd, what, h, ecdf_out, kde_out, path, ar, st);
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, need));
+    return batched_run(sets, count, xd, what, h, ecdf_out, kde_out, path, c, ar, st);
+}
+
+fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
+                     double* kde_out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    return fk_batched_ex(sets, count, xd, what, h, ecdf_out, kde_out, path, nullptr, ws, ws_bytes, stream);
+}
+
+// The autotuner's candidate values per dimension.
+static const int kTuneStreams[] = {1, 2, 4, 8};
+static const int kTuneCoarsen[] = {0, 1, 2};
+static const int kTuneCountTile[] = {0, 1, 2};
+static const int kTuneKernelTile[] = {0, 1};
+
+size_t fk_batched_autotune_workspace(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, fk_path path) {
+    if (batched_validate(sets, count, xd, what, path) != FK_OK) return 0;
+    size_t mx = 0;
+    BatchCfg c;
+    for (int s : kTuneStreams)
+        for (int co : kTuneCoarsen)
+            for (int ct : kTuneCountTile)
+                for (int kt : kTuneKernelTile) {
+                    c.streams = s;
+                    c.coarsen = co;
+                    c.count_tile = ct;
+                    c.kernel_tile = kt;
+                    mx = std::max(mx, batched_plan(sets, count, xd, what, path, c));
+                }
+    return mx;
+}
+
+fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h,
+                              int64_t* ecdf_out, double* kde_out, fk_path path, void* ws, size_t ws_bytes,
+                              fk_stream_t stream, fk_batch_config* best, double* best_ms) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!best) return set_error(FK_ERR_INVALID_ARG, "best is NULL");
+    FK_TRY(batched_check(sets, count, xd, what, h, ecdf_out, kde_out, path));
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    FK_CUDA(cudaEventCreate(&ea));
+    FK_CUDA(cudaEventCreate(&eb));
+    // one candidate: warm-up run, then the best of two timed runs
+    auto trial = [&](const BatchCfg& c, double* ms) -> fk_status {
+        const size_t need = batched_plan(sets, count, xd, what, path, c);
+        Workspace wsp(st);
+        Arena ar;
+        FK_TRY(wsp.bind(ar, ws, ws_bytes, need));
+        FK_TRY(batched_run(sets, count, xd, what, h, ecdf_out, kde_out, path, c, ar, st));
+        double bestt = 1e300;
+        for (int r = 0; r < 2; ++r) {
+            ar.used = 0;
+            FK_CUDA(cudaEventRecord(ea, st));
+            FK_TRY(batched_run(sets, count, xd, what, h, ecdf_out, kde_out, path, c, ar, st));
+            FK_CUDA(cudaEventRecord(eb, st));
+            FK_CUDA(cudaEventSynchronize(eb));
+            float t = 0.f;
+            FK_CUDA(cudaEventElapsedTime(&t, ea, eb));
+            bestt = std::min(bestt, (double)t);
+        }
+        *ms = bestt;
+        return FK_OK;
+    };
+    BatchCfg cur;
+    double cur_ms = 0.0;
+    fk_status rc = trial(cur, &cur_ms);
+    // coordinate descent, one dimension at a time
+    auto descend = [&](int BatchCfg::*field, const int* vals, int nv) {
+        const int start = cur.*field;
+        for (int i = 0; i < nv && rc == FK_OK; ++i) {
+            if (vals[i] == start) continue;
+            BatchCfg c = cur;
+            c.*field = vals[i];
+            double ms = 0.0;
+            rc = trial(c, &ms);
+            if (rc == FK_OK && ms < cur_ms) {
+                cur = c;
+                cur_ms = ms;
+            }
+        }
+    };
+    if (rc == FK_OK) descend(&BatchCfg::streams, kTuneStreams, 4);
+    if (rc == FK_OK) descend(&BatchCfg::coarsen, kTuneCoarsen, 3);
+    if (rc == FK_OK && (what & FK_BATCH_ECDF)) descend(&BatchCfg::count_tile, kTuneCountTile, 3);
+    if (rc == FK_OK && (what & FK_BATCH_KDE)) descend(&BatchCfg::kernel_tile, kTuneKernelTile, 2);
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (rc != FK_OK) return rc;
+    best->streams = cur.streams;
+    best->coarsen = cur.coarsen;
+    best->kernel_tile = cur.kernel_tile;
+    best->count_tile = cur.count_tile;
+    if (best_ms) *best_ms = cur_ms;
+    return FK_OK;
 }
 
 }  // extern "C"

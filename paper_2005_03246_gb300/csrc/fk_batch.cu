@@ -13,6 +13,7 @@
 // in a CUDA graph.
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "fk_dc_ops.cuh"
@@ -169,20 +170,26 @@ __global__ void k_batch_fin_kde(const A* __restrict__ acc, GroupTab t, int ns, i
 struct Grp {
     int d;
     int E;
+    bool doubled;
     std::vector<int> ids;
 };
 
-static std::vector<Grp> make_groups(const fk_dataset* sets, int count, bool doubled) {
+// Groups of one pass: datasets by (d, E) with E rounded up to a multiple of
+// coarsen + 1 (coarser groups: fewer, larger launches, more padding); no
+// group exceeds 2^25 slots.
+static std::vector<Grp> make_groups(const fk_dataset* sets, int count, bool doubled, int coarsen) {
+    const int w = coarsen + 1;
     std::map<std::pair<int, int>, Grp> m;
     for (int b = 0; b < count; ++b) {
         const int64_t items = doubled ? 2 * sets[b].N : sets[b].N;
         int E = dc::ceil_log2(items < 2 ? 2 : items);
+        E = ((E + w - 1) / w) * w;
         Grp& g = m[{sets[b].d, E}];
         g.d = sets[b].d;
         g.E = E;
+        g.doubled = doubled;
         g.ids.push_back(b);
     }
-    // split groups so that no group exceeds 2^25 slots
     std::vector<Grp> out;
     for (auto& kv : m) {
         const Grp& g = kv.second;
@@ -191,6 +198,7 @@ static std::vector<Grp> make_groups(const fk_dataset* sets, int count, bool doub
             Grp c;
             c.d = g.d;
             c.E = g.E;
+            c.doubled = doubled;
             c.ids.assign(g.ids.begin() + i, g.ids.begin() + std::min(g.ids.size(), i + per));
             out.push_back(c);
         }
@@ -198,10 +206,39 @@ static std::vector<Grp> make_groups(const fk_dataset* sets, int count, bool doub
     return out;
 }
 
+// Library-owned streams (and fork / join events) of each device for running
+// groups concurrently; created on first use, never destroyed.
+constexpr int kMaxStreams = 8;
+struct StreamPool {
+    cudaStream_t s[kMaxStreams];
+    cudaEvent_t fork;
+    cudaEvent_t join[kMaxStreams];
+    bool ready = false;
+};
+static std::mutex g_pool_mu;      // guards creation and each call's enqueue
+static StreamPool g_pool[64];
+
+static fk_status stream_pool(StreamPool** out) {
+    int dev = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(FK_ERR_UNSUPPORTED, "device index %d", dev);
+    StreamPool& p = g_pool[dev];
+    if (!p.ready) {
+        for (int i = 1; i < kMaxStreams; ++i) FK_CUDA(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
+        FK_CUDA(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
+        for (int i = 1; i < kMaxStreams; ++i) FK_CUDA(cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming));
+        p.ready = true;
+    }
+    *out = &p;
+    return FK_OK;
+}
+
 // One group: tables, layout, positions, then the orthant counts or the KDE.
-static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, bool doubled, double h,
+static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, double h,
                            const std::vector<int64_t>& obe, const std::vector<int64_t>& obk, int64_t* ecdf_out,
-                           double* kde_out, fk_path path, Arena& ar, cudaStream_t st) {
+                           double* kde_out, fk_path path, const BatchCfg& cfg, Arena& ar, cudaStream_t st) {
+    const bool doubled = g.doubled;
+    const int opts = cfg.kernel_tile == 1 ? dc::OPT_HALF_TILE : 0;
     const int ns = (int)g.ids.size();
     const int E = g.E, d = g.d, d_eff = d < 2 ? 2 : d;
     const int64_t n = (int64_t)ns << E;
@@ -239,11 +276,12 @@ static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, bo
     // the engine plans its own buffers above this point
     if (ar.sizing) {
         if (doubled) {
-            dom_orthant_counts_seg(d, n, seg, E, n_tgt, P, BatchOut{nullptr, nullptr, ns}, nullptr, ar, st);
+            dom_orthant_counts_seg(d, n, seg, E, n_tgt, P, BatchOut{nullptr, nullptr, ns}, nullptr, ar, st,
+                                   cfg.count_tile);
         } else {
             dc::ItemMap im{0, 0, n_tgt, seg, E};
-            if (fp64) { dc::PolKD<1> p{}; static_cast<dc::ItemMap&>(p) = im; dc::sweep_kd1(d_eff, n, P, seq_top, p, ar, st, E); }
-            else { dc::PolKF<1> p{}; static_cast<dc::ItemMap&>(p) = im; dc::sweep_kf1(d_eff, n, P, seq_top, p, ar, st, E); }
+            if (fp64) { dc::PolKD<1> p{}; static_cast<dc::ItemMap&>(p) = im; dc::sweep_kd1(d_eff, n, P, seq_top, p, ar, st, E, opts); }
+            else { dc::PolKF<1> p{}; static_cast<dc::ItemMap&>(p) = im; dc::sweep_kf1(d_eff, n, P, seq_top, p, ar, st, E, opts); }
         }
         return FK_OK;
     }
@@ -302,7 +340,7 @@ static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, bo
     }
     if (doubled) {
         BatchOut bo{t.tbase, t.obase_e, ns};
-        return dom_orthant_counts_seg(d, n, seg, E, n_tgt, P, bo, ecdf_out, ar, st);
+        return dom_orthant_counts_seg(d, n, seg, E, n_tgt, P, bo, ecdf_out, ar, st, cfg.count_tile);
     }
     // kernel sums
     if (xd == FK_F32) {
@@ -329,22 +367,26 @@ static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, bo
         static_cast<dc::ItemMap&>(p) = im;
         p.w = (const double*)wts; p.fac = (const FacD*)fac; p.n_items = n; p.nbase = d_eff - 2;
         p.base = (dc::BaseD*)base; p.acc = (double*)acc; p.terms = nullptr; p.pbmask = (1u << (d_eff - 1)) - 1u;
-        FK_TRY(dc::sweep_kd1(d_eff, n, P, seq_top, p, ar, st, E));
+        FK_TRY(dc::sweep_kd1(d_eff, n, P, seq_top, p, ar, st, E, opts));
         k_batch_fin_kde<double, double><<<gt, 256, 0, st>>>((const double*)acc, t, ns, E, d, h, (const double*)wts, n_tgt, kde_out);
     } else {
         dc::PolKF<1> p{};
         static_cast<dc::ItemMap&>(p) = im;
         p.w = (const float*)wts; p.fac = (const FacF*)fac; p.n_items = n; p.nbase = d_eff - 2;
         p.base = (dc::BaseF*)base; p.acc = (FF*)acc; p.terms = nullptr; p.pbmask = (1u << (d_eff - 1)) - 1u;
-        FK_TRY(dc::sweep_kf1(d_eff, n, P, seq_top, p, ar, st, E));
+        FK_TRY(dc::sweep_kf1(d_eff, n, P, seq_top, p, ar, st, E, opts));
         k_batch_fin_kde<FF, float><<<gt, 256, 0, st>>>((const FF*)acc, t, ns, E, d, h, (const float*)wts, n_tgt, kde_out);
     }
     FK_LAUNCH_CHECK();
     return FK_OK;
 }
 
+// All groups of both passes; with cfg.streams > 1 they are spread over that
+// many streams (the caller's and library-owned ones, forked from and joined
+// back to the caller's stream by events, so the call stays capturable), each
+// stream with its own workspace slot sized for its largest group.
 fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
-                      double* kde_out, fk_path path, Arena& ar, cudaStream_t st) {
+                      double* kde_out, fk_path path, const BatchCfg& cfg, Arena& ar, cudaStream_t st) {
     std::vector<int64_t> obe(count), obk(count);
     int64_t re = 0, rk = 0;
     for (int b = 0; b < count; ++b) {
@@ -353,20 +395,72 @@ fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned w
         re += ((int64_t)1 << sets[b].d) * sets[b].N;
         rk += sets[b].N;
     }
-    const size_t mark = ar.used;
-    size_t high = mark;
+    std::vector<Grp> groups;
     for (int pass = 0; pass < 2; ++pass) {
         const bool doubled = (pass == 0);
         if (doubled && !(what & FK_BATCH_ECDF)) continue;
         if (!doubled && !(what & FK_BATCH_KDE)) continue;
-        for (const Grp& g : make_groups(sets, count, doubled)) {
-            FK_TRY(run_group(sets, g, xd, doubled, h, obe, obk, ecdf_out, kde_out, path, ar, st));
-            if (ar.used > high) high = ar.used;
-            ar.used = mark;
+        for (Grp& g : make_groups(sets, count, doubled, cfg.coarsen)) groups.push_back(g);
+    }
+    if (groups.empty()) return FK_OK;
+    // workspace of every group, largest first, dealt round-robin to the streams
+    std::vector<size_t> need(groups.size());
+    for (size_t i = 0; i < groups.size(); ++i) {
+        Arena a;
+        run_group(sets, groups[i], xd, h, obe, obk, nullptr, nullptr, path, cfg, a, st);
+        need[i] = (a.used + 255) & ~(size_t)255;
+    }
+    std::vector<size_t> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return need[a] > need[b]; });
+    const int S = std::max(1, std::min<int>(cfg.streams, std::min<int>(kMaxStreams, (int)groups.size())));
+    std::vector<std::vector<size_t>> slot(S);
+    std::vector<size_t> slot_need(S, 0);
+    for (size_t q = 0; q < order.size(); ++q) {
+        const int s = (int)(q % S);
+        slot[s].push_back(order[q]);
+        slot_need[s] = std::max(slot_need[s], need[order[q]]);
+    }
+    std::vector<size_t> off(S + 1, 0);
+    for (int s = 0; s < S; ++s) off[s + 1] = off[s] + slot_need[s];
+    const size_t base = (ar.used + 255) & ~(size_t)255;
+    if (ar.sizing) {
+        ar.used = base + off[S];
+        return FK_OK;
+    }
+    if (base + off[S] > ar.cap) return set_error(FK_ERR_WORKSPACE, "workspace too small (batched)");
+    StreamPool* pool = nullptr;
+    std::unique_lock<std::mutex> lk(g_pool_mu, std::defer_lock);
+    if (S > 1) {
+        lk.lock();
+        FK_TRY(stream_pool(&pool));
+        FK_CUDA(cudaEventRecord(pool->fork, st));
+        for (int s = 1; s < S; ++s) FK_CUDA(cudaStreamWaitEvent(pool->s[s], pool->fork, 0));
+    }
+    fk_status rc = FK_OK;
+    for (int s = 0; s < S && rc == FK_OK; ++s) {
+        cudaStream_t ss = (s == 0) ? st : pool->s[s];
+        for (size_t i : slot[s]) {
+            Arena a;
+            a.sizing = false;
+            a.base = ar.base + base + off[s];
+            a.cap = slot_need[s];
+            a.used = 0;
+            rc = run_group(sets, groups[i], xd, h, obe, obk, ecdf_out, kde_out, path, cfg, a, ss);
+            if (rc != FK_OK) break;
         }
     }
-    ar.used = high;
-    return FK_OK;
+    if (S > 1) {
+        // join every forked stream, also after an error, so no capture is left open
+        for (int s = 1; s < S; ++s) {
+            const cudaError_t e1 = cudaEventRecord(pool->join[s], pool->s[s]);
+            const cudaError_t e2 = cudaStreamWaitEvent(st, pool->join[s], 0);
+            if (rc == FK_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
+                rc = cuda_error(e1 != cudaSuccess ? e1 : e2, "stream join");
+        }
+    }
+    ar.used = base + off[S];
+    return rc;
 }
 
 }  // namespace fk

@@ -540,11 +540,12 @@ struct LAccP {
     __device__ uint32_t operator()(int64_t i) const { return p[lpd(base + (int)i)]; }
 };
 
-template <class Pol, int CLSB, bool FOLD>
+// HALF: the tile-size option of the batched autotuner (half the default tile).
+template <class Pol, int CLSB, bool FOLD, bool HALF = false>
 struct LocalCfg {
     // items per tile (the folded form halves it at d = 4 to keep its
     // per-thread state in registers)
-    static constexpr int T = FOLD ? (CLSB >= 2 ? Pol::kFoldT / 2 : Pol::kFoldT) : Pol::kLocalT;
+    static constexpr int T = (FOLD ? (CLSB >= 2 ? Pol::kFoldT / 2 : Pol::kFoldT) : Pol::kLocalT) / (HALF ? 2 : 1);
     // threads: 512, or 256 when the per-thread channel sums alone would take
     // more than 32 registers (so that they stay in registers)
     static constexpr int NT = sizeof(typename Pol::V) * (2 << CLSB) > 128 ? 256 : 512;
@@ -761,12 +762,12 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, false>::NT)
 
 // Folded form (kernel policies without per-orthant terms).  Source weights
 // are rebuilt from the per-item factors when needed instead of being held.
-template <class Pol, int CLSB>
-__global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true>::NT)
+template <class Pol, int CLSB, bool HALF>
+__global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
     k_local_fold(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0, ClassSpecK cs,
                  int levels, Pol pol, uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
                  int write_out, int rec_out, FoldRecs<Pol> rout) {
-    typedef LocalCfg<Pol, CLSB, true> Cfg;
+    typedef LocalCfg<Pol, CLSB, true, HALF> Cfg;
     typedef typename Pol::LOps LO;
     typedef typename LO::V V;          // tile-local sums
     typedef typename Pol::M M;

@@ -599,10 +599,13 @@ inline int ceil_log2(int64_t n) {
     return e;
 }
 
-template <class Pol, int CLSB, bool FOLD>
-fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
-                       const Pol& pol, DCBuffers& b, int& L0, cudaStream_t st) {
-    typedef LocalCfg<Pol, CLSB, FOLD> Cfg;
+// Option bits of the sweeps (chosen by the batched autotuner).
+enum : int { OPT_HALF_TILE = 1 };
+
+template <class Pol, int CLSB, bool FOLD, bool HALF>
+fk_status local_levels_t(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
+                         const Pol& pol, DCBuffers& b, int& L0, cudaStream_t st) {
+    typedef LocalCfg<Pol, CLSB, FOLD, HALF> Cfg;
     int lt = 0;
     while ((1 << (lt + 1)) <= Cfg::T) ++lt;
     L0 = E < lt ? E : lt;
@@ -611,7 +614,7 @@ fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0
     static bool attr_set = false;
     if (!attr_set) {
         if constexpr (FOLD)
-            FK_CUDA(cudaFuncSetAttribute(k_local_fold<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            FK_CUDA(cudaFuncSetAttribute(k_local_fold<Pol, CLSB, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         else
             FK_CUDA(cudaFuncSetAttribute(k_local_sweep<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -623,7 +626,7 @@ fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0
     ProfScope ps(Pol::kCanFold ? PF_KLOCAL : PF_LOCAL,
                  Pol::kCanFold ? (double)n * L0 * kKernelOpsPerItemLevel : lbytes, st);
     if constexpr (FOLD)
-        k_local_fold<Pol, CLSB><<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(
+        k_local_fold<Pol, CLSB, HALF><<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(
             seq, n, P0, cs, L0, pol, b.k[0], b.m[0], E > L0 ? 1 : 0, (E > L0 && Pol::kRecords) ? 1 : 0,
             fold_recs<Pol>(b, 0));
     else
@@ -631,6 +634,15 @@ fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0
                                                                            E > L0 ? 1 : 0);
     FK_LAUNCH_CHECK();
     return FK_OK;
+}
+
+template <class Pol, int CLSB, bool FOLD>
+fk_status local_levels(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
+                       const Pol& pol, DCBuffers& b, int& L0, int opts, cudaStream_t st) {
+    if constexpr (FOLD && Pol::kNW == 1) {
+        if (opts & OPT_HALF_TILE) return local_levels_t<Pol, CLSB, FOLD, true>(seq, n, E, P0, cs, pol, b, L0, st);
+    }
+    return local_levels_t<Pol, CLSB, FOLD, false>(seq, n, E, P0, cs, pol, b, L0, st);
 }
 
 // Merge levels L0..E-1 of the folded kernel sums on records.
@@ -672,20 +684,20 @@ fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cu
 
 template <class Pol, int CLSB>
 fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, const ClassSpec& cs,
-                     const Pol& pol, DCBuffers& b, cudaStream_t st) {
+                     const Pol& pol, DCBuffers& b, int opts, cudaStream_t st) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
     // tile-local levels (gather fused into the tile load)
     int L0 = 0;
     if constexpr (Pol::kCanFold) {
         if (!pol.terms) {
-            FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, st)));
+            FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, opts, st)));
             if constexpr (Pol::kRecords) return fold_levels<Pol, CLSB>(n, E, L0, pol, b, st);
         } else {
-            FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
+            FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, opts, st)));
         }
     } else {
-        FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, st)));
+        FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, opts, st)));
     }
     int cur = 0;
     const unsigned ctas = grid_for(n, MTILE);
@@ -733,8 +745,8 @@ struct OuterBuffers {
 
 template <class Pol, int CLSB>
 fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* const* P,
-                  ClassSpec cs, const Pol& pol, OuterBuffers* ob, DCBuffers& ib, cudaStream_t st) {
-    if (k == 1) return inner_sort<Pol, CLSB>(seq, n, E, P[0], cs, pol, ib, st);
+                  ClassSpec cs, const Pol& pol, OuterBuffers* ob, DCBuffers& ib, int opts, cudaStream_t st) {
+    if (k == 1) return inner_sort<Pol, CLSB>(seq, n, E, P[0], cs, pol, ib, opts, st);
     OuterBuffers& o = ob[k];
     const uint32_t* idx = P[k];
     if (o.idx) {
@@ -752,7 +764,7 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         c2.idx[k - 2] = idx;
         c2.lvl[k - 2] = l;
         if (c2.nb < k - 1) c2.nb = k - 1;
-        FK_TRY((recurse<Pol, CLSB>(k - 1, o.m[cur], n, l + 1, P, c2, pol, ob, ib, st)));
+        FK_TRY((recurse<Pol, CLSB>(k - 1, o.m[cur], n, l + 1, P, c2, pol, ob, ib, opts, st)));
     }
     return FK_OK;
 }
@@ -761,7 +773,7 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
 // are the per-axis positions, seq_top the items sorted by P[d_eff-1].
 template <class Pol, int CLSB>
 fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,
-                   const Pol& pol, Arena& ar, cudaStream_t st, int levels = -1) {
+                   const Pol& pol, Arena& ar, cudaStream_t st, int levels = -1, int opts = 0) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
     OuterBuffers ob[8] = {};
@@ -791,7 +803,7 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
     const int E = levels >= 0 ? levels : ceil_log2(n);
     // for k == d_eff-1 the axis index is P[d_eff-1] itself (idx == nullptr above)
     if (d_eff - 1 >= 2) ob[d_eff - 1].idx = nullptr;
-    return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, st);
+    return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, opts, st);
 }
 
 }  // namespace dc

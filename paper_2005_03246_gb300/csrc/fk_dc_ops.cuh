@@ -13,7 +13,7 @@ struct SelMap { int n; int o[256]; };   // output row r <- internal orthant o[r]
 // Instantiated sweeps (one per accumulation policy); CLSB is d_eff - 2.
 #define FK_DC_SWEEP_DECL(NAME, POL)                                                              \
     fk_status NAME(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,    \
-                   const POL& pol, Arena& ar, cudaStream_t st, int levels = -1);
+                   const POL& pol, Arena& ar, cudaStream_t st, int levels = -1, int opts = 0);
 FK_DC_SWEEP_DECL(sweep_count, PolCount)
 FK_DC_SWEEP_DECL(sweep_w64, PolW64)
 FK_DC_SWEEP_DECL(sweep_wff, PolWFF)
@@ -25,11 +25,11 @@ FK_DC_SWEEP_DECL(sweep_kd2, PolKD<2>)
 
 #define FK_DC_SWEEP_DEF(NAME, POL)                                                               \
     fk_status NAME(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,    \
-                   const POL& pol, Arena& ar, cudaStream_t st, int levels) {                   \
+                   const POL& pol, Arena& ar, cudaStream_t st, int levels, int opts) {         \
         switch (d_eff) {                                                                        \
-            case 2: return dc_sweep<POL, 0>(d_eff, n, P, seq_top, pol, ar, st, levels);         \
-            case 3: return dc_sweep<POL, 1>(d_eff, n, P, seq_top, pol, ar, st, levels);         \
-            case 4: return dc_sweep<POL, 2>(d_eff, n, P, seq_top, pol, ar, st, levels);         \
+            case 2: return dc_sweep<POL, 0>(d_eff, n, P, seq_top, pol, ar, st, levels, opts);   \
+            case 3: return dc_sweep<POL, 1>(d_eff, n, P, seq_top, pol, ar, st, levels, opts);   \
+            case 4: return dc_sweep<POL, 2>(d_eff, n, P, seq_top, pol, ar, st, levels, opts);   \
             default: return set_error(FK_ERR_UNSUPPORTED, "sample-point path supports d <= 4"); \
         }                                                                                       \
     }
@@ -48,9 +48,10 @@ struct BatchOut {
     const int64_t* obase;   // [nb] output offset of each dataset (device)
     int nb;
 };
+// count_tile: tile of the tile-local counting levels (0: 2048, 1: 1024, 2: 4096).
 fk_status dom_orthant_counts_seg(int d, int64_t n, const int64_t* seg, int segE, int64_t n_tgt,
                                  const uint32_t* const* P, BatchOut bo, int64_t* out, Arena& ar,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int count_tile = 0);
 
 // Operations (fk_dc_common.cu).  All pointers are device pointers.
 fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,

@@ -70,19 +70,19 @@ struct Items {
     }
 };
 
-constexpr int LT = 2048;          // tile-local items
-constexpr int LNT = 256;          // threads
-constexpr int LIT = LT / LNT;     // items per thread
+constexpr int LNT = 256;          // threads of the tile-local kernel (tiles of 1024, 2048 or 4096 items)
 
 // Tile-local merge levels.  Input: the enclosing state (items sorted by the
 // tree axis inside their nodes); output (if more levels follow): key, meta,
 // pref, acc in merged order; otherwise the received counts are flushed.
+template <int LT>
 __global__ void __launch_bounds__(LNT) k_dom_local(const uint32_t* __restrict__ seq, int64_t n,
                                                    const uint32_t* __restrict__ P0, ClassSpecK cs, int levels,
                                                    Items im, uint32_t* __restrict__ key_out,
                                                    uint32_t* __restrict__ meta_out, uint32_t* __restrict__ pref_out,
                                                    uint32_t* __restrict__ acc_out, int write_out,
                                                    uint32_t* __restrict__ C) {
+    constexpr int LIT = LT / LNT;      // items per thread
     extern __shared__ __align__(16) uint32_t s_dyn[];
     constexpr int LP = LT + LT / 32;   // padded row
     uint32_t(*s_key)[LP] = reinterpret_cast<uint32_t(*)[LP]>(s_dyn);
@@ -604,23 +604,31 @@ struct DomBuf {
     uint32_t* idx[8];
 };
 
-static fk_status dom_inner(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, ClassSpecK cs, Items im,
-                           DomBuf& B, uint32_t* C, cudaStream_t st) {
+template <int LT>
+static fk_status dom_local_launch(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, ClassSpecK cs, Items im,
+                                  DomBuf& B, uint32_t* C, int& L0, cudaStream_t st) {
     int lt = 0;
     while ((1 << (lt + 1)) <= LT) ++lt;
-    const int L0 = E < lt ? E : lt;
-    {
-        ProfScope ps(PF_LOCAL, 8.0 * n + 8.0 * n * (E > L0 ? 2 : 0) + 8.0 * im.n_tgt, st);
-        constexpr int smem = 8 * (LT + LT / 32) * 4;
-        static bool attr = false;
-        if (!attr) {
-            FK_CUDA(cudaFuncSetAttribute(k_dom_local, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr = true;
-        }
-        k_dom_local<<<grid_for(n, LT), LNT, smem, st>>>(seq, n, P0, cs, L0, im, B.k[0], B.m[0], B.p[0], B.a[0],
-                                                        E > L0 ? 1 : 0, C);
-        FK_LAUNCH_CHECK();
+    L0 = E < lt ? E : lt;
+    ProfScope ps(PF_LOCAL, 8.0 * n + 8.0 * n * (E > L0 ? 2 : 0) + 8.0 * im.n_tgt, st);
+    constexpr int smem = 8 * (LT + LT / 32) * 4;
+    static bool attr = false;
+    if (!attr) {
+        FK_CUDA(cudaFuncSetAttribute(k_dom_local<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
     }
+    k_dom_local<LT><<<grid_for(n, LT), LNT, smem, st>>>(seq, n, P0, cs, L0, im, B.k[0], B.m[0], B.p[0], B.a[0],
+                                                        E > L0 ? 1 : 0, C);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
+static fk_status dom_inner(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, ClassSpecK cs, Items im,
+                           DomBuf& B, uint32_t* C, int count_tile, cudaStream_t st) {
+    int L0 = 0;
+    if (count_tile == 1) FK_TRY(dom_local_launch<1024>(seq, n, E, P0, cs, im, B, C, L0, st));
+    else if (count_tile == 2) FK_TRY(dom_local_launch<4096>(seq, n, E, P0, cs, im, B, C, L0, st));
+    else FK_TRY(dom_local_launch<2048>(seq, n, E, P0, cs, im, B, C, L0, st));
     int cur = 0;
     for (int m = L0; m < E; ++m) {
         const int last = (m == E - 1);
@@ -634,11 +642,11 @@ static fk_status dom_inner(const uint32_t* seq, int64_t n, int E, const uint32_t
 }
 
 static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* const* P, ClassSpecK cs,
-                             Items im, DomBuf& B, uint32_t* C, cudaStream_t st) {
+                             Items im, DomBuf& B, uint32_t* C, int count_tile, cudaStream_t st) {
     if (k == 1) {
         Items it = im;
         it.full = (1u << cs.nb) - 1u;
-        return dom_inner(seq, n, E, P[0], cs, it, B, C, st);
+        return dom_inner(seq, n, E, P[0], cs, it, B, C, count_tile, st);
     }
     const uint32_t* idx = P[k];
     if (B.idx[k]) {
@@ -672,7 +680,7 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
         c2.idx[k - 2] = idx;
         c2.lvl[k - 2] = l;
         if (c2.nb < k - 1) c2.nb = k - 1;
-        FK_TRY(dom_recurse(k - 1, B.om[k][cur], n, l + 1, P, c2, im, B, C, st));
+        FK_TRY(dom_recurse(k - 1, B.om[k][cur], n, l + 1, P, c2, im, B, C, count_tile, st));
     }
     return FK_OK;
 }
@@ -682,7 +690,7 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
 // C_A for every non-empty subset A of the d axes (rank counts for |A| = 1,
 // nested dominance for |A| >= 2); E levels of the outermost merge sort.
 static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32_t* const* P, uint32_t** Cs,
-                                 Arena& ar, cudaStream_t st) {
+                                 Arena& ar, cudaStream_t st, int count_tile = 0) {
     const int nsub = 1 << d;
     const int64_t n_tgt = im.n_tgt;
     for (int A = 1; A < nsub; ++A) Cs[A] = ar.take<uint32_t>((size_t)n_tgt);
@@ -723,7 +731,7 @@ static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32
         DomBuf BB = B;
         for (int kk = 2; kk < 8; ++kk) BB.idx[kk] = (kk < k - 1) ? B.idx[kk] : nullptr;
         ClassSpecK cs = {};
-        FK_TRY(dom_recurse(k - 1, seq, n, E, PA, cs, im, BB, Cs[A], st));
+        FK_TRY(dom_recurse(k - 1, seq, n, E, PA, cs, im, BB, Cs[A], count_tile, st));
     }
     return FK_OK;
 }
@@ -750,11 +758,11 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
 
 fk_status dom_orthant_counts_seg(int d, int64_t n, const int64_t* seg, int segE, int64_t n_tgt,
                                  const uint32_t* const* P, BatchOut bo, int64_t* out, Arena& ar,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int count_tile) {
     const int nsub = 1 << d;
     uint32_t* Cs[16] = {};
     Items im{0, 0, n_tgt, 0u, seg, segE};
-    FK_TRY(dom_counts_core(d, n, im, segE, P, Cs, ar, st));
+    FK_TRY(dom_counts_core(d, n, im, segE, P, Cs, ar, st, count_tile));
     if (ar.sizing || n_tgt == 0) return FK_OK;
     CTab ct = {};
     for (int A = 1; A < nsub; ++A) ct.c[A] = Cs[A];

@@ -67,6 +67,14 @@ struct ProfScope {
 // Device-side error codes recorded in the per-device error word.
 enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
 
+// Launch configuration of the batched path (the autotuner's search space).
+struct BatchCfg {
+    int streams = 1;       // groups run concurrently on this many streams (1..8)
+    int coarsen = 0;       // group padded sizes rounded up to multiples of coarsen+1 levels (0..2)
+    int kernel_tile = 0;   // tile-local kernel-sum levels: 0 default tile, 1 half tile
+    int count_tile = 0;    // tile-local counting levels: 0 2048, 1 1024, 2 4096 items
+};
+
 // ------------------------------------------------------------------ workspace arena
 // A bump allocator over caller scratch.  In sizing mode (base == nullptr) it
 // only accumulates the total so that the same plan code gives the size.

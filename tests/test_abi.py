@@ -44,3 +44,47 @@ def test_workspace_queries_are_host_only():
     assert need >= cells * 4
     bad = np.array([0, 5], dtype=np.int64)
     assert lib.fk_ecdf_grid_workspace(10, 2, bad.ctypes.data_as(ctypes.c_void_p), 0, 0) == 0
+
+
+def _dummy_sets(lib_mod, sizes):
+    """fk_dataset array with placeholder (never dereferenced) device pointers:
+    workspace queries only plan on the host."""
+    sets = (lib_mod.Dataset * len(sizes))()
+    for b, (n, d) in enumerate(sizes):
+        sets[b].x = 0x10000 + 256 * b
+        sets[b].y = None
+        sets[b].N, sets[b].d = n, d
+    return sets
+
+
+def test_batched_config_default_and_validation():
+    import ctypes
+    from paper_2005_03246_gb300 import _lib
+    lib = _lib.load()
+    c = _lib.BatchConfig()
+    lib.fk_batched_config_default(ctypes.byref(c))
+    assert c.as_dict() == {"streams": 1, "coarsen": 0, "kernel_tile": 0, "count_tile": 0}
+    sets = _dummy_sets(_lib, [(1000, 2), (20000, 3), (70000, 2), (5, 1)])
+    what = _lib.FK_BATCH_ECDF | _lib.FK_BATCH_KDE
+    base = lib.fk_batched_workspace_ex(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED, ctypes.byref(c))
+    assert base > 0
+    assert base == lib.fk_batched_workspace(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED)
+    for bad in ({"streams": 0}, {"streams": 9}, {"coarsen": 3}, {"kernel_tile": 2}, {"count_tile": -1}):
+        b = _lib.BatchConfig()
+        lib.fk_batched_config_default(ctypes.byref(b))
+        for k, v in bad.items():
+            setattr(b, k, v)
+        assert lib.fk_batched_workspace_ex(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED, ctypes.byref(b)) == 0
+    # more streams: one workspace slot per stream, never less than one slot
+    c.streams = 4
+    four = lib.fk_batched_workspace_ex(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED, ctypes.byref(c))
+    assert four >= base
+    # the autotuner's workspace covers every candidate configuration
+    tune = lib.fk_batched_autotune_workspace(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED)
+    for s in (1, 2, 4, 8):
+        for co in (0, 1, 2):
+            for ct in (0, 1, 2):
+                for kt in (0, 1):
+                    c.streams, c.coarsen, c.count_tile, c.kernel_tile = s, co, ct, kt
+                    assert tune >= lib.fk_batched_workspace_ex(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED,
+                                                               ctypes.byref(c))

@@ -94,3 +94,54 @@ def test_batched_config_512_datasets():
         ref = oracle.kde_laplace(x, 0.1, w=y, z=x[idx])
         scale = oracle.kde_laplace(x, 0.1, w=np.abs(y), z=x[idx]).max()
         assert np.max(np.abs(kde[b].cpu().numpy()[idx] - ref)) <= 1e-5 * scale
+
+
+CONFIGS = [
+    {"streams": 2, "coarsen": 1, "kernel_tile": 1, "count_tile": 1},
+    {"streams": 4, "coarsen": 2, "kernel_tile": 0, "count_tile": 2},
+    {"streams": 8, "coarsen": 0, "kernel_tile": 1, "count_tile": 0},
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_batched_configurations_agree(cfg):
+    """Every launch configuration (streams, group coarsening, tile sizes) gives
+    the default configuration's counts exactly and its KDE within tolerance,
+    eagerly and replayed from a CUDA graph."""
+    fk = _fk()
+    xs, ys = _sets(30, 5, nmax=6000)
+    tx, ty = [_t(x) for x in xs], [_t(y) for y in ys]
+    e0, k0 = fk.Batched(tx, ty, h=0.1, graph=False).run()
+    # signed weights: differences are measured on the density of |y|
+    scales = [oracle.kde_laplace(x, 0.1, w=np.abs(y)).max() if x.shape[0] else 0.0 for x, y in zip(xs, ys)]
+    for graph in (False, True):
+        bt = fk.Batched(tx, ty, h=0.1, graph=graph, config=cfg)
+        assert bt.config == cfg
+        for rep in range(2):
+            e1, k1 = bt.run()
+            for b in range(len(xs)):
+                assert np.array_equal(e1[b].cpu().numpy(), e0[b].cpu().numpy()), (b, graph)
+                if xs[b].shape[0] == 0:
+                    continue
+                a, r = k1[b].cpu().numpy(), k0[b].cpu().numpy()
+                assert np.max(np.abs(a - r)) <= 2e-5 * scales[b], (b, graph)
+
+
+def test_batched_autotune_512_datasets():
+    """The autotuner picks a configuration by measurement on the 512-dataset
+    workload; the tuned, graph-captured call matches the default one."""
+    fk = _fk()
+    sets = datagen.batched()
+    xs = [_t(s["x"]) for s in sets]
+    ys = [_t(s["y"]) for s in sets]
+    e0, k0 = fk.Batched(xs, ys, h=0.1, graph=False).run()
+    bt = fk.Batched(xs, ys, h=0.1, graph=True, config="tune")
+    c = bt.config
+    assert 1 <= c["streams"] <= 8 and 0 <= c["coarsen"] <= 2
+    assert c["kernel_tile"] in (0, 1) and c["count_tile"] in (0, 1, 2)
+    assert bt.tune_ms is not None and bt.tune_ms > 0
+    e1, k1 = bt.run()
+    for b in range(0, len(sets), 7):
+        assert np.array_equal(e1[b].cpu().numpy(), e0[b].cpu().numpy()), b
+        a, r = k1[b].cpu().numpy(), k0[b].cpu().numpy()
+        assert np.max(np.abs(a - r)) <= 2e-5 * np.abs(r).max(), b
