@@ -392,14 +392,18 @@ def _extras(fk, torch, dev, x, stream, flush, timed):
     xs = [torch.as_tensor(s["x"], device=dev) for s in sets]
     ys = [torch.as_tensor(s["y"], device=dev) for s in sets]
     pts = int(sum(s["n"] for s in sets))
-    bm = fk.Batched(xs, ys, h=H, path="mixed", graph=True)
-    bd = fk.Batched(xs, ys, h=H, path="fp64", graph=True)
+    # each path with the configuration its autotuner picks (and the default one)
+    bm = fk.Batched(xs, ys, h=H, path="mixed", graph=True, config="tune")
+    bd = fk.Batched(xs, ys, h=H, path="fp64", graph=True, config="tune")
+    bm0 = fk.Batched(xs, ys, h=H, path="mixed", graph=True)
     tm = timed(lambda: bm.run(), reps=5)
     td = timed(lambda: bd.run(), reps=5)
+    tm0 = timed(lambda: bm0.run(), reps=5)
     out["batched"] = {"workload": "512 datasets, N log-uniform [1e3,1e5], d 2/3, U[0,1] FP32; all orthant "
                                   "counts + Laplacian KDE h=0.1 weighted by y; CUDA-graph replay",
                       "points": pts, "mixed_ms": tm, "fp64_ms": td, "points_per_s": pts / (tm / 1e3),
-                      "mixed_speedup": td / tm}
+                      "mixed_speedup": td / tm, "mixed_config": bm.config, "fp64_config": bd.config,
+                      "mixed_default_config_ms": tm0}
     g = torch.ones(x.shape[0], dtype=torch.float64, device=dev)
     out["kde_backward_ms"] = timed(lambda: fk.kde_laplace_backward(x, H, g, need_w=True, need_z=False,
                                                                    need_h=True, path="mixed"), reps=3)
