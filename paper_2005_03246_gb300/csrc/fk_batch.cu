@@ -13,7 +13,6 @@
 // in a CUDA graph.
 #include <algorithm>
 #include <map>
-#include <mutex>
 #include <vector>
 
 #include "fk_dc_ops.cuh"
@@ -206,33 +205,6 @@ static std::vector<Grp> make_groups(const fk_dataset* sets, int count, bool doub
     return out;
 }
 
-// Library-owned streams (and fork / join events) of each device for running
-// groups concurrently; created on first use, never destroyed.
-constexpr int kMaxStreams = 8;
-struct StreamPool {
-    cudaStream_t s[kMaxStreams];
-    cudaEvent_t fork;
-    cudaEvent_t join[kMaxStreams];
-    bool ready = false;
-};
-static std::mutex g_pool_mu;      // guards creation and each call's enqueue
-static StreamPool g_pool[64];
-
-static fk_status stream_pool(StreamPool** out) {
-    int dev = 0;
-    FK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return set_error(FK_ERR_UNSUPPORTED, "device index %d", dev);
-    StreamPool& p = g_pool[dev];
-    if (!p.ready) {
-        for (int i = 1; i < kMaxStreams; ++i) FK_CUDA(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
-        FK_CUDA(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
-        for (int i = 1; i < kMaxStreams; ++i) FK_CUDA(cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming));
-        p.ready = true;
-    }
-    *out = &p;
-    return FK_OK;
-}
-
 // One group: tables, layout, positions, then the orthant counts or the KDE.
 static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, double h,
                            const std::vector<int64_t>& obe, const std::vector<int64_t>& obk, int64_t* ecdf_out,
@@ -413,7 +385,7 @@ fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned w
     std::vector<size_t> order(groups.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return need[a] > need[b]; });
-    const int S = std::max(1, std::min<int>(cfg.streams, std::min<int>(kMaxStreams, (int)groups.size())));
+    const int S = std::max(1, std::min<int>(cfg.streams, std::min<int>(kPoolStreams, (int)groups.size())));
     std::vector<std::vector<size_t>> slot(S);
     std::vector<size_t> slot_need(S, 0);
     for (size_t q = 0; q < order.size(); ++q) {
@@ -429,36 +401,23 @@ fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned w
         return FK_OK;
     }
     if (base + off[S] > ar.cap) return set_error(FK_ERR_WORKSPACE, "workspace too small (batched)");
-    StreamPool* pool = nullptr;
-    std::unique_lock<std::mutex> lk(g_pool_mu, std::defer_lock);
-    if (S > 1) {
-        lk.lock();
-        FK_TRY(stream_pool(&pool));
-        FK_CUDA(cudaEventRecord(pool->fork, st));
-        for (int s = 1; s < S; ++s) FK_CUDA(cudaStreamWaitEvent(pool->s[s], pool->fork, 0));
-    }
+    StreamFork fork;
+    FK_TRY(fork.begin(0, st, S));
     fk_status rc = FK_OK;
     for (int s = 0; s < S && rc == FK_OK; ++s) {
-        cudaStream_t ss = (s == 0) ? st : pool->s[s];
         for (size_t i : slot[s]) {
             Arena a;
             a.sizing = false;
             a.base = ar.base + base + off[s];
             a.cap = slot_need[s];
             a.used = 0;
-            rc = run_group(sets, groups[i], xd, h, obe, obk, ecdf_out, kde_out, path, cfg, a, ss);
+            rc = run_group(sets, groups[i], xd, h, obe, obk, ecdf_out, kde_out, path, cfg, a, fork.s[s]);
             if (rc != FK_OK) break;
         }
     }
-    if (S > 1) {
-        // join every forked stream, also after an error, so no capture is left open
-        for (int s = 1; s < S; ++s) {
-            const cudaError_t e1 = cudaEventRecord(pool->join[s], pool->s[s]);
-            const cudaError_t e2 = cudaStreamWaitEvent(st, pool->join[s], 0);
-            if (rc == FK_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
-                rc = cuda_error(e1 != cudaSuccess ? e1 : e2, "stream join");
-        }
-    }
+    // join every forked stream, also after an error, so no capture is left open
+    const fk_status rj = fork.end();
+    if (rc == FK_OK) rc = rj;
     ar.used = base + off[S];
     return rc;
 }

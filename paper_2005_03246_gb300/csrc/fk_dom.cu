@@ -19,6 +19,8 @@
 // are sources on the lower side of every enclosing axis (class 0); receiving
 // targets are targets on the upper side of every enclosing axis (class all
 // ones) and in D.
+#include <algorithm>
+
 #include "fk_dc_ops.cuh"
 
 namespace fk {
@@ -591,6 +593,9 @@ __global__ void k_combine_seg(CTab ct, int d, int64_t n_tgt, const int64_t* __re
 
 using namespace dom;
 
+// Streams for the independent dominance problems of one orthant-count call.
+constexpr int kCountStreams = 4;
+
 // Dominance count C_A for the axes in `axes` (sorted, size k >= 2): the
 // innermost merge sort over the second axis by the first, nested inside merge
 // sorts of the outer axes, as in fk_dc_drv.cuh.
@@ -689,51 +694,74 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
 // (sources before targets on ties), by inclusion-exclusion.
 // C_A for every non-empty subset A of the d axes (rank counts for |A| = 1,
 // nested dominance for |A| >= 2); E levels of the outermost merge sort.
+// The dominance problems of the subsets with |A| >= 2 are independent: with
+// streams > 1 they run concurrently on forked streams, each stream with its
+// own engine buffers.
 static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32_t* const* P, uint32_t** Cs,
-                                 Arena& ar, cudaStream_t st, int count_tile = 0) {
+                                 Arena& ar, cudaStream_t st, int count_tile = 0, int streams = 1) {
     const int nsub = 1 << d;
     const int64_t n_tgt = im.n_tgt;
-    for (int A = 1; A < nsub; ++A) Cs[A] = ar.take<uint32_t>((size_t)n_tgt);
-    DomBuf B = {};
-    for (int q = 0; q < 2; ++q) {
-        B.k[q] = ar.take<uint32_t>(n); B.m[q] = ar.take<uint32_t>(n);
-        B.p[q] = ar.take<uint32_t>(n); B.a[q] = ar.take<uint32_t>(n);
+    int nbig = 0;
+    for (int A = 1; A < nsub; ++A) {
+        Cs[A] = ar.take<uint32_t>((size_t)n_tgt);
+        if (__builtin_popcount((unsigned)A) >= 2) ++nbig;
     }
-    for (int k = 2; k < d; ++k) {
-        for (int q = 0; q < 2; ++q) { B.ok[k][q] = ar.take<uint32_t>(n); B.om[k][q] = ar.take<uint32_t>(n); }
-        B.idx[k] = ar.take<uint32_t>(n);
+    const int S = std::max(1, std::min(streams, std::min(nbig, kPoolStreams)));
+    DomBuf B[kPoolStreams] = {};
+    uint32_t* seq[kPoolStreams] = {};
+    for (int q = 0; q < S; ++q) {
+        for (int r = 0; r < 2; ++r) {
+            B[q].k[r] = ar.take<uint32_t>(n); B[q].m[r] = ar.take<uint32_t>(n);
+            B[q].p[r] = ar.take<uint32_t>(n); B[q].a[r] = ar.take<uint32_t>(n);
+        }
+        for (int k = 2; k < d; ++k) {
+            for (int r = 0; r < 2; ++r) { B[q].ok[k][r] = ar.take<uint32_t>(n); B[q].om[k][r] = ar.take<uint32_t>(n); }
+            B[q].idx[k] = ar.take<uint32_t>(n);
+        }
+        seq[q] = ar.take<uint32_t>(n);
     }
     uint32_t* flags = ar.take<uint32_t>(n);
     uint32_t* scanned = ar.take<uint32_t>(n);
     uint32_t* stmp = ar.take<uint32_t>(scan_u32_tmp_words(n));
-    uint32_t* seq = ar.take<uint32_t>(n);
     if (ar.sizing) return FK_OK;
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
     for (int A = 1; A < nsub; ++A) FK_CUDA(cudaMemsetAsync(Cs[A], 0, (size_t)n_tgt * 4, st));
     const unsigned g = grid_for(n, 256);
+    // rank counts (|A| = 1) on the caller's stream
     for (int A = 1; A < nsub; ++A) {
-        const int k = __builtin_popcount((unsigned)A);
-        const uint32_t* PA[8];
-        int q = 0;
-        for (int a = 0; a < d; ++a)
-            if ((A >> a) & 1) PA[q++] = P[a];
-        if (k == 1) {
-            k_src_flags<<<g, 256, 0, st>>>(PA[0], n, im, flags);
-            FK_LAUNCH_CHECK();
-            FK_TRY(scan_u32_exclusive(flags, scanned, n, stmp, st));
-            k_rank_counts<<<g, 256, 0, st>>>(PA[0], scanned, n, im, E, Cs[A]);
-            FK_LAUNCH_CHECK();
-            continue;
-        }
-        // items in the order of the outermost axis of A
-        k_seq_from_pos<<<g, 256, 0, st>>>(PA[k - 1], n, seq);
+        if (__builtin_popcount((unsigned)A) != 1) continue;
+        const uint32_t* PA = P[__builtin_ctz((unsigned)A)];
+        k_src_flags<<<g, 256, 0, st>>>(PA, n, im, flags);
         FK_LAUNCH_CHECK();
-        DomBuf BB = B;
-        for (int kk = 2; kk < 8; ++kk) BB.idx[kk] = (kk < k - 1) ? B.idx[kk] : nullptr;
-        ClassSpecK cs = {};
-        FK_TRY(dom_recurse(k - 1, seq, n, E, PA, cs, im, BB, Cs[A], count_tile, st));
+        FK_TRY(scan_u32_exclusive(flags, scanned, n, stmp, st));
+        k_rank_counts<<<g, 256, 0, st>>>(PA, scanned, n, im, E, Cs[A]);
+        FK_LAUNCH_CHECK();
     }
-    return FK_OK;
+    StreamFork fork;
+    FK_TRY(fork.begin(1, st, S));
+    fk_status rc = FK_OK;
+    int j = 0;
+    for (int A = 1; A < nsub && rc == FK_OK; ++A) {
+        const int k = __builtin_popcount((unsigned)A);
+        if (k < 2) continue;
+        const int q = j++ % S;
+        cudaStream_t ss = fork.s[q];
+        const uint32_t* PA[8];
+        int c = 0;
+        for (int a = 0; a < d; ++a)
+            if ((A >> a) & 1) PA[c++] = P[a];
+        // items in the order of the outermost axis of A
+        k_seq_from_pos<<<g, 256, 0, ss>>>(PA[k - 1], n, seq[q]);
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) { rc = cuda_error(le, "k_seq_from_pos"); break; }
+        note_launch();
+        DomBuf BB = B[q];
+        for (int kk = 2; kk < 8; ++kk) BB.idx[kk] = (kk < k - 1) ? B[q].idx[kk] : nullptr;
+        ClassSpecK cs = {};
+        rc = dom_recurse(k - 1, seq[q], n, E, PA, cs, im, BB, Cs[A], count_tile, ss);
+    }
+    const fk_status rj = fork.end();
+    return rc != FK_OK ? rc : rj;
 }
 
 fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, int64_t n_tgt,
@@ -742,7 +770,7 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
     const int nsub = 1 << d;
     uint32_t* Cs[16] = {};
     Items im{n_src, tgt_off, n_tgt, 0u, nullptr, 0};
-    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st));
+    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams));
     if (ar.sizing) return FK_OK;
     dc::SelMap sel;
     sel.n = 0;

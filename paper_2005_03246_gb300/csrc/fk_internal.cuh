@@ -1,6 +1,8 @@
 // fk_internal.cuh -- shared internals of the fastecdf library (not part of the ABI).
 #pragma once
 
+#include <mutex>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -66,6 +68,24 @@ struct ProfScope {
 
 // Device-side error codes recorded in the per-device error word.
 enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
+
+// Concurrent parts of one call (fk_streams.cu): begin() forks up to k-1
+// library-owned streams from `main` (s[0] == main), end() (or the destructor)
+// joins them back.  Pool 0 serves the batched groups, pool 1 the parts inside
+// one operation.
+constexpr int kPoolStreams = 8;
+struct StreamFork {
+    cudaStream_t s[kPoolStreams] = {};
+    int n = 1;
+    fk_status begin(int pool, cudaStream_t main, int k);
+    fk_status end();
+    ~StreamFork();
+    cudaStream_t st = nullptr;
+    int pool = 0;
+    int dev_ = 0;
+    bool forked = false;
+    std::unique_lock<std::mutex> lock;
+};
 
 // Launch configuration of the batched path (the autotuner's search space).
 struct BatchCfg {
