@@ -210,7 +210,8 @@ static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, do
                            const std::vector<int64_t>& obe, const std::vector<int64_t>& obk, int64_t* ecdf_out,
                            double* kde_out, fk_path path, const BatchCfg& cfg, Arena& ar, cudaStream_t st) {
     const bool doubled = g.doubled;
-    const int opts = cfg.kernel_tile == 1 ? dc::OPT_HALF_TILE : 0;
+    // groups run concurrently on their own; their sweeps stay serial
+    const int opts = (cfg.kernel_tile == 1 ? dc::OPT_HALF_TILE : 0) | dc::OPT_SERIAL;
     const int ns = (int)g.ids.size();
     const int E = g.E, d = g.d, d_eff = d < 2 ? 2 : d;
     const int64_t n = (int64_t)ns << E;
@@ -345,9 +346,9 @@ static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, do
         dc::PolKF<1> p{};
         static_cast<dc::ItemMap&>(p) = im;
         p.w = (const float*)wts; p.fac = (const FacF*)fac; p.n_items = n; p.nbase = d_eff - 2;
-        p.base = (dc::BaseF*)base; p.acc = (FF*)acc; p.terms = nullptr; p.pbmask = (1u << (d_eff - 1)) - 1u;
+        p.base = (dc::BaseF*)base; p.acc = (double*)acc; p.terms = nullptr; p.pbmask = (1u << (d_eff - 1)) - 1u;
         FK_TRY(dc::sweep_kf1(d_eff, n, P, seq_top, p, ar, st, E, opts));
-        k_batch_fin_kde<FF, float><<<gt, 256, 0, st>>>((const FF*)acc, t, ns, E, d, h, (const float*)wts, n_tgt, kde_out);
+        k_batch_fin_kde<double, float><<<gt, 256, 0, st>>>((const double*)acc, t, ns, E, d, h, (const float*)wts, n_tgt, kde_out);
     }
     FK_LAUNCH_CHECK();
     return FK_OK;

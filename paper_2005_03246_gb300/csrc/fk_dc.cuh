@@ -795,7 +795,8 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
             s_key[lpd(i)] = P0[item];
             s_meta[lpd(i)] = item | (c << kItemBits);
             s_home[lpd(i)] = (uint16_t)i;
-            pol.prep_item(item, c);
+            // the longer levels read per-item bases only without records
+            if constexpr (!Pol::kRecords) pol.prep_item(item, c);
             M wt;
             pol.fold_item(item, c, &s_fm[4 * i], &s_fs[4 * i], wt);
             s_wt[i] = pol.is_src(item) ? wt : (M)0;   // 0: no source role

@@ -317,16 +317,16 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
     void* fac = ar.take<char>((size_t)d_eff * n * fsz);
     void* base = ar.take<char>((size_t)n * (fp64 ? sizeof(BaseD) : sizeof(BaseF)));
     void* wts = w ? ar.take<char>((size_t)N * (fp64 ? 8 : 4)) : nullptr;
-    const size_t asz = fp64 ? 8 : 8;   // double or FF
+    const size_t asz = 8;   // double sums on both paths (FF per-orthant terms on the mixed path)
     void* acc = ar.take<char>((size_t)nw * n_tgt * asz);
     void* tacc = terms ? ar.take<char>((size_t)(1 << d_eff) * n_tgt * asz) : nullptr;
     HVec hv;
     for (int k = 0; k < 8; ++k) hv.v[k] = (k < d) ? h[k] : 1.0;
     PolKF<1> f1{}; PolKF<2> f2{}; PolKD<1> d1{}; PolKD<2> d2{};
-#define FK_SETK(P, FT, BT, AT, WT)                                            \
-    static_cast<ItemMap&>(P) = im; P.w = (const WT*)wts; P.fac = (const FT*)fac; \
-    P.n_items = n; P.nbase = d_eff - 2; P.base = (BT*)base; P.acc = (AT*)acc;    \
-    P.terms = (AT*)tacc; P.pbmask = pbmask;
+#define FK_SETK(P, FT, BT, TT, WT)                                                \
+    static_cast<ItemMap&>(P) = im; P.w = (const WT*)wts; P.fac = (const FT*)fac;     \
+    P.n_items = n; P.nbase = d_eff - 2; P.base = (BT*)base; P.acc = (double*)acc;    \
+    P.terms = (TT*)tacc; P.pbmask = pbmask;
     FK_SETK(f1, FacF, BaseF, FF, float)
     FK_SETK(f2, FacF, BaseF, FF, float)
     FK_SETK(d1, FacD, BaseD, double, double)
@@ -384,7 +384,7 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
             FK_LAUNCH_CHECK();
         }
     } else {
-        k_fin_kernel<FF, float><<<gt, 256, 0, st>>>((const FF*)acc, n_tgt, nw, C, (const float*)wts, has_self, out);
+        k_fin_kernel<double, float><<<gt, 256, 0, st>>>((const double*)acc, n_tgt, nw, C, (const float*)wts, has_self, out);
         FK_LAUNCH_CHECK();
         if (tacc) {
             k_fin_terms<FF, float><<<gt, 256, 0, st>>>((const FF*)tacc, n_tgt, d, d_eff, C, (const float*)wts, has_self, terms);

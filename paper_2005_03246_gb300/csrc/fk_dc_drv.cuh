@@ -195,7 +195,7 @@ struct PolKF : ItemMap {
     int64_t n_items;
     int nbase;                // number of enclosing axes (d - 2)
     BaseF* base;              // [n_items]
-    FF* acc;                  // [NW][n_tgt]
+    double* acc;              // [NW][n_tgt] (FP64: flushes of concurrent sorts add atomically)
     FF* terms;                // optional [2^d][n_tgt]
     uint32_t pbmask;
     __device__ static V zero() {
@@ -290,7 +290,7 @@ struct PolKF : ItemMap {
     __device__ void fold_flush(uint32_t item, const FA* a) const {
         const int64_t t = tgt_index(item);
 #pragma unroll
-        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] = ff_add(acc[(int64_t)i * n_tgt + t], a[i]);
+        for (int i = 0; i < NW; ++i) atomicAdd(acc + (int64_t)i * n_tgt + t, (double)a[i].hi + (double)a[i].lo);
     }
     __device__ BaseF base_of(uint32_t item, uint32_t cls) const {
         float m = 1.f;
@@ -329,7 +329,7 @@ struct PolKF : ItemMap {
         const FacF e0 = fac[item];
         FF a[NW];
 #pragma unroll
-        for (int i = 0; i < NW; ++i) a[i] = acc[(int64_t)i * n_tgt + t];
+        for (int i = 0; i < NW; ++i) a[i] = ff_zero();
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int h = j >> 1, dir = j & 1;
@@ -346,7 +346,7 @@ struct PolKF : ItemMap {
             }
         }
 #pragma unroll
-        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] = a[i];
+        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] += (double)a[i].hi + (double)a[i].lo;
     }
     __device__ void src_weights(uint32_t item, int half, V& f, V& b) const {
         const FacF e1 = fac[(int64_t)1 * n_items + item];
@@ -380,9 +380,7 @@ struct PolKF : ItemMap {
         for (int i = 0; i < NW; ++i) {
             const float cf = (f.v[i].hi + f.v[i].lo) * tf * pow2f_any(f.v[i].e + sf);
             const float cb = (b.v[i].hi + b.v[i].lo) * tb * pow2f_any(b.v[i].e + sb);
-            FF a = acc[(int64_t)i * n_tgt + t];
-            a = ff_add_f(ff_add_f(a, cf), cb);
-            acc[(int64_t)i * n_tgt + t] = a;
+            acc[(int64_t)i * n_tgt + t] += (double)cf + (double)cb;
             if (i == 0 && terms) {
                 terms[(int64_t)o * n_tgt + t] = ff_add_f(terms[(int64_t)o * n_tgt + t], cf);
                 terms[(int64_t)(o | 1u) * n_tgt + t] = ff_add_f(terms[(int64_t)(o | 1u) * n_tgt + t], cb);
@@ -476,7 +474,7 @@ struct PolKD : ItemMap {
     __device__ void fold_flush(uint32_t item, const FA* a) const {
         const int64_t t = tgt_index(item);
 #pragma unroll
-        for (int i = 0; i < NW; ++i) acc[(int64_t)i * n_tgt + t] += a[i];
+        for (int i = 0; i < NW; ++i) atomicAdd(acc + (int64_t)i * n_tgt + t, a[i]);
     }
     __device__ BaseD base_of(uint32_t item, uint32_t cls) const {
         double m = 1.0;
@@ -580,6 +578,9 @@ struct DCBuffers {
     void* carries;
     // folded kernel sums: record arrays (fm, fs, wt, fa) of each ping-pong side
     void* rec[2][4];
+    // kernel sums: per-item base factors of this buffer set's sorts (levels
+    // sorted concurrently have different class bits)
+    void* base;
 };
 template <class Pol>
 FoldRecs<Pol> fold_recs(const DCBuffers& b, int q) {
@@ -738,15 +739,29 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
 // states (nodes of 2^{l+1} sorted by P_{k-1}) each start the recursion one
 // axis lower with the side bit l of the axis-k index added to the class.
 struct OuterBuffers {
-    uint32_t* k[2];
-    uint32_t* m[2];
+    uint32_t* k[kPoolStreams + 1];   // level states: ping-pong, or a ring of S + 1 (concurrent levels)
+    uint32_t* m[kPoolStreams + 1];
     uint32_t* idx;    // index of every item inside its axis-k node
 };
 
+// Inner sorts of concurrent levels: streams used at the lowest tree axis.
+constexpr int kSweepStreams = 2;
+enum : int { OPT_SERIAL = 2 };   // option bit: no concurrent levels (the batched path)
+
+template <class Pol>
+__host__ int sweep_streams(const Pol& pol, int opts) {
+    if constexpr (Pol::kCanFold) {
+        // folded sums flush atomically; per-orthant terms and orthant sums do not
+        return (!pol.terms && !(opts & OPT_SERIAL)) ? kSweepStreams : 1;
+    }
+    return 1;
+}
+
 template <class Pol, int CLSB>
 fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* const* P,
-                  ClassSpec cs, const Pol& pol, OuterBuffers* ob, DCBuffers& ib, int opts, cudaStream_t st) {
-    if (k == 1) return inner_sort<Pol, CLSB>(seq, n, E, P[0], cs, pol, ib, opts, st);
+                  ClassSpec cs, const Pol& pol, OuterBuffers* ob, DCBuffers* ib, int S, int opts,
+                  cudaStream_t st) {
+    if (k == 1) return inner_sort<Pol, CLSB>(seq, n, E, P[0], cs, pol, ib[0], opts, st);
     OuterBuffers& o = ob[k];
     const uint32_t* idx = P[k];
     if (o.idx) {
@@ -754,17 +769,54 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         idx = o.idx;
     }
     FK_TRY(gather_outer(seq, n, P[k - 1], o.k[0], o.m[0], st));
-    int cur = 0;
-    for (int l = 0; l < E; ++l) {
-        MergeArgs a{o.k[cur], o.m[cur], o.k[cur ^ 1], o.m[cur ^ 1], n, l};
-        FK_TRY(plain_merge_level(a, st));
-        cur ^= 1;
+    auto class_of_level = [&](int l) {
         ClassSpec c2 = cs;
         // the enclosing axes keep their bits; axis k contributes bit (k - 2)
         c2.idx[k - 2] = idx;
         c2.lvl[k - 2] = l;
         if (c2.nb < k - 1) c2.nb = k - 1;
-        FK_TRY((recurse<Pol, CLSB>(k - 1, o.m[cur], n, l + 1, P, c2, pol, ob, ib, opts, st)));
+        return c2;
+    };
+    if (k == 2 && S > 1) {
+        // The merges of axis 2 run on the caller's stream, ahead of the inner
+        // sorts, which run on S forked streams (buffers per stream); the level
+        // states form a ring of S + 1, and a merge waits for the inner sort
+        // that last read the state it overwrites.
+        const int R = S + 1;
+        StreamFork fork;
+        FK_TRY(fork.begin(2, st, S));
+        cudaEvent_t ready = fork.ev[0];
+        cudaEvent_t* done = fork.ev + 1;
+        fk_status rc = FK_OK;
+        for (int l = 0; l < E && rc == FK_OK; ++l) {
+            const int in = l % R, out = (l + 1) % R;
+            if (l >= R) {
+                const cudaError_t e = cudaStreamWaitEvent(st, done[(l - R) % R], 0);
+                if (e != cudaSuccess) { rc = cuda_error(e, "level wait"); break; }
+            }
+            MergeArgs a{o.k[in], o.m[in], o.k[out], o.m[out], n, l};
+            rc = plain_merge_level(a, st);
+            if (rc != FK_OK) break;
+            const int q = l % S;
+            cudaError_t e = cudaEventRecord(ready, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(fork.s[q], ready, 0);
+            if (e != cudaSuccess) { rc = cuda_error(e, "level fork"); break; }
+            Pol pq = pol;
+            if constexpr (Pol::kCanFold) pq.base = (decltype(pq.base))ib[q].base;
+            rc = inner_sort<Pol, CLSB>(o.m[out], n, l + 1, P[0], class_of_level(l), pq, ib[q], opts, fork.s[q]);
+            if (rc != FK_OK) break;
+            e = cudaEventRecord(done[l % R], fork.s[q]);
+            if (e != cudaSuccess) rc = cuda_error(e, "level done");
+        }
+        const fk_status rj = fork.end();
+        return rc != FK_OK ? rc : rj;
+    }
+    int cur = 0;
+    for (int l = 0; l < E; ++l) {
+        MergeArgs a{o.k[cur], o.m[cur], o.k[cur ^ 1], o.m[cur ^ 1], n, l};
+        FK_TRY(plain_merge_level(a, st));
+        cur ^= 1;
+        FK_TRY((recurse<Pol, CLSB>(k - 1, o.m[cur], n, l + 1, P, class_of_level(l), pol, ob, ib, S, opts, st)));
     }
     return FK_OK;
 }
@@ -776,24 +828,32 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
                    const Pol& pol, Arena& ar, cudaStream_t st, int levels = -1, int opts = 0) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
+    const int S = d_eff >= 3 ? sweep_streams(pol, opts) : 1;
     OuterBuffers ob[8] = {};
     for (int k = 2; k < d_eff; ++k) {
-        for (int q = 0; q < 2; ++q) { ob[k].k[q] = ar.take<uint32_t>(n); ob[k].m[q] = ar.take<uint32_t>(n); }
+        const int nb = (k == 2 && S > 1) ? S + 1 : 2;
+        for (int q = 0; q < nb; ++q) { ob[k].k[q] = ar.take<uint32_t>(n); ob[k].m[q] = ar.take<uint32_t>(n); }
         ob[k].idx = (k < d_eff - 1) ? ar.take<uint32_t>(n) : nullptr;
     }
-    DCBuffers ib;
-    for (int q = 0; q < 2; ++q) { ib.k[q] = ar.take<uint32_t>(n); ib.m[q] = ar.take<uint32_t>(n); }
+    DCBuffers ib[kPoolStreams] = {};
     const int64_t ctas = (n + MTILE - 1) / MTILE;
-    ib.totals = ar.take<V>((size_t)ctas * 2 * NCH);
-    ib.carries = ar.take<V>((size_t)ctas * 2 * NCH);
-    for (int q = 0; q < 2; ++q)
-        for (int j = 0; j < 4; ++j) ib.rec[q][j] = nullptr;
-    if constexpr (Pol::kCanFold && Pol::kRecords) {
-        for (int q = 0; q < 2; ++q) {
-            ib.rec[q][0] = ar.take<typename Pol::M>((size_t)4 * n);
-            ib.rec[q][1] = ar.take<int>((size_t)4 * n);
-            ib.rec[q][2] = ar.take<typename Pol::M>((size_t)n);
-            ib.rec[q][3] = ar.take<typename Pol::FA>((size_t)Pol::kNW * n);
+    for (int s = 0; s < S; ++s) {
+        for (int q = 0; q < 2; ++q) { ib[s].k[q] = ar.take<uint32_t>(n); ib[s].m[q] = ar.take<uint32_t>(n); }
+        ib[s].totals = ar.take<V>((size_t)ctas * 2 * NCH);
+        ib[s].carries = ar.take<V>((size_t)ctas * 2 * NCH);
+        for (int q = 0; q < 2; ++q)
+            for (int j = 0; j < 4; ++j) ib[s].rec[q][j] = nullptr;
+        ib[s].base = nullptr;
+        if constexpr (Pol::kCanFold) {
+            if (S > 1 && !Pol::kRecords) ib[s].base = ar.take<char>((size_t)n * sizeof(*pol.base));
+        }
+        if constexpr (Pol::kCanFold && Pol::kRecords) {
+            for (int q = 0; q < 2; ++q) {
+                ib[s].rec[q][0] = ar.take<typename Pol::M>((size_t)4 * n);
+                ib[s].rec[q][1] = ar.take<int>((size_t)4 * n);
+                ib[s].rec[q][2] = ar.take<typename Pol::M>((size_t)n);
+                ib[s].rec[q][3] = ar.take<typename Pol::FA>((size_t)Pol::kNW * n);
+            }
         }
     }
     if (ar.sizing) return FK_OK;
@@ -803,7 +863,7 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
     const int E = levels >= 0 ? levels : ceil_log2(n);
     // for k == d_eff-1 the axis index is P[d_eff-1] itself (idx == nullptr above)
     if (d_eff - 1 >= 2) ob[d_eff - 1].idx = nullptr;
-    return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, opts, st);
+    return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, S, opts, st);
 }
 
 }  // namespace dc

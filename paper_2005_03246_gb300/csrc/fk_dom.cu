@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(LNT) k_dom_local(const uint32_t* __restrict__ 
             pref_out[t0 + i] = s_pref[b][pd(i)];
             acc_out[t0 + i] = s_acc[b][pd(i)];
         } else if (s_acc[b][pd(i)]) {
-            C[im.tgt_index(m & kItemMask)] += s_acc[b][pd(i)];
+            atomicAdd(C + im.tgt_index(m & kItemMask), s_acc[b][pd(i)]);
         }
     }
 }
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(NTN) k_dom_nested(const uint32_t* __restrict__
         okey_out[t0 + i] = s_okey[ob * NTP + pd(i)];
         oitem_out[t0 + i] = s_item[s_oslot[ob * NTP + pd(i)]];
         const uint32_t a = s_sum[i];
-        if (a) C[im.tgt_index(s_item[i])] += a;
+        if (a) atomicAdd(C + im.tgt_index(s_item[i]), a);
     }
 }
 
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
             ++j;
         }
         if (last) {
-            if (ac) C[im.tgt_index(mt & kItemMask)] += ac;
+            if (ac) atomicAdd(C + im.tgt_index(mt & kItemMask), ac);
         }
         rk[e] = k; rm[e] = mt; rp[e] = pf; ra[e] = ac;
         cnt = e + 1;

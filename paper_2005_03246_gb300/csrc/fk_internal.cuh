@@ -71,11 +71,15 @@ enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
 
 // Concurrent parts of one call (fk_streams.cu): begin() forks up to k-1
 // library-owned streams from `main` (s[0] == main), end() (or the destructor)
-// joins them back.  Pool 0 serves the batched groups, pool 1 the parts inside
-// one operation.
+// joins them back; ev[] are events of the pool the caller may use meanwhile.
+// Pool 0 serves the batched groups, pool 1 the parts inside one operation,
+// pool 2 the merge levels inside such a part.
 constexpr int kPoolStreams = 8;
+constexpr int kPoolAux = 16;     // extra events a fork may use between begin() and end()
+constexpr int kPools = 3;
 struct StreamFork {
     cudaStream_t s[kPoolStreams] = {};
+    cudaEvent_t ev[kPoolAux] = {};
     int n = 1;
     fk_status begin(int pool, cudaStream_t main, int k);
     fk_status end();

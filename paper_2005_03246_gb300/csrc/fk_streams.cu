@@ -1,9 +1,10 @@
 // fk_streams.cu -- library-owned streams for running independent parts of one
 // call concurrently: forked from the caller's stream by an event and joined
 // back to it by events, so a call stays stream-ordered for its caller and
-// capturable in a CUDA graph.  Two pools per device: one for the groups of
-// the batched path, one for the parts inside a single operation (which the
-// batched path may itself run on a pooled stream).  Each pool's mutex is
+// capturable in a CUDA graph.  Three pools per device: the groups of the
+// batched path, the parts inside one operation (which the batched path may
+// itself run on a pooled stream), and the merge levels inside one of those
+// parts.  Each pool's mutex is
 // held by a call while it enqueues, so overlapping calls from several host
 // threads do not interleave their fork and join events.
 #include <mutex>
@@ -17,10 +18,11 @@ struct Pool {
     cudaStream_t s[kPoolStreams];
     cudaEvent_t fork;
     cudaEvent_t join[kPoolStreams];
+    cudaEvent_t aux[kPoolAux];
     bool ready = false;
 };
-std::mutex g_mu[2];
-Pool g_pool[2][64];
+std::mutex g_mu[kPools];
+Pool g_pool[kPools][64];
 
 }  // namespace
 
@@ -39,9 +41,11 @@ fk_status StreamFork::begin(int which, cudaStream_t main, int k) {
         for (int i = 1; i < kPoolStreams; ++i) FK_CUDA(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
         FK_CUDA(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
         for (int i = 1; i < kPoolStreams; ++i) FK_CUDA(cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming));
+        for (int i = 0; i < kPoolAux; ++i) FK_CUDA(cudaEventCreateWithFlags(&p.aux[i], cudaEventDisableTiming));
         p.ready = true;
     }
     dev_ = dev;
+    for (int i = 0; i < kPoolAux; ++i) ev[i] = p.aux[i];
     FK_CUDA(cudaEventRecord(p.fork, main));
     for (int i = 1; i < n; ++i) {
         s[i] = p.s[i];
