@@ -171,6 +171,18 @@ fk_status gather_outer(const uint32_t* seq, int64_t n, const uint32_t* Pkey, uin
     FK_LAUNCH_CHECK();
     return FK_OK;
 }
+__global__ void k_add_f64(double* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] += src[i];
+}
+
+fk_status add_f64(double* dst, const double* src, int64_t n, cudaStream_t st) {
+    if (n <= 0) return FK_OK;
+    k_add_f64<<<grid_for(n, 256), 256, 0, st>>>(dst, src, n);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
 fk_status iota_u32(uint32_t* a, int64_t n, cudaStream_t st) {
     k_iota<<<grid_for(n, 256), 256, 0, st>>>(a, n);
     FK_LAUNCH_CHECK();

@@ -579,8 +579,11 @@ struct DCBuffers {
     // folded kernel sums: record arrays (fm, fs, wt, fa) of each ping-pong side
     void* rec[2][4];
     // kernel sums: per-item base factors of this buffer set's sorts (levels
-    // sorted concurrently have different class bits)
+    // sorted concurrently have different class bits), and, for the policies
+    // whose longer levels update target sums in place, a private accumulator
+    // (summed into the caller's after the sweep)
     void* base;
+    double* acc;
 };
 template <class Pol>
 FoldRecs<Pol> fold_recs(const DCBuffers& b, int q) {
@@ -594,6 +597,7 @@ fk_status gather_outer(const uint32_t* seq, int64_t n, const uint32_t* Pkey, uin
                        uint32_t* meta, cudaStream_t st);
 fk_status record_index(const uint32_t* seq, int64_t n, int E, uint32_t* idx, cudaStream_t st);
 fk_status iota_u32(uint32_t* a, int64_t n, cudaStream_t st);
+fk_status add_f64(double* dst, const double* src, int64_t n, cudaStream_t st);   // dst += src
 inline int ceil_log2(int64_t n) {
     int e = 0;
     while (((int64_t)1 << e) < n) ++e;
@@ -745,7 +749,7 @@ struct OuterBuffers {
 };
 
 // Inner sorts of concurrent levels: streams used at the lowest tree axis.
-constexpr int kSweepStreams = 2;
+constexpr int kSweepStreams = 4;
 enum : int { OPT_SERIAL = 2 };   // option bit: no concurrent levels (the batched path)
 
 template <class Pol>
@@ -802,7 +806,10 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
             if (e == cudaSuccess) e = cudaStreamWaitEvent(fork.s[q], ready, 0);
             if (e != cudaSuccess) { rc = cuda_error(e, "level fork"); break; }
             Pol pq = pol;
-            if constexpr (Pol::kCanFold) pq.base = (decltype(pq.base))ib[q].base;
+            if constexpr (Pol::kCanFold) {
+                pq.base = (decltype(pq.base))ib[q].base;
+                if (ib[q].acc) pq.acc = ib[q].acc;
+            }
             rc = inner_sort<Pol, CLSB>(o.m[out], n, l + 1, P[0], class_of_level(l), pq, ib[q], opts, fork.s[q]);
             if (rc != FK_OK) break;
             e = cudaEventRecord(done[l % R], fork.s[q]);
@@ -844,8 +851,12 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
         for (int q = 0; q < 2; ++q)
             for (int j = 0; j < 4; ++j) ib[s].rec[q][j] = nullptr;
         ib[s].base = nullptr;
+        ib[s].acc = nullptr;
         if constexpr (Pol::kCanFold) {
-            if (S > 1 && !Pol::kRecords) ib[s].base = ar.take<char>((size_t)n * sizeof(*pol.base));
+            if (S > 1 && !Pol::kRecords) {
+                ib[s].base = ar.take<char>((size_t)n * sizeof(*pol.base));
+                if (s > 0) ib[s].acc = ar.take<double>((size_t)Pol::kNW * pol.n_tgt);
+            }
         }
         if constexpr (Pol::kCanFold && Pol::kRecords) {
             for (int q = 0; q < 2; ++q) {
@@ -863,7 +874,14 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
     const int E = levels >= 0 ? levels : ceil_log2(n);
     // for k == d_eff-1 the axis index is P[d_eff-1] itself (idx == nullptr above)
     if (d_eff - 1 >= 2) ob[d_eff - 1].idx = nullptr;
-    return recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, S, opts, st);
+    for (int s = 1; s < S; ++s)
+        if (ib[s].acc) FK_CUDA(cudaMemsetAsync(ib[s].acc, 0, sizeof(double) * Pol::kNW * pol.n_tgt, st));
+    FK_TRY((recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, S, opts, st)));
+    if constexpr (Pol::kCanFold) {
+        for (int s = 1; s < S; ++s)
+            if (ib[s].acc) FK_TRY(add_f64(pol.acc, ib[s].acc, Pol::kNW * pol.n_tgt, st));
+    }
+    return FK_OK;
 }
 
 }  // namespace dc

@@ -593,25 +593,31 @@ __global__ void k_combine_seg(CTab ct, int d, int64_t n_tgt, const int64_t* __re
 
 using namespace dom;
 
-// Streams for the independent dominance problems of one orthant-count call.
+// Streams for the independent dominance problems of one orthant-count call,
+// and for the concurrent levels of tree axis 2 inside one problem.
 constexpr int kCountStreams = 4;
+constexpr int kLevelStreams = 4;
 
 // Dominance count C_A for the axes in `axes` (sorted, size k >= 2): the
 // innermost merge sort over the second axis by the first, nested inside merge
 // sorts of the outer axes, as in fk_dc_drv.cuh.
-struct DomBuf {
+struct DomInner {          // state of one innermost sort (ping-pong)
     uint32_t* k[2];
     uint32_t* m[2];
     uint32_t* p[2];
     uint32_t* a[2];
-    uint32_t* ok[8][2];
-    uint32_t* om[8][2];
+};
+struct DomBuf {
+    DomInner in[kPoolStreams];               // one per stream of concurrent levels
+    int S;                                   // streams for the levels of tree axis 2
+    uint32_t* ok[8][kPoolStreams + 1];       // level states: ping-pong, or a ring of S + 1 at axis 2
+    uint32_t* om[8][kPoolStreams + 1];
     uint32_t* idx[8];
 };
 
 template <int LT>
 static fk_status dom_local_launch(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, ClassSpecK cs, Items im,
-                                  DomBuf& B, uint32_t* C, int& L0, cudaStream_t st) {
+                                  DomInner& B, uint32_t* C, int& L0, cudaStream_t st) {
     int lt = 0;
     while ((1 << (lt + 1)) <= LT) ++lt;
     L0 = E < lt ? E : lt;
@@ -629,7 +635,7 @@ static fk_status dom_local_launch(const uint32_t* seq, int64_t n, int E, const u
 }
 
 static fk_status dom_inner(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, ClassSpecK cs, Items im,
-                           DomBuf& B, uint32_t* C, int count_tile, cudaStream_t st) {
+                           DomInner& B, uint32_t* C, int count_tile, cudaStream_t st) {
     int L0 = 0;
     if (count_tile == 1) FK_TRY(dom_local_launch<1024>(seq, n, E, P0, cs, im, B, C, L0, st));
     else if (count_tile == 2) FK_TRY(dom_local_launch<4096>(seq, n, E, P0, cs, im, B, C, L0, st));
@@ -651,14 +657,13 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
     if (k == 1) {
         Items it = im;
         it.full = (1u << cs.nb) - 1u;
-        return dom_inner(seq, n, E, P[0], cs, it, B, C, count_tile, st);
+        return dom_inner(seq, n, E, P[0], cs, it, B.in[0], C, count_tile, st);
     }
     const uint32_t* idx = P[k];
     if (B.idx[k]) {
         FK_TRY(dc::record_index(seq, n, E, B.idx[k], st));
         idx = B.idx[k];
     }
-    int cur = 0;
     int l0 = 0;
     if (k == 2) {
         // outer levels whose nodes fit in a tile: one nested launch
@@ -677,15 +682,53 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
     } else {
         FK_TRY(dc::gather_outer(seq, n, P[k - 1], B.ok[k][0], B.om[k][0], st));
     }
-    for (int l = l0; l < E; ++l) {
-        dc::MergeArgs a{B.ok[k][cur], B.om[k][cur], B.ok[k][cur ^ 1], B.om[k][cur ^ 1], n, l};
-        FK_TRY(dc::plain_merge_level(a, st));
-        cur ^= 1;
+    auto class_of_level = [&](int l) {
         ClassSpecK c2 = cs;
         c2.idx[k - 2] = idx;
         c2.lvl[k - 2] = l;
         if (c2.nb < k - 1) c2.nb = k - 1;
-        FK_TRY(dom_recurse(k - 1, B.om[k][cur], n, l + 1, P, c2, im, B, C, count_tile, st));
+        return c2;
+    };
+    if (k == 2 && B.S > 1) {
+        // merges on the caller's stream ahead of the inner sorts, which run on
+        // S forked streams (state per stream); level states in a ring of S + 1
+        const int S = B.S, R = S + 1;
+        StreamFork fork;
+        FK_TRY(fork.begin(2, st, S));
+        cudaEvent_t ready = fork.ev[0];
+        cudaEvent_t* done = fork.ev + 1;
+        fk_status rc = FK_OK;
+        for (int l = l0; l < E && rc == FK_OK; ++l) {
+            const int j = l - l0;
+            const int in = j % R, out = (j + 1) % R;
+            if (j >= R) {
+                const cudaError_t e = cudaStreamWaitEvent(st, done[(j - R) % R], 0);
+                if (e != cudaSuccess) { rc = cuda_error(e, "level wait"); break; }
+            }
+            dc::MergeArgs a{B.ok[k][in], B.om[k][in], B.ok[k][out], B.om[k][out], n, l};
+            rc = dc::plain_merge_level(a, st);
+            if (rc != FK_OK) break;
+            const int q = j % S;
+            cudaError_t e = cudaEventRecord(ready, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(fork.s[q], ready, 0);
+            if (e != cudaSuccess) { rc = cuda_error(e, "level fork"); break; }
+            ClassSpecK c2 = class_of_level(l);
+            Items it = im;
+            it.full = (1u << c2.nb) - 1u;
+            rc = dom_inner(B.om[k][out], n, l + 1, P[0], c2, it, B.in[q], C, count_tile, fork.s[q]);
+            if (rc != FK_OK) break;
+            e = cudaEventRecord(done[j % R], fork.s[q]);
+            if (e != cudaSuccess) rc = cuda_error(e, "level done");
+        }
+        const fk_status rj = fork.end();
+        return rc != FK_OK ? rc : rj;
+    }
+    int cur = 0;
+    for (int l = l0; l < E; ++l) {
+        dc::MergeArgs a{B.ok[k][cur], B.om[k][cur], B.ok[k][cur ^ 1], B.om[k][cur ^ 1], n, l};
+        FK_TRY(dc::plain_merge_level(a, st));
+        cur ^= 1;
+        FK_TRY(dom_recurse(k - 1, B.om[k][cur], n, l + 1, P, class_of_level(l), im, B, C, count_tile, st));
     }
     return FK_OK;
 }
@@ -707,15 +750,20 @@ static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32
         if (__builtin_popcount((unsigned)A) >= 2) ++nbig;
     }
     const int S = std::max(1, std::min(streams, std::min(nbig, kPoolStreams)));
+    // levels of tree axis 2 sorted concurrently (subsets with |A| >= 3)
+    const int SL = (streams > 1 && d >= 3) ? kLevelStreams : 1;
     DomBuf B[kPoolStreams] = {};
     uint32_t* seq[kPoolStreams] = {};
     for (int q = 0; q < S; ++q) {
-        for (int r = 0; r < 2; ++r) {
-            B[q].k[r] = ar.take<uint32_t>(n); B[q].m[r] = ar.take<uint32_t>(n);
-            B[q].p[r] = ar.take<uint32_t>(n); B[q].a[r] = ar.take<uint32_t>(n);
-        }
+        B[q].S = SL;
+        for (int s2 = 0; s2 < SL; ++s2)
+            for (int r = 0; r < 2; ++r) {
+                B[q].in[s2].k[r] = ar.take<uint32_t>(n); B[q].in[s2].m[r] = ar.take<uint32_t>(n);
+                B[q].in[s2].p[r] = ar.take<uint32_t>(n); B[q].in[s2].a[r] = ar.take<uint32_t>(n);
+            }
         for (int k = 2; k < d; ++k) {
-            for (int r = 0; r < 2; ++r) { B[q].ok[k][r] = ar.take<uint32_t>(n); B[q].om[k][r] = ar.take<uint32_t>(n); }
+            const int nb = (k == 2 && SL > 1) ? SL + 1 : 2;
+            for (int r = 0; r < nb; ++r) { B[q].ok[k][r] = ar.take<uint32_t>(n); B[q].om[k][r] = ar.take<uint32_t>(n); }
             B[q].idx[k] = ar.take<uint32_t>(n);
         }
         seq[q] = ar.take<uint32_t>(n);
