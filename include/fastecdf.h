@@ -336,6 +336,10 @@ uint64_t fk_kernel_launches(void);
 void fk_profile_enable(int on);
 void fk_profile_reset(void);
 fk_status fk_profile_read(int family, double* total_ms, uint64_t* launches, double* alg_bytes);
+/* The time the family kept the GPU busy: the union of its launches' intervals
+ * (operations run independent parts on several streams, whose launches
+ * overlap; total_ms above sums them). */
+fk_status fk_profile_busy(int family, double* busy_ms);
 
 #ifdef __cplusplus
 }

@@ -698,4 +698,36 @@ fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xd, un
     return FK_OK;
 }
 
+// Busy time of a family: the length of the union of its launches' intervals
+// (launches of concurrent streams overlap, so their summed durations exceed
+// the time the family kept the GPU busy).  Times are taken relative to the
+// first recorded start event of the session.
+fk_status fk_profile_busy(int family, double* busy_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!busy_ms) return set_error(FK_ERR_INVALID_ARG, "busy_ms is NULL");
+    *busy_ms = 0.0;
+    if (g_prof.empty()) return FK_OK;
+    const cudaEvent_t ref = g_prof.front().a;
+    std::vector<std::pair<double, double>> iv;
+    for (auto& r : g_prof) {
+        if (r.fam != family) continue;
+        FK_CUDA(cudaEventSynchronize(r.b));
+        float t0 = 0.f, t1 = 0.f;
+        FK_CUDA(cudaEventElapsedTime(&t0, ref, r.a));
+        FK_CUDA(cudaEventElapsedTime(&t1, ref, r.b));
+        iv.emplace_back((double)t0, (double)t1);
+    }
+    std::sort(iv.begin(), iv.end());
+    double total = 0.0, cs = 0.0, ce = 0.0;
+    bool open = false;
+    for (auto& v : iv) {
+        if (!open) { cs = v.first; ce = v.second; open = true; continue; }
+        if (v.first > ce) { total += ce - cs; cs = v.first; ce = v.second; }
+        else if (v.second > ce) ce = v.second;
+    }
+    if (open) total += ce - cs;
+    *busy_ms = total;
+    return FK_OK;
+}
+
 }  // extern "C"
