@@ -129,8 +129,13 @@ __global__ void k_batch_factors(const T* __restrict__ xg, int d, int d_eff, int6
         }
         const double r = rint(t), f = t - r;
         F o;
-        o.mp = exp2(f);
-        o.mm = exp2(-f);
+        if constexpr (sizeof(o.mp) == 4) {     // mixed path: FP32 exp2 of the FP64-split fraction
+            o.mp = exp2f((float)f);
+            o.mm = exp2f(-(float)f);
+        } else {
+            o.mp = exp2(f);
+            o.mm = exp2(-f);
+        }
         o.s = (int)r;
         fac[(int64_t)k * n + it] = o;
     }

@@ -1139,7 +1139,9 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
 
 // Carries for merged blocks that span several CTAs: exclusive prefix of the
 // forward totals and exclusive suffix of the backward totals over the CTAs of
-// each merged block.  One thread per (block, channel, direction).
+// each merged block.  One warp per (block, channel, direction): each lane
+// sums a contiguous run of CTAs (in scan order), a warp scan combines the
+// lanes, and each lane writes the carries of its run.
 template <class Pol, int NCH>
 __global__ void k_carries(const typename Pol::V* __restrict__ totals, typename Pol::V* __restrict__ carries,
                           int64_t n, int logR) {
@@ -1148,22 +1150,34 @@ __global__ void k_carries(const typename Pol::V* __restrict__ totals, typename P
     const int64_t ctas = (n + MTILE - 1) / MTILE;
     const int64_t per = R2 / MTILE;            // CTAs per full merged block
     const int64_t nblocks = (ctas + per - 1) / per;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nblocks * NCH * 2) return;
-    const int dir = (int)(t % 2);
-    const int c = (int)((t / 2) % NCH);
-    const int64_t b = t / (2 * NCH);
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // uniform per warp
+    const int lane = threadIdx.x & 31;
+    if (wid >= nblocks * NCH * 2) return;
+    const int dir = (int)(wid % 2);
+    const int c = (int)((wid / 2) % NCH);
+    const int64_t b = wid / (2 * NCH);
     const int64_t c0 = b * per, c1 = min(c0 + per, ctas);
-    V run = Pol::zero();
-    if (dir == 0) {
-        for (int64_t q = c0; q < c1; ++q) {
-            carries[(q * 2 + 0) * NCH + c] = run;
-            run = Pol::add(run, totals[(q * 2 + 0) * NCH + c]);
-        }
-    } else {
-        for (int64_t q = c1 - 1; q >= c0; --q) {
-            carries[(q * 2 + 1) * NCH + c] = run;
-            run = Pol::add(run, totals[(q * 2 + 1) * NCH + c]);
+    const int64_t len = c1 - c0, chunk = (len + 31) / 32;
+    // position of the idx-th CTA in scan order (backward: from the block's end)
+    auto at = [&](int64_t idx) -> int64_t { return ((dir ? c1 - 1 - idx : c0 + idx) * 2 + dir) * NCH + c; };
+    V sum = Pol::zero();
+    for (int64_t i = 0; i < chunk; ++i) {
+        const int64_t idx = lane * chunk + i;
+        if (idx < len) sum = Pol::add(sum, totals[at(idx)]);
+    }
+    V incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = shfl_up_t(incl, o, 32);
+        if (lane >= o) incl = Pol::add(y, incl);
+    }
+    V run = shfl_up_t(incl, 1, 32);
+    if (lane == 0) run = Pol::zero();
+    for (int64_t i = 0; i < chunk; ++i) {
+        const int64_t idx = lane * chunk + i;
+        if (idx < len) {
+            carries[at(idx)] = run;
+            run = Pol::add(run, totals[at(idx)]);
         }
     }
 }

@@ -71,6 +71,20 @@ __global__ void k_record_index(const uint32_t* __restrict__ seq, int64_t n, uint
 // Exponent factors e^{+-v/h} = m * 2^{+-s}: t = v/(h ln 2) in FP64, s the
 // nearest integer, m = 2^{+-(t-s)} evaluated in FP64 (rounded to FP32 for
 // the mixed path).  Axes beyond d (the padding axis of d = 1) get factor 1.
+// The mantissas 2^{+-f} of a factor, |f| <= 1/2 (the exponent split t = s + f
+// is done in FP64 by the caller): FP64 on the FP64 path; on the mixed path,
+// whose mantissas are FP32 anyway, the FP32 exp2 of the FP64-split fraction
+// (no large-argument error can arise for |f| <= 1/2).
+__device__ __forceinline__ void set_mantissas(FacD& o, double f) {
+    o.mp = exp2(f);
+    o.mm = exp2(-f);
+}
+__device__ __forceinline__ void set_mantissas(FacF& o, double f) {
+    const float ff = (float)f;
+    o.mp = exp2f(ff);
+    o.mm = exp2f(-ff);
+}
+
 template <class T, class F>
 __global__ void k_factors(const T* __restrict__ x, const T* __restrict__ z, int d, int d_eff, int64_t n_x,
                           int64_t n, HVec h, F* __restrict__ fac) {
@@ -85,8 +99,7 @@ __global__ void k_factors(const T* __restrict__ x, const T* __restrict__ z, int 
         const double s = rint(t);
         const double f = t - s;
         F o;
-        o.mp = exp2(f);
-        o.mm = exp2(-f);
+        set_mantissas(o, f);
         o.s = (int)s;
         fac[(int64_t)k * n + it] = o;
     }

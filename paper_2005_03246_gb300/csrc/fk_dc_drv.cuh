@@ -674,7 +674,7 @@ fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cu
             }
             const int64_t per = R2 / MTILE;
             const int64_t nblk = ((int64_t)ctas + per - 1) / per;
-            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2, 128), 128, 0, st>>>((const V*)b.totals,
+            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
                                                                               (V*)b.carries, n, m);
             FK_LAUNCH_CHECK();
             carries = (const V*)b.carries;
@@ -721,7 +721,7 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
             }
             const int64_t per = R2 / MTILE;
             const int64_t nblk = ((int64_t)ctas + per - 1) / per;
-            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2, 128), 128, 0, st>>>((const V*)b.totals,
+            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
                                                                               (V*)b.carries, n, m);
             FK_LAUNCH_CHECK();
             ProfScope ps(PF_MERGE_SWEEP, sweep_bytes, st);
