@@ -436,11 +436,14 @@ size_t fk_kde_laplace_backward_workspace(int64_t N, int d, int64_t M, int sample
     const void* z = sample_points ? nullptr : (const void*)1;
     if (points_validate((const void*)1, FK_F32, N, d, z, M, path, false) != FK_OK) return 0;
     double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    // the plan differs with and without weights (terms vs signed sums): the larger
     size_t best = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < 4; ++t) {
         Arena ar;
-        kde_backward_run(nullptr, t ? FK_F64 : FK_F32, N, d, (const void*)1, z, M, h, 0, nullptr, (double*)1,
-                         sample_points ? nullptr : (double*)1, (double*)1, path, ar, 0);
+        // plans pass placeholders: x must be non-NULL, the transposed pass at
+        // explicit targets takes it as its target array
+        kde_backward_run((const void*)1, (t & 1) ? FK_F64 : FK_F32, N, d, (t & 2) ? (const void*)1 : nullptr, z, M, h, 0,
+                         nullptr, (double*)1, sample_points ? nullptr : (double*)1, (double*)1, path, ar, 0);
         if (ar.used > best) best = ar.used;
     }
     return best;
@@ -469,7 +472,7 @@ fk_status fk_kde_laplace_backward(const void* x, fk_dtype xd, int64_t N, int d, 
     FK_TRY(sg.out(grad_z, z ? (size_t)M * d * 8 : 0, &gzp));
     FK_TRY(sg.out(grad_h, (size_t)d * 8, &ghp));
     Arena plan;
-    kde_backward_run(nullptr, xd, N, d, w, z, M, h, flags, nullptr, (double*)grad_w, (double*)grad_z,
+    kde_backward_run((const void*)1, xd, N, d, w, z, M, h, flags, nullptr, (double*)grad_w, (double*)grad_z,
                      (double*)grad_h, path, plan, st);
     Workspace wsp(st);
     Arena ar;
@@ -489,9 +492,10 @@ size_t fk_loo_laplace_workspace(int64_t N, int d, fk_path path) {
     if (points_validate((const void*)1, FK_F32, N, d, nullptr, 0, path, false) != FK_OK) return 0;
     double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     size_t best = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < 4; ++t) {
         Arena ar;
-        loo_run(nullptr, t ? FK_F64 : FK_F32, N, d, (const void*)1, h, (double*)1, (double*)1, path, ar, 0);
+        loo_run((const void*)1, (t & 1) ? FK_F64 : FK_F32, N, d, (t & 2) ? (const void*)1 : nullptr, h, (double*)1,
+                (double*)1, path, ar, 0);
         if (ar.used > best) best = ar.used;
     }
     return best;
@@ -514,7 +518,7 @@ fk_status fk_loo_laplace(const void* x, fk_dtype xd, int64_t N, int d, const voi
     FK_TRY(sg.out(loglik, 8, &lp));
     FK_TRY(sg.out(grad_h, (size_t)d * 8, &ghp));
     Arena plan;
-    loo_run(nullptr, xd, N, d, w, h, (double*)loglik, grad_h, path, plan, st);
+    loo_run((const void*)1, xd, N, d, w, h, (double*)loglik, grad_h, path, plan, st);
     Workspace wsp(st);
     Arena ar;
     FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));

@@ -846,7 +846,7 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
                 }
                 const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
                 Pol::fold_value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
-                add_at<LO>(fe, own, Pol::fold_src(f0[e], g0[e], wt[e]));
+                add_at<LO>(fe, own, Pol::fold_src(f0[e], g0[e], wt[e], pol.is_src(em[e] & kItemMask)));
             }
         }
 #pragma unroll
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
                 }
                 const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
                 Pol::fold_value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
-                add_at<LO>(be, own, Pol::fold_src(f1[e], g1[e], wt[e]));
+                add_at<LO>(be, own, Pol::fold_src(f1[e], g1[e], wt[e], pol.is_src(em[e] & kItemMask)));
             }
         }
         // blocks spanning several threads: the exclusive prefix / suffix of
@@ -881,7 +881,11 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
         }
 #pragma unroll
         for (int e = 0; e < IT; ++e)
-            if (e < cnt && pol.is_tgt(em[e] & kItemMask)) Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e]);
+            if (e < cnt && pol.is_tgt(em[e] & kItemMask)) {
+                M sf, sb;
+                pol.signs((int)(eh[e] >> 16), em[e] >> kItemBits, sf, sb);
+                Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e], sf, sb);
+            }
         local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
     }
     // write the tile out for the longer merge levels (as records when they
@@ -989,8 +993,8 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
                 int g0, g1;
                 rec_move<Pol>(rin, g, rin, -1, half, f0, f1, g0, g1, wt);
                 const int ch = (half << CLSB) | (int)(m >> kItemBits);
-                add_at<Pol>(tf, ch, Pol::fold_src_g(f0, g0, wt));
-                add_at<Pol>(tb, ch, Pol::fold_src_g(f1, g1, wt));
+                add_at<Pol>(tf, ch, Pol::fold_src_g(f0, g0, wt, true));
+                add_at<Pol>(tb, ch, Pol::fold_src_g(f1, g1, wt, true));
             }
         }
         V fe[NCH], be[NCH];
@@ -1079,7 +1083,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
             }
             const int own = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
             Pol::fold_value_g(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
-            add_at<Pol>(fe, own, Pol::fold_src_g(f0[e], g0[e], wt[e]));
+            add_at<Pol>(fe, own, Pol::fold_src_g(f0[e], g0[e], wt[e], pol.is_src(em[e] & kItemMask)));
         }
     }
 #pragma unroll
@@ -1093,7 +1097,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
             }
             const int own = (eh[e] << CLSB) | (int)(em[e] >> kItemBits);
             Pol::fold_value_g(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
-            add_at<Pol>(be, own, Pol::fold_src_g(f1[e], g1[e], wt[e]));
+            add_at<Pol>(be, own, Pol::fold_src_g(f1[e], g1[e], wt[e], pol.is_src(em[e] & kItemMask)));
         }
     }
     if (ts > 1) {
@@ -1126,7 +1130,11 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
             FA acc[NW];
 #pragma unroll
             for (int q = 0; q < NW; ++q) acc[q] = rin.fa[src * NW + q];
-            if (pol.is_tgt(item)) Pol::fold_add(acc, cf[e], cb[e]);
+            if (pol.is_tgt(item)) {
+                M sf, sb;
+                pol.signs(eh[e], em[e] >> kItemBits, sf, sb);
+                Pol::fold_add(acc, cf[e], cb[e], sf, sb);
+            }
             if (!last) {
 #pragma unroll
                 for (int q = 0; q < NW; ++q) rout.fa[(o0 + p0 + e) * NW + q] = acc[q];

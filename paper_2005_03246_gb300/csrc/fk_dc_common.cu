@@ -105,6 +105,13 @@ __global__ void k_factors(const T* __restrict__ x, const T* __restrict__ z, int 
     }
 }
 
+// out[i][t] = C acc[i][t] (signed sums of the gradients: no self term).
+__global__ void k_fin_raw(const double* __restrict__ acc, int64_t n_tgt, int nw, double C, double* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tgt) return;
+    for (int i = 0; i < nw; ++i) out[(int64_t)i * n_tgt + t] = C * acc[(int64_t)i * n_tgt + t];
+}
+
 template <class T, class W>
 __global__ void k_convert(const T* __restrict__ y, int64_t n, W* __restrict__ w) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -326,7 +333,8 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
 // ------------------------------------------------------------------ kernel sums
 fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                         const double* h, unsigned flags, int nw, double* out, double* terms, fk_path path,
-                        Arena& ar, cudaStream_t st, fk_dtype wd) {
+                        Arena& ar, cudaStream_t st, fk_dtype wd, int sgn) {
+    if (sgn >= 0 && (nw != 2 || terms)) return set_error(FK_ERR_INVALID_ARG, "signed sums need nw == 2, no terms");
     if ((int)wd < 0) wd = xd;
     const int d_eff = d < 2 ? 2 : d;
     const bool sample = (z == nullptr);
@@ -357,6 +365,7 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
     FK_SETK(d1, FacD, BaseD, double, double)
     FK_SETK(d2, FacD, BaseD, double, double)
 #undef FK_SETK
+    f1.sgn = f2.sgn = d1.sgn = d2.sgn = sgn;
     const uint32_t* const* P = pos.P;
     auto run = [&]() -> fk_status {
         if (!fp64) return nw == 1 ? sweep_kf1(d_eff, n, P, pos.seq_top, f1, ar, st)
@@ -401,6 +410,11 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
     }
     const int has_self = (sample && !loo) ? 1 : 0;
     const unsigned gt = grid_for(n_tgt, 256);
+    if (sgn >= 0) {
+        k_fin_raw<<<gt, 256, 0, st>>>((const double*)acc, n_tgt, nw, C, out);
+        FK_LAUNCH_CHECK();
+        return FK_OK;
+    }
     if (fp64) {
         k_fin_kernel<double, double><<<gt, 256, 0, st>>>((const double*)acc, n_tgt, nw, C, (const double*)wts, has_self, out);
         FK_LAUNCH_CHECK();

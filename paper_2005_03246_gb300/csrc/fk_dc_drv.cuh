@@ -198,6 +198,7 @@ struct PolKF : ItemMap {
     double* acc;              // [NW][n_tgt] (FP64: flushes of concurrent sorts add atomically)
     FF* terms;                // optional [2^d][n_tgt]
     uint32_t pbmask;
+    int sgn = -1;             // >= 0: every contribution signed by delta_sgn (see signs())
     __device__ static V zero() {
         V r;
 #pragma unroll
@@ -248,10 +249,12 @@ struct PolKF : ItemMap {
         }
     };
     __device__ static FA fa_zero() { return ff_zero(); }
-    __device__ static typename LOps::V fold_src(float m, int s, float wt) {
+    // source weights of an element: channel 0 carries wt (0 without a source
+    // role), channel 1 (two-channel sums) carries 1 for sources only
+    __device__ static typename LOps::V fold_src(float m, int s, float wt, bool src) {
         typename LOps::V r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r.v[i] = sf_term(((NW == 2 && i == 1) ? 1.f : wt) * m, s);
+        for (int i = 0; i < NW; ++i) r.v[i] = sf_term(((NW == 2 && i == 1) ? (src ? 1.f : 0.f) : wt) * m, s);
         return r;
     }
     // kernel values v * (m 2^s) per weight channel, and a += cf + cb
@@ -259,15 +262,24 @@ struct PolKF : ItemMap {
 #pragma unroll
         for (int i = 0; i < NW; ++i) c[i] = v.v[i].m * m * pow2f_any(v.v[i].e + s);
     }
-    __device__ static void fold_add(FA* a, const float* cf, const float* cb) {
+    __device__ static void fold_add(FA* a, const float* cf, const float* cb, float sf, float sb) {
 #pragma unroll
-        for (int i = 0; i < NW; ++i) a[i] = ff_add_f(ff_add_f(a[i], cf[i]), cb[i]);
+        for (int i = 0; i < NW; ++i) a[i] = ff_add_f(ff_add_f(a[i], sf * cf[i]), sb * cb[i]);
+    }
+    // Signs of a target's forward and backward contributions for the signed
+    // sums of axis sgn: +1 for orthants with delta_sgn = +1 (the source at or
+    // below the target on that axis), -1 otherwise; 1 when unsigned.
+    __device__ void signs(int half, uint32_t cls, float& sf, float& sb) const {
+        if (sgn < 0) { sf = sb = 1.f; return; }
+        if (sgn == 0) { sf = 1.f; sb = -1.f; return; }
+        const int up = (sgn == 1) ? half : (int)((cls >> (sgn - 2)) & 1u);
+        sf = sb = up ? 1.f : -1.f;
     }
     // the same for the compensated sums of the longer merge levels
-    __device__ static V fold_src_g(float m, int s, float wt) {
+    __device__ static V fold_src_g(float m, int s, float wt, bool src) {
         V r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r.v[i] = sff_term(((NW == 2 && i == 1) ? 1.f : wt) * m, s);
+        for (int i = 0; i < NW; ++i) r.v[i] = sff_term(((NW == 2 && i == 1) ? (src ? 1.f : 0.f) : wt) * m, s);
         return r;
     }
     __device__ static void fold_value_g(const V& v, float m, int s, float* c) {
@@ -380,7 +392,9 @@ struct PolKF : ItemMap {
         for (int i = 0; i < NW; ++i) {
             const float cf = (f.v[i].hi + f.v[i].lo) * tf * pow2f_any(f.v[i].e + sf);
             const float cb = (b.v[i].hi + b.v[i].lo) * tb * pow2f_any(b.v[i].e + sb);
-            acc[(int64_t)i * n_tgt + t] += (double)cf + (double)cb;
+            float gf, gb;
+            signs(half, pb >> 1, gf, gb);
+            acc[(int64_t)i * n_tgt + t] += (double)(gf * cf) + (double)(gb * cb);
             if (i == 0 && terms) {
                 terms[(int64_t)o * n_tgt + t] = ff_add_f(terms[(int64_t)o * n_tgt + t], cf);
                 terms[(int64_t)(o | 1u) * n_tgt + t] = ff_add_f(terms[(int64_t)(o | 1u) * n_tgt + t], cb);
@@ -405,6 +419,7 @@ struct PolKD : ItemMap {
     double* acc;
     double* terms;
     uint32_t pbmask;
+    int sgn = -1;             // >= 0: every contribution signed by delta_sgn (see signs())
     __device__ static V zero() {
         V r;
 #pragma unroll
@@ -443,21 +458,27 @@ struct PolKD : ItemMap {
         __device__ static V add(V a, V b) { return PolKD::add(a, b); }
     };
     __device__ static FA fa_zero() { return 0.0; }
-    __device__ static V fold_src(double m, int s, double wt) {
+    __device__ static V fold_src(double m, int s, double wt, bool src) {
         V r;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) r.v[i] = sd_term(((NW == 2 && i == 1) ? 1.0 : wt) * m, s);
+        for (int i = 0; i < NW; ++i) r.v[i] = sd_term(((NW == 2 && i == 1) ? (src ? 1.0 : 0.0) : wt) * m, s);
         return r;
     }
     __device__ static void fold_value(const V& v, double m, int s, double* c) {
 #pragma unroll
         for (int i = 0; i < NW; ++i) c[i] = ldexp_i(v.v[i].m * m, max(v.v[i].e + s, -4096));
     }
-    __device__ static void fold_add(FA* a, const double* cf, const double* cb) {
+    __device__ static void fold_add(FA* a, const double* cf, const double* cb, double sf, double sb) {
 #pragma unroll
-        for (int i = 0; i < NW; ++i) a[i] += cf[i] + cb[i];
+        for (int i = 0; i < NW; ++i) a[i] += sf * cf[i] + sb * cb[i];
     }
-    __device__ static V fold_src_g(double m, int s, double wt) { return fold_src(m, s, wt); }
+    __device__ void signs(int half, uint32_t cls, double& sf, double& sb) const {
+        if (sgn < 0) { sf = sb = 1.0; return; }
+        if (sgn == 0) { sf = 1.0; sb = -1.0; return; }
+        const int up = (sgn == 1) ? half : (int)((cls >> (sgn - 2)) & 1u);
+        sf = sb = up ? 1.0 : -1.0;
+    }
+    __device__ static V fold_src_g(double m, int s, double wt, bool src) { return fold_src(m, s, wt, src); }
     __device__ static void fold_value_g(const V& v, double m, int s, double* c) { fold_value(v, m, s, c); }
     __device__ void fold_item(uint32_t item, uint32_t cls, double* fm, int* fs, double& wt) const {
         const BaseD B = base_of(item, cls);
@@ -558,7 +579,9 @@ struct PolKD : ItemMap {
         for (int i = 0; i < NW; ++i) {
             const double cf = ldexp_i(f.v[i].m * tf, max(f.v[i].e + sf, -4096));
             const double cb = ldexp_i(b.v[i].m * tb, max(b.v[i].e + sb, -4096));
-            acc[(int64_t)i * n_tgt + t] += cf + cb;
+            double gf, gb;
+            signs(half, pb >> 1, gf, gb);
+            acc[(int64_t)i * n_tgt + t] += gf * cf + gb * cb;
             if (i == 0 && terms) {
                 terms[(int64_t)o * n_tgt + t] += cf;
                 terms[(int64_t)(o | 1u) * n_tgt + t] += cb;

@@ -57,9 +57,13 @@ fk_status dom_orthant_counts_seg(int d, int64_t n, const int64_t* seg, int segE,
 fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,
                          int64_t M, const uint32_t* mask, void* out, fk_path path, Arena& ar,
                          cudaStream_t st);
-// `wd` is the dtype of w (default: that of x).
+// `wd` is the dtype of w (default: that of x).  sgn >= 0: signed sums for the
+// gradients -- nw must be 2 (weights w and 1) and every contribution carries
+// the sign delta_sgn of its orthant; out[i][t] = C * (signed sum of channel i)
+// with no self term (a pair at distance 0 on axis sgn contributes nothing to
+// the gradients).
 fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
                         int64_t M, const double* h, unsigned flags, int nw, double* out, double* terms,
-                        fk_path path, Arena& ar, cudaStream_t st, fk_dtype wd = (fk_dtype)-1);
+                        fk_path path, Arena& ar, cudaStream_t st, fk_dtype wd = (fk_dtype)-1, int sgn = -1);
 
 }  // namespace fk

@@ -20,6 +20,13 @@
 // The leave-one-out log-likelihood L(h) = (1/N) sum_j log f_{-j}(x_j) and its
 // gradient are the forward pass with FK_LOO and the h-adjoint with
 // g_j = 1 / (N f_{-j}).
+//
+// Without weights (w == 1) the z- and h-adjoints need per axis k only the two
+// signed sums sum_delta delta_k T_delta and sum_delta delta_k U^k_delta, which
+// a target forms inside the folded sweep by signing each contribution with
+// its orthant's delta_k: one two-channel pass (weights x_k and 1) per axis,
+// instead of the 2^d per-orthant terms (mixed path; with weights, and on the
+// FP64 path, the terms are used).
 #include "fk_dc_ops.cuh"
 
 namespace fk {
@@ -80,6 +87,28 @@ __global__ void k_grad_h_axis(const double* __restrict__ Tt, const double* __res
     }
     const double b = block_sum(v);
     if (threadIdx.x == 0) atomicAdd(gh + k, b);
+}
+
+// Signed sums of axis k: a[0][j] = C sum_delta delta_k U_delta (weights x_k),
+// a[1][j] = C sum_delta delta_k T_delta (weights 1).  The distance-weighted
+// sum is z_jk a1 - a0, so
+//   gh[k] += sum_j g_j ( -f_j/h_k + (z_jk a1_j - a0_j) / h_k^2 ),
+//   gz[j][k] = -g_j a1_j / h_k.
+template <class T>
+__global__ void k_grad_signed(const double* __restrict__ a, const double* __restrict__ f,
+                              const double* __restrict__ g, const T* __restrict__ zc, int d, int k, int64_t m,
+                              double hk, double* __restrict__ gz, double* __restrict__ gh) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (j < m) {
+        const double a0 = a[j], a1 = a[m + j];
+        if (gz) gz[j * d + k] = -g[j] * a1 / hk;
+        if (gh) v = g[j] * (-f[j] / hk + ((double)zc[j * d + k] * a1 - a0) / (hk * hk));
+    }
+    if (gh) {
+        const double b = block_sum(v);
+        if (threadIdx.x == 0) atomicAdd(gh + k, b);
+    }
 }
 
 // g_j = 1 / (N f_j); L += (1/N) sum_j log f_j
@@ -154,27 +183,72 @@ static fk_status grad_h_run(const void* x, fk_dtype xd, int64_t N, int d, const 
     return FK_OK;
 }
 
+// z- and h-adjoints of the unweighted KDE from signed sums (gz, gh optional;
+// gh zeroed by the caller).
+static fk_status grad_signed_run(const void* x, fk_dtype xd, int64_t N, int d, const void* z, int64_t M,
+                                 const double* h, unsigned flags, const double* g, const double* f, double* gz,
+                                 double* gh, fk_path path, Arena& ar, cudaStream_t st) {
+    const bool sample = (z == nullptr);
+    const int64_t m = sample ? N : M;
+    double* wx = ar.take<double>((size_t)N);
+    double* a2 = ar.take<double>((size_t)2 * m);
+    if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (signed adjoint)");
+    Nested nest(ar);
+    for (int k = 0; k < d; ++k) {
+        if (!ar.sizing) {
+            if (xd == FK_F32)
+                k_weight_times_coord<float><<<grid_for(N, 256), 256, 0, st>>>((const float*)x, nullptr, d, k, N, wx);
+            else
+                k_weight_times_coord<double><<<grid_for(N, 256), 256, 0, st>>>((const double*)x, nullptr, d, k, N, wx);
+            FK_LAUNCH_CHECK();
+        }
+        FK_TRY(points_kernel(x, xd, N, d, ar.sizing ? (const double*)1 : wx, z, M, h, flags, 2,
+                             ar.sizing ? (double*)1 : a2, nullptr, path, ar, st, FK_F64, k));
+        nest.done();
+        if (!ar.sizing && m > 0) {
+            const void* zc = sample ? x : z;
+            if (xd == FK_F32)
+                k_grad_signed<float><<<grid_for(m, 256), 256, 0, st>>>(a2, f, g, (const float*)zc, d, k, m, h[k], gz, gh);
+            else
+                k_grad_signed<double><<<grid_for(m, 256), 256, 0, st>>>(a2, f, g, (const double*)zc, d, k, m, h[k], gz, gh);
+            FK_LAUNCH_CHECK();
+        }
+    }
+    nest.finish();
+    return FK_OK;
+}
+
 fk_status kde_backward_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                            const double* h, unsigned flags, const double* g, double* gw, double* gz, double* gh,
                            fk_path path, Arena& ar, cudaStream_t st) {
     const bool sample = (z == nullptr);
     const int64_t m = sample ? N : M;
     const int no = 1 << d;
-    double* T = (gz || gh) ? ar.take<double>((size_t)no * m) : nullptr;
+    // signed sums instead of per-orthant terms: unweighted, mixed path (the
+    // FP64 path's cost is FP64 arithmetic, which two channels double)
+    const bool fast = (w == nullptr) && path == FK_PATH_MIXED;
+    double* T = ((gz || gh) && !fast) ? ar.take<double>((size_t)no * m) : nullptr;
     double* f = (gz || gh) ? ar.take<double>((size_t)m) : nullptr;
     if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (kde backward)");
     Nested nest(ar);
-    if (gz || gh) {
+    if ((gz || gh) && fast) {
+        FK_TRY(points_kernel(x, xd, N, d, nullptr, z, M, h, flags, 1, ar.sizing ? (double*)1 : f, nullptr, path, ar, st));
+        nest.done();
+        if (gh && !ar.sizing) FK_CUDA(cudaMemsetAsync(gh, 0, (size_t)d * sizeof(double), st));
+        FK_TRY(grad_signed_run(x, xd, N, d, z, M, h, flags, g, f, gz, gh, path, ar, st));
+        nest.done();
+    }
+    if ((gz || gh) && !fast) {
         FK_TRY(points_kernel(x, xd, N, d, w, z, M, h, flags, 1, f, ar.sizing ? (double*)1 : T, path, ar, st));
         nest.done();
     }
-    if (gz && !ar.sizing && m > 0) {
+    if (gz && !fast && !ar.sizing && m > 0) {
         dc::HVec hv;
         for (int k = 0; k < 8; ++k) hv.v[k] = (k < d) ? h[k] : 1.0;
         k_grad_z<<<grid_for(m, 256), 256, 0, st>>>(T, g, hv, d, m, gz);
         FK_LAUNCH_CHECK();
     }
-    if (gh) {
+    if (gh && !fast) {
         if (!ar.sizing) FK_CUDA(cudaMemsetAsync(gh, 0, (size_t)d * sizeof(double), st));
         FK_TRY(grad_h_run(x, xd, N, d, w, z, M, h, flags, g, f, T, gh, path, ar, st));
         nest.done();
@@ -202,12 +276,14 @@ fk_status kde_backward_run(const void* x, fk_dtype xd, int64_t N, int d, const v
 fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* h, double* L,
                   double* gh, fk_path path, Arena& ar, cudaStream_t st) {
     const int no = 1 << d;
-    double* T = ar.take<double>((size_t)no * N);
+    const bool fast = (w == nullptr) && path == FK_PATH_MIXED;   // as in kde_backward_run
+    double* T = (gh && !fast) ? ar.take<double>((size_t)no * N) : nullptr;
     double* f = ar.take<double>((size_t)N);
     double* g = ar.take<double>((size_t)N);
     if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (loo)");
     Nested nest(ar);
-    FK_TRY(points_kernel(x, xd, N, d, w, nullptr, 0, h, FK_LOO, 1, f, ar.sizing ? (double*)1 : T, path, ar, st));
+    FK_TRY(points_kernel(x, xd, N, d, w, nullptr, 0, h, FK_LOO, 1, f,
+                         (gh && !fast) ? (ar.sizing ? (double*)1 : T) : nullptr, path, ar, st));
     nest.done();
     if (!ar.sizing) {
         FK_CUDA(cudaMemsetAsync(L, 0, sizeof(double), st));
@@ -216,7 +292,8 @@ fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, c
     }
     if (gh) {
         if (!ar.sizing) FK_CUDA(cudaMemsetAsync(gh, 0, (size_t)d * sizeof(double), st));
-        FK_TRY(grad_h_run(x, xd, N, d, w, nullptr, 0, h, FK_LOO, g, f, T, gh, path, ar, st));
+        if (fast) FK_TRY(grad_signed_run(x, xd, N, d, nullptr, 0, h, FK_LOO, g, f, nullptr, gh, path, ar, st));
+        else FK_TRY(grad_h_run(x, xd, N, d, w, nullptr, 0, h, FK_LOO, g, f, T, gh, path, ar, st));
         nest.done();
     }
     nest.finish();

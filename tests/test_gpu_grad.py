@@ -132,3 +132,20 @@ def test_bandwidth_selection_steps_match_oracle_gradients():
         assert abs(L - rL) <= 1e-9 * max(1.0, abs(rL))
         assert _err(g, rg) <= 1e-9
     assert hist[-1][1] >= hist[0][1]           # ascent increased the likelihood
+
+
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+def test_backward_unweighted_explicit_targets_d3(path):
+    """d=3, N=70000 sources, 300 explicit targets, no weights (the signed-sum
+    adjoint on the mixed path): every output against the oracle.  At this
+    shape the transposed grad-w pass is the largest part of the plan."""
+    r = np.random.default_rng(71)
+    x = _pts(70000, 3, 72)
+    z = (x[r.choice(70000, 300, replace=False)] + r.normal(0.0, 0.05, (300, 3))).astype(np.float32)
+    g = r.standard_normal(300)
+    h = np.array([0.1, 0.12, 0.15])
+    gw, gz, gh = _fk().kde_laplace_backward(_t(x), h, _t(g), z=_t(z), path=path)
+    rw, rz, rh = oracle.kde_grad(x, h, g, z=z)
+    assert _err(gw.cpu().numpy(), rw) <= TOL[path]
+    assert _err(gz.cpu().numpy(), rz) <= TOL[path]
+    assert _err(gh.cpu().numpy(), rh) <= TOL[path]

@@ -208,6 +208,21 @@ def test_kreg(path):
     assert np.max(np.abs(got - ref)) <= TOL[path] * 10 * np.abs(y).max()
 
 
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_kreg_explicit_targets(path, d):
+    """Nadaraya-Watson at explicit targets: the target items carry no weight
+    in either channel (numerator y, denominator 1)."""
+    r = np.random.default_rng(60 + d)
+    x = r.standard_normal((5000, d)).astype(np.float32)
+    y = (np.sin(x.sum(axis=1)) + 0.1 * r.standard_normal(5000)).astype(np.float32)
+    z = (r.standard_normal((700, d)) * 1.1).astype(np.float32)
+    h = np.linspace(0.2, 0.35, d)
+    got = _fk().kreg_laplace(_t(x), _t(y), h, z=_t(z), path=path).cpu().numpy()
+    ref = oracle.kreg_laplace(x, y, h, z=z)
+    assert np.max(np.abs(got - ref)) <= TOL[path] * 10 * np.abs(y).max()
+
+
 def test_kde_full_size_d3_sampled():
     """d=3, N=1e6, h=0.1 (the paper's bandwidth): 1024 sampled targets."""
     x = datagen.ecdf_gauss3()["x"]
