@@ -49,7 +49,7 @@ H = 0.1
 WORKLOAD = "ecdf_gauss3_d3_n1e6_grid256_kde_h0.1"
 
 
-def _args():
+def _args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -61,7 +61,7 @@ def _args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
                     help="run one operation per step (profiling of a single kernel family)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def _dist():
@@ -220,6 +220,19 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU arm
 
 
+def aggregate_replicas(total_ms, steps, n, ws, device="cpu"):
+    """Whole-job throughput of `ws` independent replicas, each timing `steps`
+    steps of `n` points in `total_ms`: the step time is the slowest rank's
+    (all-reduce MAX over the process group when ws > 1) and the value counts
+    the points of all ranks.  Returns (ms_per_step, points per second)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_step = float(t.item()) / steps
+    return ms_step, ws * n / (ms_step / 1e3)
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -283,11 +296,7 @@ def run_ours(args):
     lib.fk_profile_enable(0)
     clk = clocks.stop()
     total_ms = float(sum(times))
-    t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    ms_step = float(t_max.item()) / args.steps
-    value = ws * n / (ms_step / 1e3)
+    ms_step, value = aggregate_replicas(total_ms, args.steps, n, ws, dev)
 
     # ---- roofline of the dominant kernel family
     fams = {}
