@@ -87,6 +87,7 @@ struct StreamFork {
     cudaStream_t st = nullptr;
     int pool = 0;
     int dev_ = 0;
+    int slot_ = 0;
     bool forked = false;
     std::unique_lock<std::mutex> lock;
 };

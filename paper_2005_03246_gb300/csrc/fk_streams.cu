@@ -21,8 +21,17 @@ struct Pool {
     cudaEvent_t aux[kPoolAux];
     bool ready = false;
 };
-std::mutex g_mu[kPools];
-Pool g_pool[kPools][64];
+// Pool instances per device: a call forks onto the instance its own stream
+// maps to, so operations issued from different streams fork onto different
+// streams and can overlap.
+constexpr int kSlots = 4;
+std::mutex g_mu[kPools][kSlots];
+Pool g_pool[kPools][64][kSlots];
+
+int slot_of(cudaStream_t st) {
+    const uintptr_t v = (uintptr_t)st;
+    return (int)((v ^ (v >> 7) ^ (v >> 13)) % kSlots);
+}
 
 }  // namespace
 
@@ -35,8 +44,9 @@ fk_status StreamFork::begin(int which, cudaStream_t main, int k) {
     FK_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return set_error(FK_ERR_UNSUPPORTED, "device index %d", dev);
     pool = which;
-    lock = std::unique_lock<std::mutex>(g_mu[which]);
-    Pool& p = g_pool[which][dev];
+    slot_ = slot_of(main);
+    lock = std::unique_lock<std::mutex>(g_mu[which][slot_]);
+    Pool& p = g_pool[which][dev][slot_];
     if (!p.ready) {
         for (int i = 1; i < kPoolStreams; ++i) FK_CUDA(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
         FK_CUDA(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
@@ -58,7 +68,7 @@ fk_status StreamFork::begin(int which, cudaStream_t main, int k) {
 fk_status StreamFork::end() {
     if (!forked) return FK_OK;
     forked = false;
-    Pool& p = g_pool[pool][dev_];
+    Pool& p = g_pool[pool][dev_][slot_];
     fk_status rc = FK_OK;
     for (int i = 1; i < n; ++i) {
         const cudaError_t e1 = cudaEventRecord(p.join[i], p.s[i]);
