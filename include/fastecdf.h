@@ -35,8 +35,10 @@
  *   size returned by the matching *_workspace function (256-byte aligned).
  *   If ws == NULL the library allocates and frees its scratch itself
  *   (stream-ordered).  A non-NULL ws that is too small returns FK_ERR_WORKSPACE.
- * Limits.  1 <= d <= 4 for the sample-point (divide-and-conquer) calls and
- *   1 <= d <= 8 for the grid call; N + M must be below 2^26 items on the
+ * Limits.  1 <= d <= 8 for the grid call and for orthant counts at the
+ *   sample points (fk_ecdf_points / fk_esf_points with y == NULL; the work
+ *   grows as N log^(d-1) N); 1 <= d <= 4 for the other sample-point
+ *   (divide-and-conquer) calls; N + M must be below 2^26 items on the
  *   sample-point path (2N + ... when orthant sums are taken at the sample
  *   points, which doubles each point into a source and a target copy).
  *   Other values return FK_ERR_UNSUPPORTED.

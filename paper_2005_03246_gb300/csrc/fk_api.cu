@@ -287,10 +287,13 @@ fk_status fk_ecdf_grid(const void* x, fk_dtype xd, int64_t N, int d, const void*
 }
 
 // ------------------------------------------------------------------ sample-point path
+// max_d: 8 for orthant counts (inclusion-exclusion over dominance counts),
+// 4 for the weighted and kernel sums (2^(d-1) channels per sweep).
 static fk_status points_validate(const void* x, fk_dtype xd, int64_t N, int d, const void* z, int64_t M,
-                                 fk_path path, bool doubled) {
+                                 fk_path path, bool doubled, int max_d = 4) {
     FK_TRY(check_common(x, xd, N, d, path));
-    if (d > 4) return set_error(FK_ERR_UNSUPPORTED, "the sample-point path supports d <= 4");
+    if (d > max_d)
+        return set_error(FK_ERR_UNSUPPORTED, "this sample-point call supports d <= %d (counts: d <= 8)", max_d);
     if (z && M < 0) return set_error(FK_ERR_INVALID_ARG, "M must be >= 0");
     const int64_t items = z ? N + M : (doubled ? 2 * N : N);
     if (items >= ((int64_t)1 << dc::kItemBits))
@@ -307,7 +310,7 @@ static fk_status check_h(const double* h, int d) {
 
 size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
     const void* z = sample_points ? nullptr : (const void*)1;
-    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, true) != FK_OK) return 0;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, true, weighted ? 4 : 8) != FK_OK) return 0;
     size_t best = 0;
     for (int t = 0; t < 2; ++t) {   // size for both dtypes (FP64 keys are wider)
         Arena ar;
@@ -322,7 +325,7 @@ static fk_status ecdf_points_impl(const void* x, fk_dtype xd, int64_t N, int d, 
                                   int64_t M, const uint32_t* mask, void* out, fk_path path, void* ws,
                                   size_t ws_bytes, fk_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    FK_TRY(points_validate(x, xd, N, d, z, M, path, true));
+    FK_TRY(points_validate(x, xd, N, d, z, M, path, true, y ? 4 : 8));
     const int64_t m_out = z ? M : N;
     int nsel = 0;
     for (int o = 0; o < (1 << d); ++o)

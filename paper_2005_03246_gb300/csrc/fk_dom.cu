@@ -534,7 +534,7 @@ __global__ void k_seq_from_pos(const uint32_t* __restrict__ P, int64_t n, uint32
     if (it < n) seq[P[it]] = (uint32_t)it;
 }
 
-struct CTab { const uint32_t* c[16]; };   // C_A for every subset A of the d axes (A as a bitmask)
+struct CTab { const uint32_t* c[256]; };   // C_A for every subset A of the d <= 8 axes (A as a bitmask)
 
 // Orthant o: sum over subsets T of neg(o) of (-1)^|T| C_{pos(o) | T}.
 __global__ void k_combine(CTab ct, int d, int64_t n_tgt, uint32_t n_src, dc::SelMap sel, int64_t* __restrict__ out) {
@@ -816,7 +816,7 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
                              const uint32_t* const* P, const uint32_t* mask, int64_t* out, Arena& ar,
                              cudaStream_t st) {
     const int nsub = 1 << d;
-    uint32_t* Cs[16] = {};
+    uint32_t* Cs[256] = {};
     Items im{n_src, tgt_off, n_tgt, 0u, nullptr, 0};
     FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams));
     if (ar.sizing) return FK_OK;
@@ -836,7 +836,7 @@ fk_status dom_orthant_counts_seg(int d, int64_t n, const int64_t* seg, int segE,
                                  const uint32_t* const* P, BatchOut bo, int64_t* out, Arena& ar,
                                  cudaStream_t st, int count_tile) {
     const int nsub = 1 << d;
-    uint32_t* Cs[16] = {};
+    uint32_t* Cs[256] = {};
     Items im{0, 0, n_tgt, 0u, seg, segE};
     FK_TRY(dom_counts_core(d, n, im, segE, P, Cs, ar, st, count_tile));
     if (ar.sizing || n_tgt == 0) return FK_OK;

@@ -88,3 +88,14 @@ def test_batched_config_default_and_validation():
                     c.streams, c.coarsen, c.count_tile, c.kernel_tile = s, co, ct, kt
                     assert tune >= lib.fk_batched_workspace_ex(sets, 4, _lib.FK_F32, what, _lib.FK_PATH_MIXED,
                                                                ctypes.byref(c))
+
+
+def test_sample_point_dimension_limits():
+    """Counts at the sample points accept d <= 8, weighted sums d <= 4."""
+    from paper_2005_03246_gb300 import _lib
+    lib = _lib.load()
+    for d in (5, 8):
+        assert lib.fk_ecdf_points_workspace(1000, d, 0, 1, 0, 0) > 0
+        assert lib.fk_ecdf_points_workspace(1000, d, 0, 1, 1, 0) == 0
+    assert lib.fk_ecdf_points_workspace(1000, 9, 0, 1, 0, 0) == 0
+    assert lib.fk_kde_laplace_workspace(1000, 5, 0, 1, 0, 0) == 0

@@ -255,3 +255,20 @@ def test_kernel_sums_with_zero_weights_and_wide_spread(path):
     rk = oracle.kreg_laplace(x, y, h)
     ok = np.isfinite(rk)
     assert np.max(np.abs(gk[ok] - rk[ok])) <= TOL[path] * 10 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("d,n", [(5, 1500), (6, 900), (8, 300)])
+def test_orthant_counts_high_dimension(d, n):
+    """Exact counts at the sample points for d = 5..8 (inclusion-exclusion
+    over dominance counts of up to 8 axes), with ties; explicit targets with
+    an orthant mask; the ESF."""
+    x = _points(n, d, seed=700 + d)
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    assert got.shape == (1 << d, n)
+    assert np.array_equal(got, oracle.orthant_sums(x))
+    z = _points(120, d, seed=800 + d)
+    sel = [0, 1, (1 << d) - 1, 5, (1 << (d - 1))]
+    got_z = _fk().ecdf_points(_t(x), z=_t(z), orthants=sel).cpu().numpy()
+    assert np.array_equal(got_z, oracle.orthant_sums(x, z=z, mask=sel))
+    esf = _fk().esf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(esf.reshape(-1), oracle.orthant_sums(x, mask=[(1 << d) - 1])[0])
