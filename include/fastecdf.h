@@ -88,7 +88,7 @@ const char* fk_version(void);
  * fk_ecdf_grid -- orthant sums on a rectilinear grid (Sec. 2.1, Algorithm 1,
  * with the local sums of Appendix A, Algorithms 6-7).
  *   z_axes : concatenation of the d grid axes, axis k holding M[k] strictly
- *            increasing FP64 values (P: "z_{k,1} < ... < z_{k,M_k}"); host or
+ *            increasing FP64 values (as eq. partial sums requires); host or
  *            device.  Not strictly increasing -> FK_ERR_INVALID_ARG.
  *   M      : HOST array of d axis lengths, each >= 1.
  *   y      : [N] weights or NULL (exact int64 counts).
@@ -105,6 +105,36 @@ fk_status fk_ecdf_grid(const void* x, fk_dtype xdtype, int64_t N, int d, const v
                        const double* z_axes, const int64_t* M,
                        const uint32_t* orthant_mask, void* out, fk_path path,
                        void* ws, size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_kde_grid -- the Laplacian KDE of eq. (Laplacian kde nD) at every point
+ * of a rectilinear grid (x, w, z_axes, M as fk_ecdf_grid; h [d] > 0):
+ *   out[M[0]]...[M[d-1]] (double) = 1/(2^d N prod h) sum_i w_i e^{-sum_k |x_ik - z_k| / h_k}.
+ * The grid form of eq. (Laplacian decomposition nD): each point enters one
+ * histogram channel per orthant with its factors relative to its own cell's
+ * grid lines (all <= 1), and per-axis linear recurrences with the decays
+ * e^{-(z_{k,s} - z_{k,s-1}) / h_k} (<= 1) carry them to every grid point --
+ * the fast summation of Sec. 2.1 with a decay.  Exact at the grid points, no
+ * exponent can overflow, any strictly increasing axes.  FK_PATH_MIXED takes
+ * the point factors with an FP32 exponential (the recurrences stay FP64).
+ * Workspace: 2 x 2^d x prod(M_k + 1) doubles.
+ */
+size_t fk_kde_grid_workspace(int64_t N, int d, const int64_t* M, fk_path path);
+fk_status fk_kde_grid(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w,
+                      const double* z_axes, const int64_t* M, const double* h, double* out,
+                      fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_grid_interp -- multilinear interpolation of a grid function
+ * f [M[0]]...[M[d-1]] (double, device or host; e.g. the output of
+ * fk_kde_grid) at Q points q [Q][d] (qdtype): out [Q] double.  Coordinates
+ * outside [z_{k,0}, z_{k,M_k - 1}] are clamped to the nearest grid line.
+ * Workspace: fk_grid_interp_workspace() bytes (or NULL: allocated).
+ */
+size_t fk_grid_interp_workspace(void);
+fk_status fk_grid_interp(const double* f, int d, const double* z_axes, const int64_t* M, const void* q,
+                         fk_dtype qdtype, int64_t Q, double* out, void* ws, size_t ws_bytes,
+                         fk_stream_t stream);
 
 /*
  * -------------------------------------------------------- sample-point path

@@ -17,6 +17,7 @@ from . import _lib
 from ._lib import FastEcdfError
 
 __all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplace", "kde", "Batched",
+           "kde_grid", "grid_interp",
            "kde_laplace_backward", "loo_laplace", "select_bandwidth_loo",
            "FastEcdfError", "mask_words"]
 
@@ -110,6 +111,56 @@ def ecdf_grid(x, axes, y=None, orthants=None, path="mixed"):
                           M.ctypes.data_as(ctypes.c_void_p), mw.ctypes.data_as(ctypes.c_void_p),
                           _ptr(out), pc, _ptr(ws), wsb, _stream_ptr(dev))
     _lib.check(rc, "fk_ecdf_grid")
+    return out
+
+
+def _axes_tensor(axes, dev):
+    M = np.array([len(a) for a in axes], dtype=np.int64)
+    z = _torch().as_tensor(np.concatenate([np.asarray(a, dtype=np.float64) for a in axes]), device=dev)
+    return M, z
+
+
+def kde_grid(x, h, axes, w=None, path="mixed"):
+    """Laplacian KDE (eq. Laplacian kde nD) at every point of the rectilinear
+    grid ``axes`` (list of d strictly increasing 1-D arrays): the grid form of
+    eq. Laplacian decomposition nD with per-axis decaying recurrences, exact at
+    the grid points.  Returns float64 [M_1, ..., M_d]."""
+    torch = _torch()
+    lib = _lib.load()
+    x = _prep_points(x)
+    n, d = x.shape
+    dev = x.device
+    M, z = _axes_tensor(axes, dev)
+    w = _weights(w, x)
+    hh = _h_array(h, d)
+    out = torch.empty(tuple(int(m) for m in M), dtype=torch.float64, device=dev)
+    pc = _path_code(path)
+    need = lib.fk_kde_grid_workspace(n, d, M.ctypes.data_as(ctypes.c_void_p), pc)
+    if need == 0:
+        _lib.check(-1, "fk_kde_grid_workspace")
+    ws, wsb = _workspace(need, dev)
+    rc = lib.fk_kde_grid(_ptr(x), _dtype_code(x.dtype), n, d, _ptr(w), _ptr(z), M.ctypes.data_as(ctypes.c_void_p),
+                         hh.ctypes.data_as(ctypes.c_void_p), _ptr(out), pc, _ptr(ws), wsb, _stream_ptr(dev))
+    _lib.check(rc, "fk_kde_grid")
+    return out
+
+
+def grid_interp(f, axes, q):
+    """Multilinear interpolation of the grid function f [M_1, ..., M_d]
+    (float64, e.g. kde_grid's output) at the points q [Q, d]; coordinates
+    outside the grid box are clamped to it.  Returns float64 [Q]."""
+    torch = _torch()
+    lib = _lib.load()
+    q = _prep_points(q)
+    nq, d = q.shape
+    dev = q.device
+    M, z = _axes_tensor(axes, dev)
+    f = f.to(device=dev, dtype=torch.float64).contiguous()
+    out = torch.empty((nq,), dtype=torch.float64, device=dev)
+    ws, wsb = _workspace(lib.fk_grid_interp_workspace(), dev)
+    rc = lib.fk_grid_interp(_ptr(f), d, _ptr(z), M.ctypes.data_as(ctypes.c_void_p), _ptr(q), _dtype_code(q.dtype),
+                            nq, _ptr(out), _ptr(ws), wsb, _stream_ptr(dev))
+    _lib.check(rc, "fk_grid_interp")
     return out
 
 

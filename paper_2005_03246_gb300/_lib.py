@@ -41,6 +41,10 @@ SIGNATURES = {
     "fk_device_status": (I, [P]),
     "fk_ecdf_grid_workspace": (SZ, [I64, I, P, I, I]),
     "fk_ecdf_grid": (I, [P, I, I64, I, P, P, P, P, P, I, P, SZ, P]),
+    "fk_kde_grid_workspace": (SZ, [I64, I, P, I]),
+    "fk_kde_grid": (I, [P, I, I64, I, P, P, P, P, P, I, P, SZ, P]),
+    "fk_grid_interp_workspace": (SZ, []),
+    "fk_grid_interp": (I, [P, I, P, P, P, I, I64, P, P, SZ, P]),
     "fk_ecdf_points_workspace": (SZ, [I64, I, I64, I, I, I]),
     "fk_ecdf_points": (I, [P, I, I64, I, P, P, I64, P, P, I, P, SZ, P]),
     "fk_esf_points": (I, [P, I, I64, I, P, P, I64, P, I, P, SZ, P]),

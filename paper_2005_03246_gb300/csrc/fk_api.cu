@@ -18,6 +18,12 @@ fk_status kde_backward_run(const void* x, fk_dtype xd, int64_t N, int d, const v
 fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* h, double* L,
                   double* gh, fk_path path, Arena& ar, cudaStream_t st);
 
+fk_status kde_grid_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* z_dev,
+                       const int64_t* M, const double* h, double* out, fk_path path, Arena& ar, cudaStream_t st,
+                       int* err_word);
+fk_status grid_interp_run(const double* f, int d, const double* z_dev, const int64_t* M, const void* q, fk_dtype qd,
+                          int64_t nq, double* out, Arena& ar, cudaStream_t st, int* err_word);
+
 fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
                       double* kde_out, fk_path path, const BatchCfg& cfg, Arena& ar, cudaStream_t st);
 
@@ -286,6 +292,110 @@ fk_status fk_ecdf_grid(const void* x, fk_dtype xd, int64_t N, int d, const void*
     return sg.finish();
 }
 
+static fk_status check_h(const double* h, int d) {
+    if (!h) return set_error(FK_ERR_INVALID_ARG, "h is NULL");
+    for (int k = 0; k < d; ++k)
+        if (!(h[k] > 0.0) || !(h[k] < 1e300)) return set_error(FK_ERR_INVALID_ARG, "h[%d] must be finite and > 0", k);
+    return FK_OK;
+}
+
+// host-side strict monotonicity of host-resident axes
+static fk_status check_axes_host(const double* z_axes, int d, const int64_t* M) {
+    if (is_device_pointer(z_axes)) return FK_OK;
+    int64_t off = 0;
+    for (int k = 0; k < d; ++k) {
+        for (int64_t j = 0; j < M[k]; ++j) {
+            const double v = z_axes[off + j];
+            if (!(v == v) || (j > 0 && !(z_axes[off + j - 1] < v)))
+                return set_error(FK_ERR_INVALID_ARG, "grid axis %d not strictly increasing at %lld", k, (long long)j);
+        }
+        off += M[k];
+    }
+    return FK_OK;
+}
+
+size_t fk_kde_grid_workspace(int64_t N, int d, const int64_t* M, fk_path path) {
+    if (grid_validate((const void*)1, FK_F32, N, d, M, path) != FK_OK) return 0;
+    Arena ar;
+    int one = 0;
+    double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    kde_grid_run(nullptr, FK_F32, N, d, nullptr, nullptr, M, h, nullptr, path, ar, 0, &one);
+    return ar.used;
+}
+
+fk_status fk_kde_grid(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* z_axes,
+                      const int64_t* M, const double* h, double* out, fk_path path, void* ws, size_t ws_bytes,
+                      fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(grid_validate(x, xd, N, d, M, path));
+    FK_TRY(check_h(h, d));
+    if (!z_axes) return set_error(FK_ERR_INVALID_ARG, "z_axes is NULL");
+    if (!out) return set_error(FK_ERR_INVALID_ARG, "out is NULL");
+    FK_TRY(check_axes_host(z_axes, d, M));
+    int64_t ztot = 0, gpts = 1;
+    for (int k = 0; k < d; ++k) { ztot += M[k]; gpts *= M[k]; }
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xp = nullptr, *wp = nullptr, *zp = nullptr;
+    void* op = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xp));
+    FK_TRY(sg.in(w, (size_t)N * ds, &wp));
+    FK_TRY(sg.in(z_axes, (size_t)ztot * sizeof(double), &zp));
+    FK_TRY(sg.out(out, (size_t)gpts * 8, &op));
+    Arena plan;
+    int dummy = 0;
+    kde_grid_run(nullptr, xd, N, d, w, nullptr, M, h, nullptr, path, plan, st, &dummy);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    int* errw = nullptr;
+    FK_TRY(device_error_word(&errw));
+    FK_TRY(kde_grid_run(xp, xd, N, d, wp, (const double*)zp, M, h, (double*)op, path, ar, st, errw));
+    return sg.finish();
+}
+
+size_t fk_grid_interp_workspace(void) {
+    Arena ar;
+    int one = 0;
+    int64_t M[1] = {1};
+    grid_interp_run(nullptr, 1, nullptr, M, nullptr, FK_F64, 0, nullptr, ar, 0, &one);
+    return ar.used;
+}
+
+fk_status fk_grid_interp(const double* f, int d, const double* z_axes, const int64_t* M, const void* q,
+                         fk_dtype qd, int64_t Q, double* out, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (qd != FK_F32 && qd != FK_F64) return set_error(FK_ERR_INVALID_ARG, "qdtype must be FK_F32 or FK_F64");
+    if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "grid_interp supports d in [1, 8]");
+    if (!M || !z_axes || !f) return set_error(FK_ERR_INVALID_ARG, "f, z_axes and M must be given");
+    if (Q < 0) return set_error(FK_ERR_INVALID_ARG, "Q must be >= 0");
+    if (Q > 0 && (!q || !out)) return set_error(FK_ERR_INVALID_ARG, "q and out must be given");
+    int64_t ztot = 0, gpts = 1;
+    for (int k = 0; k < d; ++k) {
+        if (M[k] < 1) return set_error(FK_ERR_INVALID_ARG, "M[%d] must be >= 1", k);
+        ztot += M[k];
+        gpts *= M[k];
+    }
+    FK_TRY(check_axes_host(z_axes, d, M));
+    Stager sg(st);
+    const void *fp = nullptr, *zp = nullptr, *qp = nullptr;
+    void* op = nullptr;
+    FK_TRY(sg.in(f, (size_t)gpts * 8, &fp));
+    FK_TRY(sg.in(z_axes, (size_t)ztot * sizeof(double), &zp));
+    FK_TRY(sg.in(q, (size_t)Q * d * dtype_size(qd), &qp));
+    FK_TRY(sg.out(out, (size_t)Q * 8, &op));
+    Arena plan;
+    int dummy = 0;
+    grid_interp_run(nullptr, d, nullptr, M, nullptr, qd, Q, nullptr, plan, st, &dummy);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    int* errw = nullptr;
+    FK_TRY(device_error_word(&errw));
+    FK_TRY(grid_interp_run((const double*)fp, d, (const double*)zp, M, qp, qd, Q, (double*)op, ar, st, errw));
+    return sg.finish();
+}
+
 // ------------------------------------------------------------------ sample-point path
 // max_d: 8 for orthant counts (inclusion-exclusion over dominance counts),
 // 4 for the weighted and kernel sums (2^(d-1) channels per sweep).
@@ -301,12 +411,6 @@ static fk_status points_validate(const void* x, fk_dtype xd, int64_t N, int d, c
     return FK_OK;
 }
 
-static fk_status check_h(const double* h, int d) {
-    if (!h) return set_error(FK_ERR_INVALID_ARG, "h is NULL");
-    for (int k = 0; k < d; ++k)
-        if (!(h[k] > 0.0) || !(h[k] < 1e300)) return set_error(FK_ERR_INVALID_ARG, "h[%d] must be finite and > 0", k);
-    return FK_OK;
-}
 
 size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
     const void* z = sample_points ? nullptr : (const void*)1;
