@@ -427,6 +427,29 @@ def _extras(fk, torch, dev, x, stream, flush, timed):
     g = torch.ones(x.shape[0], dtype=torch.float64, device=dev)
     out["kde_backward_ms"] = timed(lambda: fk.kde_laplace_backward(x, H, g, need_w=True, need_z=False,
                                                                    need_h=True, path="mixed"), reps=3)
+    out["kde_grid"] = _grid_kde_study(fk, torch, x, timed)
+    return out
+
+
+def _grid_kde_study(fk, torch, x, timed):
+    """The grid KDE (exact at the grid points) on grids over the data range,
+    interpolated to the N sample points, against the exact sample-point KDE:
+    time of the grid KDE and of the interpolation, and the interpolation
+    error (relative, on values >= 1e-6 max)."""
+    exact = fk.kde_laplace(x, H, path="fp64")
+    big = exact >= 1e-6 * exact.max()
+    lo = x.min(dim=0).values.double().cpu().numpy()
+    hi = x.max(dim=0).values.double().cpu().numpy()
+    out = {}
+    for m in (64, 128, 256):
+        axes = [np.linspace(lo[k], hi[k], m) for k in range(D)]
+        t_grid = timed(lambda: fk.kde_grid(x, H, axes, path="mixed"), reps=3)
+        f = fk.kde_grid(x, H, axes, path="mixed")
+        t_int = timed(lambda: fk.grid_interp(f, axes, x), reps=3)
+        fi = fk.grid_interp(f, axes, x)
+        rel = ((fi - exact).abs() / exact)[big]
+        out["grid%d" % m] = {"kde_grid_ms": t_grid, "interp_ms": t_int,
+                             "interp_max_rel_err": float(rel.max()), "interp_median_rel_err": float(rel.median())}
     return out
 
 
