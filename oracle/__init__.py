@@ -13,6 +13,14 @@ Every function is a brute-force restatement of a definition in the paper:
 * ``ecdf_grid``     -- the same sums evaluated on a rectilinear grid (Sec. 2.1).
 * ``kde_laplace``   -- eq. (Laplacian kde nD), Sec. 3.1, term by term.
 * ``kreg_laplace``  -- Nadaraya-Watson ratio with the Laplacian kernel (Sec. 4).
+* ``kde_uniform``   -- eq. (uniform kde nD), Sec. 3.2, box counts term by term.
+* ``kde_matern32``  -- the additive Matern-3/2 kernel, eq. (Matern32 average),
+  Appendix C, term by term.
+* ``kde_laplace_hmatrix`` -- eq. (kde nD H), Appendix B: Laplacian KDE with a
+  full bandwidth matrix H, H^{-1/2} = diag(1/h) R^T from H = R diag(h)^2 R^T.
+* ``kreg_loclin``   -- locally linear kernel regression (the weighted least
+  squares fit of an affine function around each target; Sec. 4 names it
+  beside Nadaraya-Watson), solved target by target.
 * ``kde_grad``      -- exact derivatives of eq. (Laplacian kde nD).
 * ``loo_loglik``    -- leave-one-out log-likelihood of the KDE and its h-gradient.
 * ``fenwick2d``     -- an independent sort + binary-indexed-tree 2D count.
@@ -65,9 +73,12 @@ def _load():
     lib.fko_loo_loglik.argtypes = [P, I64, I, P, P, P, P, I]
     lib.fko_kde_at.argtypes = [P, I64, I, P, P, I64, P, I, P, I]
     lib.fko_fenwick2d.argtypes = [P, I64, P, I64, P]
+    lib.fko_kde_uniform.argtypes = [P, I64, I, P, P, I64, P, I, P, I]
+    lib.fko_kde_matern32.argtypes = [P, I64, I, P, P, I64, P, I, P, I]
     lib.fko_max_threads.argtypes = []
     for f in (lib.fko_orthant_sums, lib.fko_kde, lib.fko_kreg, lib.fko_kde_grad,
-              lib.fko_loo_loglik, lib.fko_fenwick2d, lib.fko_max_threads, lib.fko_kde_at):
+              lib.fko_loo_loglik, lib.fko_fenwick2d, lib.fko_max_threads, lib.fko_kde_at,
+              lib.fko_kde_uniform, lib.fko_kde_matern32):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -206,6 +217,92 @@ def kreg_laplace(x, y, h, z=None, loo=False, threads=0):
     rc = _load().fko_kreg(_ptr(x), x.shape[0], d, _ptr(yy), _ptr(zz), m, _ptr(hh),
                           int(bool(loo)), _ptr(out), int(threads))
     _check(rc)
+    return out
+
+
+def _kernel_call(fn, x, h, w, z, loo, threads):
+    x = np.asarray(x)
+    d = x.shape[1] if x.ndim == 2 else 1
+    x = _f64(x, d)
+    hh = _f64(np.broadcast_to(np.asarray(h, dtype=np.float64), (d,)))
+    zz = None if z is None else _f64(z, d)
+    m = x.shape[0] if zz is None else zz.shape[0]
+    out = np.zeros(m, dtype=np.float64)
+    ww = None if w is None else _f64(w).reshape(-1)
+    _check(fn(_ptr(x), x.shape[0], d, _ptr(ww), _ptr(zz), m, _ptr(hh), int(bool(loo)), _ptr(out),
+              int(threads)))
+    return out
+
+
+def kde_uniform(x, h, w=None, z=None, loo=False, threads=0):
+    """Uniform-kernel KDE, eq. (uniform kde nD): the weight in the closed box
+    [z - h, z + h] (corners rounded once in FP64) over 2^d N prod h."""
+    return _kernel_call(_load().fko_kde_uniform, x, h, w, z, loo, threads)
+
+
+def kde_matern32(x, h, w=None, z=None, loo=False, threads=0):
+    """Additive Matern-3/2 KDE, eq. (Matern32 average) with u = (x - z)/h:
+    sum_i w_i (1 + D_i) e^{-D_i} / (2^d (1+d) N prod h), D_i = sum_k |x_ik - z_k|/h_k."""
+    return _kernel_call(_load().fko_kde_matern32, x, h, w, z, loo, threads)
+
+
+def hmatrix_factor(H):
+    """H = R diag(h)^2 R^T (numpy's symmetric eigendecomposition).  Returns
+    (R, h) with h > 0; raises if H is not symmetric positive definite."""
+    H = np.asarray(H, dtype=np.float64)
+    if H.ndim != 2 or H.shape[0] != H.shape[1] or not np.allclose(H, H.T, rtol=0, atol=1e-12 * np.abs(H).max()):
+        raise ValueError("H must be a symmetric matrix")
+    ev, R = np.linalg.eigh(0.5 * (H + H.T))
+    if not np.all(ev > 0):
+        raise ValueError("H must be positive definite")
+    return R, np.sqrt(ev)
+
+
+def kde_laplace_hmatrix(x, H, w=None, z=None, chunk=256):
+    """eq. (kde nD H), Appendix B, with the Laplacian kernel K(u) = 2^-d e^{-|u|_1}:
+    f(z) = 1/(|H|^{1/2} N) sum_i w_i K(H^{-1/2}(x_i - z)), H^{-1/2} = diag(1/h) R^T."""
+    x = np.asarray(x)
+    d = x.shape[1] if x.ndim == 2 else 1
+    x = _f64(x, d)
+    zz = x if z is None else _f64(z, d)
+    ww = np.ones(x.shape[0]) if w is None else _f64(w).reshape(-1)
+    R, h = hmatrix_factor(H)
+    A = (R / h[None, :]).T                 # diag(1/h) R^T
+    c = 1.0 / (2.0 ** d * np.prod(h) * x.shape[0])   # |H|^{1/2} = prod h
+    out = np.empty(zz.shape[0])
+    for s in range(0, zz.shape[0], chunk):
+        diff = x[None, :, :] - zz[s:s + chunk, None, :]          # [c, N, d]
+        u = np.einsum("kl,cnl->cnk", A, diff)
+        out[s:s + chunk] = c * (np.exp(-np.abs(u).sum(axis=2)) @ ww)
+    return out
+
+
+def kreg_loclin(x, y, h, z=None, loo=False):
+    """Locally linear regression with the Laplacian kernel: at each target z,
+    the intercept a of the fit minimising sum_i K_i (y_i - a - b.(x_i - z))^2,
+    K_i = exp(-(D_i - min D)), D_i = sum_k |x_ik - z_k| / h_k (the shift by the
+    minimum cancels in the fit).  NaN where the normal matrix is singular."""
+    x = np.asarray(x)
+    d = x.shape[1] if x.ndim == 2 else 1
+    x = _f64(x, d)
+    yy = _f64(y).reshape(-1)
+    hh = np.broadcast_to(np.asarray(h, dtype=np.float64), (d,))
+    zz = x if z is None else _f64(z, d)
+    out = np.empty(zz.shape[0])
+    for j in range(zz.shape[0]):
+        diff = x - zz[j]
+        D = (np.abs(diff) / hh).sum(axis=1)
+        keep = np.ones(x.shape[0], dtype=bool)
+        if loo and z is None:
+            keep[j] = False
+        K = np.exp(-(D[keep] - D[keep].min()))
+        X = np.concatenate([np.ones((int(keep.sum()), 1)), diff[keep]], axis=1)
+        A = X.T @ (K[:, None] * X)
+        b = X.T @ (K * yy[keep])
+        try:
+            out[j] = np.linalg.solve(A, b)[0]
+        except np.linalg.LinAlgError:
+            out[j] = np.nan
     return out
 
 

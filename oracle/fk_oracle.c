@@ -21,6 +21,9 @@
  *   - Nadaraya-Watson        : ratio of two kernel sums (Sec. 4 text on kernel
  *                              regression), with the kernel exponent shifted by
  *                              its minimum so the ratio is always defined.
+ *   - uniform / Matern-3/2   : eq. (uniform kde nD) of Sec. 3.2 and the additive
+ *                              Matern-3/2 kernel, eq. (Matern32 average) of
+ *                              Appendix C, term by term.
  *   - gradients / LOO        : exact derivatives of eq. (Laplacian kde nD).
  *   - 2D Fenwick sweep       : an independent textbook sort + binary-indexed
  *                              tree count of 2D dominance (used as a second
@@ -344,6 +347,80 @@ int fko_kde_grad(const double* x, int64_t n, int d, const double* w,
             }
             grad_w[i] = cst * neum_get(&a);
         }
+    }
+    return FKO_OK;
+}
+
+/*
+ * Uniform-kernel KDE, eq. (uniform kde nD) of Sec. 3.2:
+ *   f(z_j) = 1/(2^d N' prod h) sum_i w_i prod_k 1{lo_jk <= x_ik <= hi_jk},
+ * with the box corners lo = z - h and hi = z + h each rounded once in FP64:
+ * eq. (uniform decomposition nD) evaluates its ECDFs at exactly these corner
+ * points z + delta h.  loo != 0 (z == NULL only) drops the i == j term and
+ * uses N' = N - 1.  Weighted sums are Neumaier sums; without weights the box
+ * count is exact before the final scaling.
+ */
+int fko_kde_uniform(const double* x, int64_t n, int d, const double* w, const double* z,
+                    int64_t m, const double* h, int loo, double* out, int nthreads) {
+    if (d < 1 || d > 12 || n < 0) return FKO_EINVAL;
+    if (loo && z) return FKO_EINVAL;
+    for (int k = 0; k < d; ++k) if (!(h[k] > 0.0)) return FKO_EINVAL;
+    const double* zz = z ? z : x;
+    int64_t mm = z ? m : n;
+    int64_t nn = loo ? n - 1 : n;
+    if (nn <= 0) { for (int64_t j = 0; j < mm; ++j) out[j] = 0.0; return FKO_OK; }
+    const double cst = kde_const(nn, d, h);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < mm; ++j) {
+        const double* zj = zz + j * d;
+        double lo[12], hi[12];
+        for (int k = 0; k < d; ++k) { lo[k] = zj[k] - h[k]; hi[k] = zj[k] + h[k]; }
+        neum_t acc = {0.0, 0.0};
+        int64_t cnt = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (loo && i == j) continue;
+            const double* xi = x + i * d;
+            int in = 1;
+            for (int k = 0; k < d; ++k) in &= (lo[k] <= xi[k]) & (xi[k] <= hi[k]);
+            if (!in) continue;
+            if (w) neum_add(&acc, w[i]);
+            else ++cnt;
+        }
+        out[j] = cst * (w ? neum_get(&acc) : (double)cnt);
+    }
+    return FKO_OK;
+}
+
+/*
+ * Additive multivariate Matern-3/2 KDE, eq. (Matern32 average) of Appendix C
+ * with u = (x - z)/h:
+ *   f(z_j) = 1/(2^d (1+d) N' prod h) sum_i w_i (1 + D_ij) exp(-D_ij),
+ *   D_ij = sum_k |x_ik - z_jk| / h_k,
+ * each term evaluated directly (never through eq. Matern32 decomposition nD).
+ * For d = 1 this is eq. (Matern32) with bandwidth sqrt(3) h.
+ */
+int fko_kde_matern32(const double* x, int64_t n, int d, const double* w, const double* z,
+                     int64_t m, const double* h, int loo, double* out, int nthreads) {
+    if (d < 1 || d > 12 || n < 0) return FKO_EINVAL;
+    if (loo && z) return FKO_EINVAL;
+    for (int k = 0; k < d; ++k) if (!(h[k] > 0.0)) return FKO_EINVAL;
+    const double* zz = z ? z : x;
+    int64_t mm = z ? m : n;
+    int64_t nn = loo ? n - 1 : n;
+    if (nn <= 0) { for (int64_t j = 0; j < mm; ++j) out[j] = 0.0; return FKO_OK; }
+    const double cst = kde_const(nn, d, h) / (double)(1 + d);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < mm; ++j) {
+        const double* zj = zz + j * d;
+        neum_t acc = {0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) {
+            if (loo && i == j) continue;
+            const double a = l1h(x + i * d, zj, h, d);
+            neum_add(&acc, (w ? w[i] : 1.0) * (1.0 + a) * exp(-a));
+        }
+        out[j] = cst * neum_get(&acc);
     }
     return FKO_OK;
 }
