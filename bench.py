@@ -454,16 +454,17 @@ def _grid_kde_study(fk, torch, x, timed):
 
 
 def _traffic(kernel, alg_bytes):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the
-    current build of the kernel; else None."""
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current sources of that kernel family; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         from paper_2005_03246_gb300 import build as _b
-        if t.get("digest") != _b._digest() or kernel not in t.get("kernels", {}):
+        k = t.get("kernels", {}).get(kernel)
+        if not k or k.get("digest") != _b.kernel_digest(kernel):
             return None
-        return t["kernels"][kernel]["dram_bytes_per_launch"]
+        return k["dram_bytes_per_launch"]
     except Exception:
         return None
 

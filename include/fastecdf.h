@@ -232,6 +232,90 @@ fk_status fk_loo_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const
                          fk_stream_t stream);
 
 /*
+ * ------------------------------------------------ other kernels, full H, local linear
+ * fk_kde_uniform -- uniform-kernel KDE, eq. (uniform kde nD), Sec. 3.2:
+ *   f(z_j) = 1/(2^d N' prod h) sum_i w_i prod_k 1{z_jk - h_k <= x_ik <= z_jk + h_k},
+ * computed as eq. (uniform decomposition nD): the signed sum over delta of
+ * the ECDFs at the 2^d box corners z + delta h, the corner z_k - h_k taken
+ * strict (x_k < z_k - h_k, eq. ECDFdelta).  Each corner is rounded once in
+ * FP64 and turned into an exact threshold of the data's type, so the box test
+ * is exact: without weights the result is the exact box count times the
+ * constant.  The corners are 2^d M' explicit targets of one orthant-0 call of
+ * the sample-point engine (N + 2^d M' < 2^26; d <= 8 without weights, d <= 4
+ * with).  A weighted result is a signed difference of ECDFs: its error is
+ * relative to the weight magnitude of the enclosing corner ECDFs.
+ *   w : [N] or NULL;  z : [M][d] or NULL (the sample points);  h : HOST [d] > 0;
+ *   flags : FK_LOO (z == NULL only: drops exactly i == j, N' = N - 1);
+ *   out : [M'] double.
+ */
+size_t fk_kde_uniform_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path);
+fk_status fk_kde_uniform(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w, const void* z,
+                         int64_t M, const double* h, unsigned flags, double* out, fk_path path, void* ws,
+                         size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_kde_matern32 -- KDE with the additive multivariate Matern-3/2 kernel,
+ * eq. (Matern32 average) of Appendix C with u = (x - z)/h:
+ *   f(z_j) = 1/(2^d (1+d) N' prod h) sum_i w_i (1 + D_ij) e^{-D_ij},
+ *   D_ij = sum_k |x_ik - z_jk| / h_k
+ * (for d = 1, eq. Matern32 with bandwidth sqrt(3) h), assembled as eq.
+ * (Matern32 decomposition nD): the Laplacian orthant sums with weights w
+ * (giving sum w e^{-D}) plus, per axis, the orthant sums with weights w x_k,
+ * which give sum w e^{-D} |x_k - z_k| (2^d (d+1) CDFs).  Coordinates are
+ * centred on the first point before they become weights.  Arguments, flags,
+ * limits (1 <= d <= 4) and precision paths as fk_kde_laplace.
+ */
+size_t fk_kde_matern32_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path);
+fk_status fk_kde_matern32(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w, const void* z,
+                          int64_t M, const double* h, unsigned flags, double* out, fk_path path, void* ws,
+                          size_t ws_bytes, fk_stream_t stream);
+
+/*
+ * fk_kde_laplace_hmatrix -- Laplacian KDE with a full bandwidth matrix,
+ * eq. (kde nD H) of Appendix B:
+ *   f(z) = 1/(|H|^{1/2} N') sum_i w_i 2^{-d} e^{-|H^{-1/2}(x_i - z)|_1},
+ * with H = R diag(h)^2 R^T (symmetric eigendecomposition, cyclic Jacobi on
+ * the host) and H^{-1/2} = diag(1/h) R^T, so that both point sets are rotated
+ * by R^T (in FP64, on the device) and the diagonal-bandwidth KDE of
+ * fk_kde_laplace runs on the rotated coordinates.  The L1 norm is not
+ * rotation invariant: where H has a repeated eigenvalue the estimator
+ * depends on the eigenbasis within that eigenspace (Appendix B fixes none;
+ * this call uses the one its Jacobi iteration converges to).
+ *   H : HOST [d][d] row-major, symmetric (to 1e-12 relative) positive
+ *       definite, else FK_ERR_INVALID_ARG.  Other arguments as fk_kde_laplace
+ *       (1 <= d <= 4).
+ */
+size_t fk_kde_laplace_hmatrix_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path);
+fk_status fk_kde_laplace_hmatrix(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w, const void* z,
+                                 int64_t M, const double* H, unsigned flags, double* out, fk_path path, void* ws,
+                                 size_t ws_bytes, fk_stream_t stream);
+/*
+ * fk_hmatrix_factor -- the host-side factorisation used by
+ * fk_kde_laplace_hmatrix: H = R diag(h)^2 R^T with R [d][d] row-major
+ * (orthonormal columns = eigenvectors) and h [d] > 0.  Host pointers only;
+ * no device work.  1 <= d <= 8.
+ */
+fk_status fk_hmatrix_factor(const double* H, int d, double* R, double* h);
+
+/*
+ * fk_kreg_loclin_laplace -- locally linear kernel regression with the
+ * Laplacian kernel K_ij = e^{-D_ij} (Sec. 4 names it beside Nadaraya-Watson):
+ * m(z) = a, where (a, b) minimises sum_i K_i (y_i - a - b.(x_i - z))^2.  The
+ * normal equations need the kernel sums of the weights 1, u_k, u_k u_l, y and
+ * y u_k (u = x - x_0, the coordinates centred on the first point): 2 + 2d +
+ * d(d+1)/2 Laplacian kernel sums, each by the engine of fk_kde_laplace; a
+ * (d+1) x (d+1) solve with partial pivoting per target; NaN where a pivot
+ * vanishes.  The expanded moments cancel by up to (|z - x_0| / h)^2, so only
+ * FK_PATH_FP64 is accepted (FK_ERR_UNSUPPORTED otherwise).
+ *   y : [N] responses (required);  other arguments as fk_kreg_laplace
+ *   (FK_LOO drops i == j from every sum; 1 <= d <= 4).
+ */
+size_t fk_kreg_loclin_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path);
+fk_status fk_kreg_loclin_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const void* y, const void* z,
+                                 int64_t M, const double* h, unsigned flags, double* out, fk_path path, void* ws,
+                                 size_t ws_bytes, fk_stream_t stream);
+
+/*
  * ---------------------------------------------------------------- batching
  * fk_batched -- many independent datasets of uneven size and dimension in one
  * call (not in the paper, which treats one dataset).  Dataset b has N_b points

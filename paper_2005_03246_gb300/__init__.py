@@ -17,7 +17,8 @@ from . import _lib
 from ._lib import FastEcdfError
 
 __all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplace", "kde", "Batched",
-           "kde_grid", "grid_interp",
+           "kde_grid", "grid_interp", "kde_uniform", "kde_matern32", "kde_laplace_hmatrix", "hmatrix_factor",
+           "kreg_loclin",
            "kde_laplace_backward", "loo_laplace", "select_bandwidth_loo",
            "FastEcdfError", "mask_words"]
 
@@ -280,6 +281,78 @@ def kreg_laplace(x, y, h, z=None, loo=False, path="mixed"):
                              pc, _ptr(ws), wsb, _stream_ptr(dev))
     _lib.check(rc, "fk_kreg_laplace")
     return out
+
+
+# ----------------------------------------------------------------------------- other kernels
+
+
+def _kfam_call(name, x, h_or_H, w, z, loo, path, weighted_ws=True, ws_fn=None):
+    torch = _torch()
+    lib = _lib.load()
+    x = _prep_points(x)
+    n, d = x.shape
+    dev = x.device
+    w = _weights(w, x)
+    z, m = _prep_targets(z, x)
+    mo = m if z is not None else n
+    out = torch.empty((mo,), dtype=torch.float64, device=dev)
+    pc = _path_code(path)
+    if weighted_ws:
+        need = getattr(lib, name + "_workspace")(n, d, m, int(z is None), int(w is not None), pc)
+    else:
+        need = getattr(lib, name + "_workspace")(n, d, m, int(z is None), pc)
+    if need == 0 and n > 0 and mo > 0:
+        _lib.check(-2, name + "_workspace")
+    ws, wsb = _workspace(need, dev)
+    rc = getattr(lib, name)(_ptr(x), _dtype_code(x.dtype), n, d, _ptr(w), _ptr(z), m,
+                            h_or_H.ctypes.data_as(ctypes.c_void_p), _lib.FK_LOO if loo else 0, _ptr(out), pc,
+                            _ptr(ws), wsb, _stream_ptr(dev))
+    _lib.check(rc, name)
+    return out
+
+
+def kde_uniform(x, h, w=None, z=None, loo=False, path="mixed"):
+    """Uniform-kernel KDE (eq. uniform kde nD) by the signed corner
+    combination of 2^d ECDFs (eq. uniform decomposition nD).  Returns [M'] float64."""
+    x = _prep_points(x)
+    return _kfam_call("fk_kde_uniform", x, _h_array(h, x.shape[1]), w, z, loo, path)
+
+
+def kde_matern32(x, h, w=None, z=None, loo=False, path="mixed"):
+    """KDE with the additive Matern-3/2 kernel (eq. Matern32 average,
+    Appendix C) from 2^d (d+1) orthant sums (eq. Matern32 decomposition nD)."""
+    x = _prep_points(x)
+    return _kfam_call("fk_kde_matern32", x, _h_array(h, x.shape[1]), w, z, loo, path)
+
+
+def kde_laplace_hmatrix(x, H, w=None, z=None, loo=False, path="mixed"):
+    """Laplacian KDE with a full bandwidth matrix H (eq. kde nD H, Appendix B):
+    points rotated by R^T, H = R diag(h)^2 R^T, then the diagonal KDE."""
+    x = _prep_points(x)
+    d = x.shape[1]
+    HH = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(d, d))
+    return _kfam_call("fk_kde_laplace_hmatrix", x, HH, w, z, loo, path, weighted_ws=False)
+
+
+def hmatrix_factor(H):
+    """H = R diag(h)^2 R^T as the library factors it (host only).  Returns (R, h)."""
+    lib = _lib.load()
+    HH = np.ascontiguousarray(np.asarray(H, dtype=np.float64))
+    d = HH.shape[0]
+    R = np.zeros((d, d))
+    h = np.zeros(d)
+    rc = lib.fk_hmatrix_factor(HH.ctypes.data_as(ctypes.c_void_p), d, R.ctypes.data_as(ctypes.c_void_p),
+                               h.ctypes.data_as(ctypes.c_void_p))
+    _lib.check(rc, "fk_hmatrix_factor")
+    return R, h
+
+
+def kreg_loclin(x, y, h, z=None, loo=False, path="fp64"):
+    """Locally linear regression with the Laplacian kernel (the intercept of
+    the kernel-weighted affine least-squares fit at each target).  FP64 path
+    only.  Returns [M'] float64."""
+    x = _prep_points(x)
+    return _kfam_call("fk_kreg_loclin_laplace", x, _h_array(h, x.shape[1]), y, z, loo, path, weighted_ws=False)
 
 
 # ----------------------------------------------------------------------------- adjoints

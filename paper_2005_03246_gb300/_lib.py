@@ -63,6 +63,15 @@ SIGNATURES = {
     "fk_batched_ex": (I, [P, I, I, U, ctypes.c_double, P, P, I, P, P, SZ, P]),
     "fk_batched_autotune_workspace": (SZ, [P, I, I, U, I]),
     "fk_batched_autotune": (I, [P, I, I, U, ctypes.c_double, P, P, I, P, SZ, P, P, P]),
+    "fk_kde_uniform_workspace": (SZ, [I64, I, I64, I, I, I]),
+    "fk_kde_uniform": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
+    "fk_kde_matern32_workspace": (SZ, [I64, I, I64, I, I, I]),
+    "fk_kde_matern32": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
+    "fk_kde_laplace_hmatrix_workspace": (SZ, [I64, I, I64, I, I]),
+    "fk_kde_laplace_hmatrix": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
+    "fk_hmatrix_factor": (I, [P, I, P, P]),
+    "fk_kreg_loclin_laplace_workspace": (SZ, [I64, I, I64, I, I]),
+    "fk_kreg_loclin_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
     "fk_ecdf_grid_counts_noalloc": (I, [P, I, I64, I, P, P, P, P, P]),
     "fk_kernel_launches": (ctypes.c_uint64, []),
     "fk_profile_enable": (None, [I]),

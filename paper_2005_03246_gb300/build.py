@@ -52,6 +52,26 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# Source files that define each profiled kernel family (its kernels, their
+# device helpers and the launch code that sizes them).  A committed DRAM
+# traffic figure of a family stays valid while the digest of these files and
+# of the compile flags is unchanged.
+FAMILY_SOURCES = {
+    "merge_sweep": ["fk_dom.cu", "fk_dc.cuh", "fk_dc_drv.cuh", "fk_dc_ops.cuh", "fk_internal.cuh"],
+    "kernel_local": ["fk_dc.cuh", "fk_dc_drv.cuh", "fk_dc_ops.cuh", "fk_internal.cuh"],
+}
+
+
+def kernel_digest(family: str) -> str:
+    h = hashlib.sha256()
+    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    for name in FAMILY_SOURCES[family]:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp.txt")

@@ -1,6 +1,7 @@
 // fk_api.cu -- extern "C" entry points of fastecdf.h: argument validation,
 // host/device staging of the caller's arrays, workspace handling, dispatch.
 #include <algorithm>
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -23,6 +24,16 @@ fk_status kde_grid_run(const void* x, fk_dtype xd, int64_t N, int d, const void*
                        int* err_word);
 fk_status grid_interp_run(const double* f, int d, const double* z_dev, const int64_t* M, const void* q, fk_dtype qd,
                           int64_t nq, double* out, Arena& ar, cudaStream_t st, int* err_word);
+
+fk_status uniform_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                      const double* h, unsigned flags, double* out, fk_path path, Arena& ar, cudaStream_t st);
+fk_status matern32_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                       const double* h, unsigned flags, double* out, fk_path path, Arena& ar, cudaStream_t st);
+fk_status hmatrix_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                      const double* R, const double* hd, unsigned flags, double* out, fk_path path, Arena& ar,
+                      cudaStream_t st);
+fk_status loclin_run(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
+                     const double* h, unsigned flags, double* out, fk_path path, Arena& ar, cudaStream_t st);
 
 fk_status batched_run(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
                       double* kde_out, fk_path path, const BatchCfg& cfg, Arena& ar, cudaStream_t st);
@@ -631,6 +642,190 @@ fk_status fk_loo_laplace(const void* x, fk_dtype xd, int64_t N, int d, const voi
     FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
     FK_TRY(loo_run(xp, xd, N, d, wp, h, (double*)lp, (double*)ghp, path, ar, st));
     return sg.finish();
+}
+
+// ------------------------------------------------------------------ other kernels, full H, local linear
+// Which estimator an extra-kernel call runs (one validation and staging path for all four).
+enum KFam { KF_UNIFORM = 0, KF_MATERN = 1, KF_HMATRIX = 2, KF_LOCLIN = 3 };
+
+static fk_status kfam_run(int fam, const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
+                          int64_t M, const double* h, const double* R, unsigned flags, double* out, fk_path path,
+                          Arena& ar, cudaStream_t st) {
+    switch (fam) {
+        case KF_UNIFORM: return uniform_run(x, xd, N, d, w, z, M, h, flags, out, path, ar, st);
+        case KF_MATERN: return matern32_run(x, xd, N, d, w, z, M, h, flags, out, path, ar, st);
+        case KF_HMATRIX: return hmatrix_run(x, xd, N, d, w, z, M, R, h, flags, out, path, ar, st);
+        default: return loclin_run(x, xd, N, d, w, z, M, h, flags, out, path, ar, st);
+    }
+}
+
+// Validation shared by the four calls; m_items is the item count of the
+// sample-point engine run they make (the uniform kernel's corner targets).
+static fk_status kfam_validate(int fam, const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
+                               int64_t M, fk_path path) {
+    FK_TRY(check_common(x, xd, N, d, path));
+    if (z && M < 0) return set_error(FK_ERR_INVALID_ARG, "M must be >= 0");
+    const int max_d = (fam == KF_UNIFORM && !w) ? 8 : 4;
+    if (d > max_d) return set_error(FK_ERR_UNSUPPORTED, "this call supports d <= %d", max_d);
+    const int64_t m = z ? M : N;
+    const int64_t items = (fam == KF_UNIFORM) ? N + ((int64_t)1 << d) * m : N + (z ? M : 0);
+    if (items >= ((int64_t)1 << dc::kItemBits))
+        return set_error(FK_ERR_UNSUPPORTED, "too many items (%lld) for the sample-point path", (long long)items);
+    if (fam == KF_LOCLIN && path != FK_PATH_FP64)
+        return set_error(FK_ERR_UNSUPPORTED, "locally linear regression needs FK_PATH_FP64");
+    return FK_OK;
+}
+
+// Cyclic Jacobi eigendecomposition of a symmetric d x d matrix (d <= 8):
+// H = V diag(ev) V^T, V row-major with the eigenvectors as columns.
+static void jacobi_eigen(const double* H, int d, double* V, double* ev) {
+    double A[8][8];
+    for (int p = 0; p < d; ++p)
+        for (int q = 0; q < d; ++q) {
+            A[p][q] = 0.5 * (H[p * d + q] + H[q * d + p]);
+            V[p * d + q] = (p == q) ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < d; ++p) {
+            diag += A[p][p] * A[p][p];
+            for (int q = p + 1; q < d; ++q) off += A[p][q] * A[p][q];
+        }
+        if (off <= 1e-32 * diag) break;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                if (A[p][q] == 0.0) continue;
+                // rotation angle phi with cot(2 phi) = theta zeroes A[p][q]
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < d; ++k) {     // A <- A J
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {     // A <- J^T A
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < d; ++k) {     // V <- V J
+                    const double vkp = V[k * d + p], vkq = V[k * d + q];
+                    V[k * d + p] = c * vkp - s * vkq;
+                    V[k * d + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int p = 0; p < d; ++p) ev[p] = A[p][p];
+}
+
+fk_status fk_hmatrix_factor(const double* H, int d, double* R, double* h) {
+    if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "d out of range");
+    if (!H || !R || !h) return set_error(FK_ERR_INVALID_ARG, "NULL argument");
+    double amax = 0.0;
+    for (int e = 0; e < d * d; ++e) {
+        if (!std::isfinite(H[e])) return set_error(FK_ERR_NONFINITE, "H has a non-finite entry");
+        amax = std::max(amax, fabs(H[e]));
+    }
+    for (int p = 0; p < d; ++p)
+        for (int q = p + 1; q < d; ++q)
+            if (fabs(H[p * d + q] - H[q * d + p]) > 1e-12 * amax)
+                return set_error(FK_ERR_INVALID_ARG, "H is not symmetric");
+    double ev[8];
+    jacobi_eigen(H, d, R, ev);
+    for (int p = 0; p < d; ++p) {
+        if (!(ev[p] > 0.0)) return set_error(FK_ERR_INVALID_ARG, "H is not positive definite");
+        h[p] = sqrt(ev[p]);
+    }
+    return FK_OK;
+}
+
+static size_t kfam_workspace(int fam, int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
+    const void* z = sample_points ? nullptr : (const void*)1;
+    const void* w = weighted ? (const void*)1 : nullptr;
+    if (kfam_validate(fam, (const void*)1, FK_F32, N, d, w, z, M, path) != FK_OK) return 0;
+    double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    double R[64] = {0};
+    size_t best = 0;
+    for (int t = 0; t < 2; ++t) {
+        Arena ar;
+        kfam_run(fam, (const void*)1, t ? FK_F64 : FK_F32, N, d, w, z, M, h, R, 0, nullptr, path, ar, 0);
+        if (ar.used > best) best = ar.used;
+    }
+    return best;
+}
+
+static fk_status kfam_impl(int fam, const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
+                           int64_t M, const double* h, const double* H, unsigned flags, double* out, fk_path path,
+                           void* ws, size_t ws_bytes, fk_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    FK_TRY(kfam_validate(fam, x, xd, N, d, w, z, M, path));
+    double R[64], hd[8];
+    if (fam == KF_HMATRIX) {
+        if (!H) return set_error(FK_ERR_INVALID_ARG, "H is NULL");
+        FK_TRY(fk_hmatrix_factor(H, d, R, hd));
+        h = hd;
+    } else {
+        FK_TRY(check_h(h, d));
+    }
+    if ((flags & FK_LOO) && z) return set_error(FK_ERR_INVALID_ARG, "FK_LOO needs z == NULL");
+    if ((flags & FK_LOO) && N < 2) return set_error(FK_ERR_INVALID_ARG, "leave-one-out needs N >= 2");
+    if (fam == KF_LOCLIN && !w && N > 0) return set_error(FK_ERR_INVALID_ARG, "y is NULL");
+    const int64_t m_out = z ? M : N;
+    if (m_out == 0) return FK_OK;                        // nothing to write
+    if (!out) return set_error(FK_ERR_INVALID_ARG, "out is NULL");
+    const size_t ds = dtype_size(xd);
+    Stager sg(st);
+    const void *xp = nullptr, *wp = nullptr, *zp = nullptr;
+    void* op = nullptr;
+    FK_TRY(sg.in(x, (size_t)N * d * ds, &xp));
+    FK_TRY(sg.in(w, (size_t)N * ds, &wp));
+    FK_TRY(sg.in(z, z ? (size_t)M * d * ds : 0, &zp));
+    FK_TRY(sg.out(out, (size_t)m_out * 8, &op));
+    if (N == 0) {
+        FK_CUDA(cudaMemsetAsync(op, 0, (size_t)m_out * 8, st));
+        return sg.finish();
+    }
+    Arena plan;
+    kfam_run(fam, (const void*)1, xd, N, d, w, z, M, h, R, flags, nullptr, path, plan, st);
+    Workspace wsp(st);
+    Arena ar;
+    FK_TRY(wsp.bind(ar, ws, ws_bytes, plan.used));
+    FK_TRY(kfam_run(fam, xp, xd, N, d, wp, zp, M, h, R, flags, (double*)op, path, ar, st));
+    return sg.finish();
+}
+
+size_t fk_kde_uniform_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
+    return kfam_workspace(KF_UNIFORM, N, d, M, sample_points, weighted, path);
+}
+fk_status fk_kde_uniform(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                         const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
+                         fk_stream_t stream) {
+    return kfam_impl(KF_UNIFORM, x, xd, N, d, w, z, M, h, nullptr, flags, out, path, ws, ws_bytes, stream);
+}
+size_t fk_kde_matern32_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
+    return kfam_workspace(KF_MATERN, N, d, M, sample_points, weighted, path);
+}
+fk_status fk_kde_matern32(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
+                          const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
+                          fk_stream_t stream) {
+    return kfam_impl(KF_MATERN, x, xd, N, d, w, z, M, h, nullptr, flags, out, path, ws, ws_bytes, stream);
+}
+size_t fk_kde_laplace_hmatrix_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
+    return kfam_workspace(KF_HMATRIX, N, d, M, sample_points, 1, path);
+}
+fk_status fk_kde_laplace_hmatrix(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
+                                 int64_t M, const double* H, unsigned flags, double* out, fk_path path, void* ws,
+                                 size_t ws_bytes, fk_stream_t stream) {
+    return kfam_impl(KF_HMATRIX, x, xd, N, d, w, z, M, nullptr, H, flags, out, path, ws, ws_bytes, stream);
+}
+size_t fk_kreg_loclin_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
+    return kfam_workspace(KF_LOCLIN, N, d, M, sample_points, 1, path);
+}
+fk_status fk_kreg_loclin_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,
+                                 int64_t M, const double* h, unsigned flags, double* out, fk_path path, void* ws,
+                                 size_t ws_bytes, fk_stream_t stream) {
+    return kfam_impl(KF_LOCLIN, x, xd, N, d, y, z, M, h, nullptr, flags, out, path, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------------------ batching

@@ -99,3 +99,45 @@ def test_sample_point_dimension_limits():
         assert lib.fk_ecdf_points_workspace(1000, d, 0, 1, 1, 0) == 0
     assert lib.fk_ecdf_points_workspace(1000, 9, 0, 1, 0, 0) == 0
     assert lib.fk_kde_laplace_workspace(1000, 5, 0, 1, 0, 0) == 0
+
+
+def test_extra_kernel_workspaces_and_limits():
+    """Workspace queries of the uniform / Matern-3/2 / matrix-bandwidth / local
+    linear calls: sizes are positive where the call is supported, 0 where not
+    (local linear only on the FP64 path; uniform counts to d = 8)."""
+    from paper_2005_03246_gb300 import _lib
+    lib = _lib.load()
+    for d in (1, 2, 3, 4):
+        for path in (0, 1):
+            assert lib.fk_kde_uniform_workspace(5000, d, 0, 1, 1, path) > 0
+            assert lib.fk_kde_matern32_workspace(5000, d, 300, 0, 0, path) > 0
+            assert lib.fk_kde_laplace_hmatrix_workspace(5000, d, 0, 1, path) > 0
+        assert lib.fk_kreg_loclin_laplace_workspace(5000, d, 0, 1, 1) > 0
+        assert lib.fk_kreg_loclin_laplace_workspace(5000, d, 0, 1, 0) == 0
+    assert lib.fk_kde_uniform_workspace(5000, 8, 0, 1, 0, 0) > 0       # counts: d <= 8
+    assert lib.fk_kde_uniform_workspace(5000, 5, 0, 1, 1, 0) == 0      # weighted: d <= 4
+    assert lib.fk_kde_matern32_workspace(5000, 5, 0, 1, 0, 0) == 0
+    # the uniform kernel's 2^d corner targets count against the item limit
+    assert lib.fk_kde_uniform_workspace(300_000, 8, 0, 1, 0, 0) == 0
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_hmatrix_factor_host(d):
+    """The host factorisation H = R diag(h)^2 R^T: reconstructs H, R orthonormal,
+    eigenvalues equal numpy's; non-symmetric / indefinite H are rejected."""
+    import numpy as np
+    from paper_2005_03246_gb300 import hmatrix_factor, FastEcdfError
+    r = np.random.default_rng(70 + d)
+    A = r.standard_normal((d, d))
+    H = A @ A.T + 0.1 * np.eye(d)
+    R, h = hmatrix_factor(H)
+    np.testing.assert_allclose(R @ np.diag(h ** 2) @ R.T, H, rtol=0, atol=1e-13 * np.abs(H).max())
+    np.testing.assert_allclose(R.T @ R, np.eye(d), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(np.sort(h ** 2), np.linalg.eigvalsh(H), rtol=1e-13)
+    if d >= 2:
+        bad = H.copy()
+        bad[0, 1] += 1.0
+        with pytest.raises(FastEcdfError):
+            hmatrix_factor(bad)
+        with pytest.raises(FastEcdfError):
+            hmatrix_factor(-H)
