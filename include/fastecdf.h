@@ -411,8 +411,9 @@ fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xdtype
  * buffers of up to 2^(d-1) (M_1+1)...(M_d+1) 4-byte entries) would exceed it
  * returns FK_ERR_UNSUPPORTED.  x, z_axes and out must be device pointers
  * (host arrays would need staging buffers); M and orthant_mask are host
- * arrays as for fk_ecdf_grid.  The first call on a device looks up the
- * scratch's device address on that device (make it the current device).
+ * arrays as for fk_ecdf_grid.  The first call on a device does a one-time
+ * set-up: it looks up the scratch's device address on that device (make it
+ * the current device), so make that first call before any stream capture.
  * Every call uses the same scratch and zeroes the part it accumulates into;
  * calls whose work overlaps on the GPU (concurrent streams, or several host
  * threads on one device) race on it and must be serialised by the caller.

@@ -29,7 +29,8 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the static scratch on the current device.  The symbol's
 // name in host code is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached: the first call on a
+// device does this set-up and should come before any stream capture.
 fk_status noalloc_scratch(void** out) {
     int dev = 0;
     FK_CUDA(cudaGetDevice(&dev));
