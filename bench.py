@@ -428,7 +428,33 @@ def _extras(fk, torch, dev, x, stream, flush, timed):
     out["kde_backward_ms"] = timed(lambda: fk.kde_laplace_backward(x, H, g, need_w=True, need_z=False,
                                                                    need_h=True, path="mixed"), reps=3)
     out["kde_grid"] = _grid_kde_study(fk, torch, x, timed)
+    out["other_estimators"] = _other_estimators(fk, torch, x, timed)
     return out
+
+
+def _other_estimators(fk, torch, x, timed):
+    """The other estimators on the same d=3, N=1e6 points at the sample points
+    (ms, median of the timed runs, L2 flushed): uniform kernel (exact box
+    counts; weighted FP64), additive Matern-3/2, full bandwidth matrix,
+    Nadaraya-Watson and locally linear regression."""
+    y = torch.sin(x.double().sum(dim=1)).to(x.dtype)
+    H = np.array([[0.010, 0.004, 0.0], [0.004, 0.012, 0.002], [0.0, 0.002, 0.015]])
+
+    def timed_warm(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        return timed(fn, reps=reps)
+
+    return {
+        "hmatrix": H.tolist(),
+        "kde_uniform_counts_ms": timed_warm(lambda: fk.kde_uniform(x, 0.1), reps=3),
+        "kde_uniform_weighted_fp64_ms": timed_warm(lambda: fk.kde_uniform(x, 0.1, w=y, path="fp64"), reps=2),
+        "kde_matern32_mixed_ms": timed_warm(lambda: fk.kde_matern32(x, 0.1, path="mixed"), reps=3),
+        "kde_matern32_fp64_ms": timed_warm(lambda: fk.kde_matern32(x, 0.1, path="fp64"), reps=2),
+        "kde_laplace_hmatrix_mixed_ms": timed_warm(lambda: fk.kde_laplace_hmatrix(x, H, path="mixed"), reps=3),
+        "kreg_nw_mixed_ms": timed_warm(lambda: fk.kreg_laplace(x, y, 0.1, path="mixed"), reps=3),
+        "kreg_loclin_fp64_ms": timed_warm(lambda: fk.kreg_loclin(x, y, 0.1), reps=1),
+    }
 
 
 def _grid_kde_study(fk, torch, x, timed):

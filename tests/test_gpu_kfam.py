@@ -267,3 +267,46 @@ def test_loclin_refuses_mixed_path():
     x = np.random.default_rng(1).standard_normal((100, 2))
     with pytest.raises(fk.FastEcdfError):
         fk.kreg_loclin(_t(x), _t(x[:, 0]), 0.3, path="mixed")
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+def test_edge_cases_single_point_empty_targets_and_two_point_loo():
+    """N = 1 (one source: the kernel itself), M = 0 explicit targets (an empty
+    result), N = 2 with leave-one-out (each point sees only the other)."""
+    import torch
+    fk = _fk()
+    x1 = np.array([[0.25, -0.5]])
+    z = np.array([[0.25, -0.5], [0.3, -0.45], [1.0, 1.0], [0.5, -0.25]])
+    h = np.array([0.25, 0.25])
+    np.testing.assert_allclose(fk.kde_uniform(_t(x1), h, z=_t(z)).cpu().numpy(),
+                               oracle.kde_uniform(x1, h, z=z), rtol=1e-15, atol=0)
+    for path in ("mixed", "fp64"):
+        np.testing.assert_allclose(fk.kde_matern32(_t(x1), h, z=_t(z), path=path).cpu().numpy(),
+                                   oracle.kde_matern32(x1, h, z=z), rtol=TOL[path], atol=1e-300)
+    H = np.array([[0.05, 0.01], [0.01, 0.04]])
+    np.testing.assert_allclose(fk.kde_laplace_hmatrix(_t(x1), H, z=_t(z), path="fp64").cpu().numpy(),
+                               oracle.kde_laplace_hmatrix(x1, H, z=z), rtol=1e-12, atol=1e-300)
+    empty = torch.empty((0, 2), dtype=torch.float64, device="cuda:0")
+    assert fk.kde_uniform(_t(x1), h, z=empty).shape == (0,)
+    assert fk.kde_matern32(_t(x1), h, z=empty).shape == (0,)
+    x2 = np.array([[0.0, 0.0], [0.1, 0.2]])
+    np.testing.assert_allclose(fk.kde_uniform(_t(x2), h, loo=True).cpu().numpy(),
+                               oracle.kde_uniform(x2, h, loo=True), rtol=1e-15, atol=0)
+    for path in ("mixed", "fp64"):
+        np.testing.assert_allclose(fk.kde_matern32(_t(x2), h, loo=True, path=path).cpu().numpy(),
+                                   oracle.kde_matern32(x2, h, loo=True), rtol=TOL[path])
+
+
+def test_invalid_arguments_are_refused():
+    fk = _fk()
+    x = np.random.default_rng(2).standard_normal((50, 2))
+    with pytest.raises(fk.FastEcdfError):
+        fk.kde_uniform(_t(x), [0.1, -0.1])                       # h <= 0
+    with pytest.raises(fk.FastEcdfError):
+        fk.kde_laplace_hmatrix(_t(x), np.array([[1.0, 2.0], [2.0, 1.0]]))   # indefinite
+    with pytest.raises(fk.FastEcdfError):
+        fk.kde_laplace_hmatrix(_t(x), np.array([[1.0, 0.2], [0.1, 1.0]]))   # not symmetric
+    with pytest.raises(fk.FastEcdfError):
+        fk.kde_matern32(_t(np.random.default_rng(3).standard_normal((50, 5))), 0.1)   # d > 4
