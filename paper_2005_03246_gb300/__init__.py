@@ -461,15 +461,34 @@ def kde(x, h, w=None, z=None, loo=False, path="mixed"):
     return _KDE_FN.apply(x, w, z, hfull, loo, path)
 
 
-def select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, w=None, path="mixed", per_axis=False):
+def select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, w=None, path="mixed", per_axis=False, checkpoint=None):
     """Leave-one-out likelihood bandwidth selection: gradient ascent on u = log h,
     u <- u + lr * dL/du (dL/du = h * dL/dh), from h0, for `steps` steps.
-    Returns a list of (h, L, dL/dh) per step (h before the step)."""
+    Returns a list of (h, L, dL/dh) per step (h before the step).
+
+    checkpoint: optional path of a JSON file holding the optimiser state (steps
+    done, log h and the history so far), rewritten atomically after every step.
+    If it exists when the call starts, the search resumes from it (it must come
+    from a search with the same d, lr, per_axis and path, else ValueError);
+    floats round-trip exactly through the file."""
+    import json
+    import os
     x = _prep_points(x)
     d = x.shape[1]
     u = np.log(np.broadcast_to(np.asarray(h0, dtype=np.float64), (d,)).copy())
     hist = []
-    for _ in range(steps):
+    start = 0
+    meta = {"d": int(d), "lr": float(lr), "per_axis": bool(per_axis), "path": str(path)}
+    if checkpoint is not None and os.path.exists(checkpoint):
+        with open(checkpoint) as f:
+            st = json.load(f)
+        if {k: st.get(k) for k in meta} != meta:
+            raise ValueError("checkpoint %s belongs to another search (%s)" % (checkpoint, {k: st.get(k) for k in meta}))
+        u = np.asarray(st["log_h"], dtype=np.float64)
+        hist = [(np.asarray(e["h"], dtype=np.float64), float(e["L"]), np.asarray(e["grad_h"], dtype=np.float64))
+                for e in st["history"]]
+        start = int(st["step"])
+    for step in range(start, steps):
         h = np.exp(u)
         L, gh = loo_laplace(x, h, w=w, path=path)
         g = gh.cpu().numpy()
@@ -478,6 +497,14 @@ def select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, w=None, path="mixed", per_
             u = u + lr * h * g
         else:
             u = u + lr * float(np.sum(h * g))
+        if checkpoint is not None:
+            st = dict(meta, step=step + 1, log_h=[float(v) for v in u],
+                      history=[{"h": [float(v) for v in a], "L": b, "grad_h": [float(v) for v in c]}
+                               for a, b, c in hist])
+            tmp = "%s.tmp%d" % (checkpoint, os.getpid())
+            with open(tmp, "w") as f:
+                json.dump(st, f)
+            os.replace(tmp, checkpoint)
     return hist
 
 
