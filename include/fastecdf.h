@@ -16,6 +16,8 @@
  *   o = 0 is the ECDF (eq. ECDF), o = 2^d - 1 the ESF (eq. ESF); the 2^d
  *   orthants partition the sources.  A source equal to its target is counted
  *   once, in orthant 0.
+ * Targets.  z == NULL always means the sample points; an empty explicit
+ *   target set (M = 0) is passed with any non-NULL z and writes nothing.
  * Orthant selection.  `orthant_mask` is a HOST bitset of ceil(2^d/32) uint32
  *   words (bit o of word o/32 selects orthant o); NULL selects all orthants.
  *   Outputs hold the selected orthants in increasing index, one row each.
@@ -26,9 +28,13 @@
  *   combination in FP64; FK_PATH_FP64 does everything in FP64.  Counts are
  *   exact on both paths.
  * Memory.  Every array argument may be a device pointer (the normal case) or
- *   a host pointer; host arrays are staged through device buffers by the
- *   library and the call then returns only after the host outputs are written.
- *   With device pointers the call is asynchronous on `stream`.  The caller owns
+ *   a host pointer; host arrays are staged through device buffers that the
+ *   library allocates and frees in stream order.  With device pointers the
+ *   call is asynchronous on `stream`.  If every host array of the call is
+ *   page-locked (cudaHostAlloc / cudaHostRegister) the call is asynchronous
+ *   too: host outputs are written when `stream` reaches the copies, and host
+ *   inputs must not change before then.  With any pageable host array the
+ *   call returns only after the host outputs are written.  The caller owns
  *   every buffer; the library never frees caller memory and keeps no state
  *   between calls other than the per-device error word (fk_device_status).
  * Workspace.  `ws`/`ws_bytes` is caller-owned device scratch of at least the

@@ -201,6 +201,8 @@ def ecdf_points(x, y=None, z=None, orthants=None, path="mixed"):
     nsel = int(sum(bin(int(v)).count("1") for v in mw))
     mo = m if z is not None else n
     out = torch.empty((nsel, mo), dtype=torch.int64 if y is None else torch.float64, device=dev)
+    if z is not None and m == 0:      # no targets: nothing to compute (an empty z has no address)
+        return out
     pc = _path_code(path)
     need = lib.fk_ecdf_points_workspace(n, d, m, int(z is None), int(y is not None), pc)
     ws, wsb = _workspace(need, dev)
@@ -222,6 +224,8 @@ def esf_points(x, y=None, z=None, path="mixed"):
     z, m = _prep_targets(z, x)
     mo = m if z is not None else n
     out = torch.empty((mo,), dtype=torch.int64 if y is None else torch.float64, device=dev)
+    if z is not None and m == 0:      # no targets: nothing to compute (an empty z has no address)
+        return out
     pc = _path_code(path)
     need = lib.fk_ecdf_points_workspace(n, d, m, int(z is None), int(y is not None), pc)
     ws, wsb = _workspace(need, dev)
@@ -251,6 +255,8 @@ def kde_laplace(x, h, w=None, z=None, loo=False, terms=False, path="mixed"):
     mo = m if z is not None else n
     out = torch.empty((mo,), dtype=torch.float64, device=dev)
     tt = torch.empty((1 << d, mo), dtype=torch.float64, device=dev) if terms else None
+    if z is not None and m == 0:      # no targets: nothing to compute (an empty z has no address)
+        return (out, tt) if terms else out
     pc = _path_code(path)
     need = lib.fk_kde_laplace_workspace(n, d, m, int(z is None), int(bool(terms)), pc)
     ws, wsb = _workspace(need, dev)
@@ -273,6 +279,8 @@ def kreg_laplace(x, y, h, z=None, loo=False, path="mixed"):
     hh = _h_array(h, d)
     mo = m if z is not None else n
     out = torch.empty((mo,), dtype=torch.float64, device=dev)
+    if z is not None and m == 0:      # no targets: nothing to compute (an empty z has no address)
+        return out
     pc = _path_code(path)
     need = lib.fk_kreg_laplace_workspace(n, d, m, int(z is None), pc)
     ws, wsb = _workspace(need, dev)
@@ -296,6 +304,8 @@ def _kfam_call(name, x, h_or_H, w, z, loo, path, weighted_ws=True, ws_fn=None):
     z, m = _prep_targets(z, x)
     mo = m if z is not None else n
     out = torch.empty((mo,), dtype=torch.float64, device=dev)
+    if z is not None and m == 0:      # no targets: nothing to compute (an empty z has no address)
+        return out
     pc = _path_code(path)
     if weighted_ws:
         need = getattr(lib, name + "_workspace")(n, d, m, int(z is None), int(w is not None), pc)
@@ -378,6 +388,8 @@ def kde_laplace_backward(x, h, grad_out, w=None, z=None, loo=False, need_w=True,
     gw = torch.empty((n,), dtype=torch.float64, device=dev) if need_w else None
     gz = torch.empty((mo, d), dtype=torch.float64, device=dev) if (need_z and z is not None) else None
     gh = torch.empty((d,), dtype=torch.float64, device=dev) if need_h else None
+    if z is not None and m == 0:      # no targets: nothing to compute (an empty z has no address)
+        return (None if gw is None else gw.zero_()), gz, (None if gh is None else gh.zero_())
     pc = _path_code(path)
     need = lib.fk_kde_laplace_backward_workspace(n, d, m, int(z is None), pc)
     ws, wsb = _workspace(need, dev)

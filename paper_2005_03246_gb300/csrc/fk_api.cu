@@ -63,6 +63,19 @@ bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory (cudaHostAlloc / cudaHostRegister): copies to and
+// from it are asynchronous on the stream.
+static bool is_pinned_host_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -97,13 +110,16 @@ fk_status device_error_word(int** ptr) {
     return FK_OK;
 }
 
-// Stages caller arrays that live in host memory through device buffers.
+// Stages caller arrays that live in host memory through device buffers.  The
+// staging buffers are allocated and freed in stream order.  If every host
+// array of the call is page-locked the copies stay asynchronous and so does
+// the call; a pageable host array makes the call wait for its host outputs.
 struct Stager {
     cudaStream_t st;
     std::vector<void*> allocs;
     struct Out { void* dev; void* host; size_t bytes; };
     std::vector<Out> outs;
-    bool any_host = false;
+    bool any_pageable = false;
     explicit Stager(cudaStream_t s) : st(s) {}
     ~Stager() {
         for (void* p : allocs) cudaFreeAsync(p, st);
@@ -112,7 +128,7 @@ struct Stager {
     fk_status in(const void* p, size_t bytes, const void** dev) {
         *dev = p;
         if (!p || bytes == 0 || is_device_pointer(p)) return FK_OK;
-        any_host = true;
+        if (!is_pinned_host_pointer(p)) any_pageable = true;
         void* d = nullptr;
         FK_CUDA(cudaMallocAsync(&d, bytes, st));
         allocs.push_back(d);
@@ -124,7 +140,7 @@ struct Stager {
     fk_status out(void* p, size_t bytes, void** dev) {
         *dev = p;
         if (!p || bytes == 0 || is_device_pointer(p)) return FK_OK;
-        any_host = true;
+        if (!is_pinned_host_pointer(p)) any_pageable = true;
         void* d = nullptr;
         FK_CUDA(cudaMallocAsync(&d, bytes, st));
         allocs.push_back(d);
@@ -135,7 +151,7 @@ struct Stager {
     fk_status finish() {
         for (auto& o : outs)
             FK_CUDA(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
-        if (any_host) FK_CUDA(cudaStreamSynchronize(st));
+        if (any_pageable) FK_CUDA(cudaStreamSynchronize(st));
         return FK_OK;
     }
 };
