@@ -150,6 +150,14 @@ fk_status fk_grid_interp(const double* f, int d, const double* z_axes, const int
  * in Appendix D, Algorithms 8-12).
  *   out : [n_sel][M'] with M' = N (sample points) or M; int64 when y == NULL,
  *         else double.
+ * Counts at the sample points (y == NULL, z == NULL, N >= 2) hold each point
+ * as one item that is both a source and a target: equal coordinates are
+ * ordered by point index, and the pairs this order misses (tied on an axis,
+ * later index as the source) are added from the tie groups of the sorted
+ * axes.  The call reads the tie statistics back once (it synchronises
+ * `stream` after the rank transform); if some axis has a tie group longer
+ * than 64 points it uses a source copy and a target copy of every point
+ * instead.  Either way the counts are exact.
  */
 size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points,
                                 int weighted, fk_path path);

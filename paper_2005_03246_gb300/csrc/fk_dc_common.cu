@@ -281,12 +281,29 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
     const uint32_t pbmask = (1u << (d_eff - 1)) - 1u;
     const int kind = (y == nullptr) ? 0 : (path == FK_PATH_FP64 ? 1 : 2);
     const size_t asz = kind == 0 ? 4 : 8;
+    size_t single_high = 0;
+    if (kind == 0 && sample && N >= 2) {
+        // counts at the sample points: one item per point, ties corrected;
+        // the source/target-copy layout below only when tie groups are long
+        // (sizing plans both and keeps the larger)
+        const size_t mark = ar.used;
+        Positions p1;
+        FK_TRY(plan_positions(x, nullptr, xd, N, N, d, d_eff, p1, ar, st));
+        if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
+        bool fallback = ar.sizing;
+        FK_TRY(dom_self_counts(d, N, p1.P, x, xd, mask, (int64_t*)out, ar, st, &fallback));
+        if (!fallback) return FK_OK;
+        single_high = ar.used;
+        ar.used = mark;
+    }
     Positions pos;
     FK_TRY(plan_positions(x, z, xd, N, n, d, d_eff, pos, ar, st));
     if (kind == 0) {
         // counts: exact inclusion-exclusion over single-orthant dominance counts
         if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
-        return dom_orthant_counts(d, n, N, N, n_tgt, pos.P, mask, (int64_t*)out, ar, st);
+        FK_TRY(dom_orthant_counts(d, n, N, N, n_tgt, pos.P, mask, (int64_t*)out, ar, st));
+        if (ar.used < single_high) ar.used = single_high;
+        return FK_OK;
     }
     void* acc = ar.take<char>((size_t)(1 << d_eff) * n_tgt * asz);
     void* wts = (kind == 0) ? nullptr : ar.take<char>((size_t)N * 8);

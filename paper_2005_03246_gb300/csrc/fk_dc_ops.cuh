@@ -40,6 +40,13 @@ FK_DC_SWEEP_DECL(sweep_kd2, PolKD<2>)
 fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, int64_t n_tgt,
                              const uint32_t* const* P, const uint32_t* mask, int64_t* out, Arena& ar,
                              cudaStream_t st);
+// The same at the sample points with one item per point (each a source and a
+// target).  Synchronises `st` once, after the tie statistics: if a tie group
+// on some axis is too long for the tie correction, sets *fallback and
+// computes nothing (the caller then uses the source/target-copy layout).  In
+// sizing mode *fallback is left as passed.
+fk_status dom_self_counts(int d, int64_t n, const uint32_t* const* P, const void* x, fk_dtype xd,
+                          const uint32_t* mask, int64_t* out, Arena& ar, cudaStream_t st, bool* fallback);
 // Batched form: items in segments of 2^segE slots described by seg (see
 // dc::ItemMap); the counts of target t go to out_base[b] + r * n_b + (t - t0_b)
 // for dataset b (targets numbered by dataset), every orthant r < 2^d.

@@ -272,3 +272,33 @@ def test_orthant_counts_high_dimension(d, n):
     assert np.array_equal(got_z, oracle.orthant_sums(x, z=z, mask=sel))
     esf = _fk().esf_points(_t(x)).cpu().numpy()
     assert np.array_equal(esf.reshape(-1), oracle.orthant_sums(x, mask=[(1 << d) - 1])[0])
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 6])
+def test_counts_single_item_tie_correction(d, dtype):
+    """Counts at the sample points with one item per point: ties in short
+    groups (half the coordinates on a 1/256 lattice, and 5% of the points
+    exact duplicates of others, tied on every axis) are corrected exactly."""
+    r = np.random.default_rng(900 + d)
+    n = 4000 if d <= 4 else 1500
+    x = r.standard_normal((n, d))
+    m = r.random((n, d)) < 0.5
+    x[m] = np.round(x[m] * 256) / 256
+    dup = r.choice(n, size=n // 20, replace=False)
+    x[dup] = x[r.integers(0, n, size=dup.size)]
+    x = x.astype(dtype)
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(got, oracle.orthant_sums(x))
+    esf = _fk().esf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(esf.reshape(-1), oracle.orthant_sums(x, mask=[(1 << d) - 1])[0])
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_counts_long_tie_groups_fall_back(d):
+    """Integer points in {0..3}^d: tie groups of hundreds of points on every
+    axis (the copy layout is used); counts still exact."""
+    r = np.random.default_rng(950 + d)
+    x = r.integers(0, 4, size=(3000, d)).astype(np.float32)
+    got = _fk().ecdf_points(_t(x)).cpu().numpy()
+    assert np.array_equal(got, oracle.orthant_sums(x))
