@@ -12,7 +12,9 @@ One step is one pass of the whole hot path over the d=3, N=1e6 workload
                    precision (Sec. 3.1).
 
 value = N sample points / step time (each point gets its 8 orthant counts and
-its density; the 256^3 grid is evaluated alongside).  Inputs are resident in
+its density; the 256^3 grid is evaluated alongside).  The three calls are
+independent and run on three streams (--serial: one after another; the
+per-call times are reported beside the step either way).  Inputs are resident in
 HBM; L2 (129 MB) is flushed by writing a 256 MB buffer between timed steps.
 `e2e` times the same step through the C ABI with pinned HOST buffers (copies
 in and out inside the timed region).  `--impl reference` times the CPU oracle
@@ -59,6 +61,8 @@ def _args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serial", action="store_true",
+                    help="run the step's three calls one after another on one stream")
     ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
                     help="run one operation per step (profiling of a single kernel family)")
     return ap.parse_args(argv)
@@ -258,12 +262,34 @@ def run_ours(args):
             "kde64": lambda: fk.kde_laplace(x, H, path="fp64"),
             "kreg": lambda: fk.kreg_laplace(x, ywt, H, path="mixed")}
 
+    # The three calls of a step are independent: unless --serial, the KDE and
+    # the grid counts run on their own streams (forked from and joined back to
+    # the timing stream by events) while the sample-point counts run on the
+    # timing stream; they are issued last because they read their tie
+    # statistics back once.
+    side = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+
     def step():
         if args.only:
             return only[args.only]()
-        g = fk.ecdf_grid(x, grid)
+        if args.serial:
+            g = fk.ecdf_grid(x, grid)
+            p = fk.ecdf_points(x)
+            f = fk.kde_laplace(x, H, path="mixed")
+            return g, p, f
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for s in side:
+            s.wait_event(fork)
+        with torch.cuda.stream(side[0]):
+            f = fk.kde_laplace(x, H, path="mixed")
+        with torch.cuda.stream(side[1]):
+            g = fk.ecdf_grid(x, grid)
         p = fk.ecdf_points(x)
-        f = fk.kde_laplace(x, H, path="mixed")
+        for s in side:
+            join = torch.cuda.Event()
+            join.record(s)
+            stream.wait_event(join)
         return g, p, f
 
     for _ in range(max(3, args.warmup)):
@@ -393,6 +419,8 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "u32/i64 counts; f32+f64 (mixed KDE)", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": n, "d": D, "grid": [M_AXIS] * D, "orthants": 8,
                            "h": H, "kde_path": "mixed", "l2": "flushed (256 MB write) between steps",
+                           "calls": "one after another" if args.serial else
+                                    "independent calls on three streams (KDE, grid counts, sample-point counts)",
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roofline, "kernel_families": breakdown,
                 "split": split, "fp64_path": fp64, "extras": extras, "e2e": e2e, "cpu_baseline": cpu,
