@@ -364,6 +364,13 @@ def run_ours(args):
                          "avg_launch_us": tms / cnt * 1e3, "busy_ms_per_step": busy / args.steps,
                          "share_of_step": busy / total_ms})
 
+    # compulsory I/O of a step (read x once per call, write every output once)
+    # over the step time: the floor any implementation of the step must move
+    gpts = M_AXIS ** D
+    b_io = 3 * x_np.nbytes + 8 * gpts * 8 + 8 * n * 8 + n * 8
+    io_floor = {"bytes_per_step": int(b_io), "gbs": b_io / (ms_step / 1e3) / 1e9,
+                "frac_of_peak": b_io / (ms_step / 1e3) / 1e9 / peak}
+
     def _rate(name, v):   # work per busy second
         if v[3] <= 0:
             return None
@@ -422,7 +429,8 @@ def run_ours(args):
                            "calls": "one after another" if args.serial else
                                     "independent calls on three streams (KDE, grid counts, sample-point counts)",
                            "parallelism": "replicas" if ws > 1 else "single"},
-                "gpu_launches": int(launches), "roofline": roofline, "kernel_families": breakdown,
+                "gpu_launches": int(launches), "roofline": roofline, "io_floor": io_floor,
+                "kernel_families": breakdown,
                 "split": split, "fp64_path": fp64, "extras": extras, "e2e": e2e, "cpu_baseline": cpu,
                 "clocks": clk}
         print(json.dumps(line), flush=True)

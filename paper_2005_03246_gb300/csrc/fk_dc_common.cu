@@ -271,21 +271,62 @@ static SelMap make_selmap(int d, const uint32_t* mask) {
 }
 
 // ------------------------------------------------------------------ orthant sums
+// Weighted orthant sums of the sweep engine for one item layout (im, n items,
+// positions pos), finalised into out [sel rows][n_tgt] double.
+static fk_status orthant_sums_run(const void* y, fk_dtype xd, int64_t N, int d, int d_eff, const ItemMap& im,
+                                  int64_t n, int64_t n_tgt, const Positions& pos, int kind, const SelMap& sel,
+                                  double* out, Arena& ar, cudaStream_t st) {
+    const uint32_t pbmask = (1u << (d_eff - 1)) - 1u;
+    void* acc = ar.take<char>((size_t)(1 << d_eff) * n_tgt * 8);
+    void* wts = ar.take<char>((size_t)N * 8);
+    PolW64 pw{};
+    PolWFF pf{};
+    static_cast<ItemMap&>(pw) = im;
+    static_cast<ItemMap&>(pf) = im;
+    pw.acc = (double*)acc; pw.w = (const double*)wts; pw.pbmask = pbmask;
+    pf.acc = (FF*)acc; pf.w = (const FF*)wts; pf.pbmask = pbmask;
+    const uint32_t* const* P = pos.P;
+    if (ar.sizing) {
+        if (kind == 1) return sweep_w64(d_eff, n, P, pos.seq_top, pw, ar, st);
+        return sweep_wff(d_eff, n, P, pos.seq_top, pf, ar, st);
+    }
+    if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant sums)");
+    FK_CUDA(cudaMemsetAsync(acc, 0, (size_t)(1 << d_eff) * n_tgt * 8, st));
+    if (kind == 1) {
+        if (xd == FK_F32) k_convert<float, double><<<grid_for(N, 256), 256, 0, st>>>((const float*)y, N, (double*)wts);
+        else k_convert<double, double><<<grid_for(N, 256), 256, 0, st>>>((const double*)y, N, (double*)wts);
+    } else {
+        if (xd == FK_F32) k_convert_ff<float><<<grid_for(N, 256), 256, 0, st>>>((const float*)y, N, (FF*)wts);
+        else k_convert_ff<double><<<grid_for(N, 256), 256, 0, st>>>((const double*)y, N, (FF*)wts);
+    }
+    FK_LAUNCH_CHECK();
+    if (kind == 1) FK_TRY(sweep_w64(d_eff, n, P, pos.seq_top, pw, ar, st));
+    else FK_TRY(sweep_wff(d_eff, n, P, pos.seq_top, pf, ar, st));
+    if (sel.n == 0 || n_tgt == 0) return FK_OK;
+    const unsigned g = grid_for(n_tgt, 256);
+    if (kind == 1) k_fin_sums<double><<<g, 256, 0, st>>>((const double*)acc, n_tgt, sel, out);
+    else k_fin_sums<FF><<<g, 256, 0, st>>>((const FF*)acc, n_tgt, sel, out);
+    FK_LAUNCH_CHECK();
+    return FK_OK;
+}
+
 fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
                          const uint32_t* mask, void* out, fk_path path, Arena& ar, cudaStream_t st) {
     const int d_eff = d < 2 ? 2 : d;
     const bool sample = (z == nullptr);
     const int64_t n_tgt = sample ? N : M;
     const int64_t n = N + n_tgt;                 // sources, then target copies / targets
-    ItemMap im{N, N, n_tgt};
-    const uint32_t pbmask = (1u << (d_eff - 1)) - 1u;
     const int kind = (y == nullptr) ? 0 : (path == FK_PATH_FP64 ? 1 : 2);
-    const size_t asz = kind == 0 ? 4 : 8;
+    const SelMap sel = make_selmap(d, mask);
     size_t single_high = 0;
+    // Counts at the sample points: one item per point (a source and a
+    // target), the ties this misses corrected exactly from the tie groups of
+    // the sorted axes (fk_ties.cu); the source/target-copy layout below only
+    // when a tie group is long.  Sizing plans both and keeps the larger.
+    // (Weighted sums keep the copy layout: moving a tied term between two
+    // floating-point sums after the fact leaves a rounding residue in an
+    // orthant that holds no term.)
     if (kind == 0 && sample && N >= 2) {
-        // counts at the sample points: one item per point, ties corrected;
-        // the source/target-copy layout below only when tie groups are long
-        // (sizing plans both and keeps the larger)
         const size_t mark = ar.used;
         Positions p1;
         FK_TRY(plan_positions(x, nullptr, xd, N, N, d, d_eff, p1, ar, st));
@@ -302,48 +343,11 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
         // counts: exact inclusion-exclusion over single-orthant dominance counts
         if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
         FK_TRY(dom_orthant_counts(d, n, N, N, n_tgt, pos.P, mask, (int64_t*)out, ar, st));
-        if (ar.used < single_high) ar.used = single_high;
-        return FK_OK;
+    } else {
+        const ItemMap im{N, N, n_tgt};
+        FK_TRY(orthant_sums_run(y, xd, N, d, d_eff, im, n, n_tgt, pos, kind, sel, (double*)out, ar, st));
     }
-    void* acc = ar.take<char>((size_t)(1 << d_eff) * n_tgt * asz);
-    void* wts = (kind == 0) ? nullptr : ar.take<char>((size_t)N * 8);
-    // the sweep plans its own buffers
-    PolCount pc{};
-    PolW64 pw{};
-    PolWFF pf{};
-    static_cast<ItemMap&>(pc) = im;
-    static_cast<ItemMap&>(pw) = im;
-    static_cast<ItemMap&>(pf) = im;
-    pc.acc = (uint32_t*)acc; pc.pbmask = pbmask;
-    pw.acc = (double*)acc; pw.w = (const double*)wts; pw.pbmask = pbmask;
-    pf.acc = (FF*)acc; pf.w = (const FF*)wts; pf.pbmask = pbmask;
-    const uint32_t* const* P = pos.P;
-    if (ar.sizing) {
-        if (kind == 0) return sweep_count(d_eff, n, P, pos.seq_top, pc, ar, st);
-        if (kind == 1) return sweep_w64(d_eff, n, P, pos.seq_top, pw, ar, st);
-        return sweep_wff(d_eff, n, P, pos.seq_top, pf, ar, st);
-    }
-    if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant sums)");
-    FK_CUDA(cudaMemsetAsync(acc, 0, (size_t)(1 << d_eff) * n_tgt * asz, st));
-    if (kind == 1) {
-        if (xd == FK_F32) k_convert<float, double><<<grid_for(N, 256), 256, 0, st>>>((const float*)y, N, (double*)wts);
-        else k_convert<double, double><<<grid_for(N, 256), 256, 0, st>>>((const double*)y, N, (double*)wts);
-        FK_LAUNCH_CHECK();
-    } else if (kind == 2) {
-        if (xd == FK_F32) k_convert_ff<float><<<grid_for(N, 256), 256, 0, st>>>((const float*)y, N, (FF*)wts);
-        else k_convert_ff<double><<<grid_for(N, 256), 256, 0, st>>>((const double*)y, N, (FF*)wts);
-        FK_LAUNCH_CHECK();
-    }
-    if (kind == 0) FK_TRY(sweep_count(d_eff, n, P, pos.seq_top, pc, ar, st));
-    else if (kind == 1) FK_TRY(sweep_w64(d_eff, n, P, pos.seq_top, pw, ar, st));
-    else FK_TRY(sweep_wff(d_eff, n, P, pos.seq_top, pf, ar, st));
-    SelMap sel = make_selmap(d, mask);
-    if (sel.n == 0 || n_tgt == 0) return FK_OK;
-    const unsigned g = grid_for(n_tgt, 256);
-    if (kind == 0) k_fin_counts<<<g, 256, 0, st>>>((const uint32_t*)acc, n_tgt, sel, (int64_t*)out);
-    else if (kind == 1) k_fin_sums<double><<<g, 256, 0, st>>>((const double*)acc, n_tgt, sel, (double*)out);
-    else k_fin_sums<FF><<<g, 256, 0, st>>>((const FF*)acc, n_tgt, sel, (double*)out);
-    FK_LAUNCH_CHECK();
+    if (ar.used < single_high) ar.used = single_high;
     return FK_OK;
 }
 

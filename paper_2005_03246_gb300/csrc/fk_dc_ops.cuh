@@ -47,6 +47,22 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
 // sizing mode *fallback is left as passed.
 fk_status dom_self_counts(int d, int64_t n, const uint32_t* const* P, const void* x, fk_dtype xd,
                           const uint32_t* mask, int64_t* out, Arena& ar, cudaStream_t st, bool* fallback);
+// Ties at the sample points with one item per point (fk_ties.cu).  The rank
+// transform orders equal coordinates by point index on every axis, so the
+// engine pairs source i with target j (i != j) on the <= side of an axis
+// exactly when x_i < x_j there, or x_i == x_j and i < j.
+// tie_check: tie statistics of the d sorted axes, read back once (it
+// synchronises `st`); *fallback is set when a tie group is longer than
+// kTieGroupMax points, or the tied pairs exceed the correction's budget.
+// `sorted` [n] and `stats` [2] are scratch.
+constexpr int kTieGroupMax = 64;
+fk_status tie_check(const void* x, fk_dtype xd, int d, int64_t n, const uint32_t* const* P, uint32_t* sorted,
+                    unsigned long long* stats, cudaStream_t st, bool* fallback);
+// Counts: adds to C_A[j] (Cs[A], A a bitmask over the d axes) the sources i > j
+// with x_i <= x_j on A and a tie on some axis of A, each pair once per A.
+fk_status tie_fix_counts(const void* x, fk_dtype xd, int d, int64_t n, const uint32_t* const* P, uint32_t* sorted,
+                         uint32_t* const* Cs, cudaStream_t st);
+
 // Batched form: items in segments of 2^segE slots described by seg (see
 // dc::ItemMap); the counts of target t go to out_base[b] + r * n_b + (t - t0_b)
 // for dataset b (targets numbered by dataset), every orthant r < 2^d.

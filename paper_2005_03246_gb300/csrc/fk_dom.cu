@@ -853,87 +853,8 @@ fk_status dom_orthant_counts_seg(int d, int64_t n, const int64_t* seg, int segE,
 
 // ------------------------------------------------------------------ one item per sample point
 // At the sample points every point can be a single item that is both a
-// source and a target (half the items of the source/target-copy layout).
-// The rank transform orders equal coordinates by point index on every axis,
-// so the engine counts source i for target j (i != j) exactly when, on every
-// axis of A, x_i < x_j or (x_i == x_j and i < j).  The pairs it misses are
-// those with x_i <= x_j on A, a tie on some axis of A, and i > j; they sit in
-// the tie groups of the sorted axes and are added here, each pair once: at
-// the first axis of A on which it ties.  The self pair (x_j <= x_j) is added
-// in the combine.  Tie groups longer than kTieGroupMax fall back to the copy
-// layout (bounded work).
-namespace {
-constexpr int kTieGroupMax = 64;
-
-// The rank transform's sort key of a coordinate (-0 and +0 are one value).
-__device__ __forceinline__ uint64_t okey(float v) {
-    if (v == 0.0f) v = 0.0f;
-    const uint32_t u = __float_as_uint(v);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ uint64_t okey(double v) {
-    if (v == 0.0) v = 0.0;
-    const uint64_t u = (uint64_t)__double_as_longlong(v);
-    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
-}
-
-// stats[0] += pairs inside the tie groups of axis a; stats[1] = 1 if a group
-// is longer than kTieGroupMax.  The first position of each group counts it.
-template <class T>
-__global__ void k_tie_stats(const T* __restrict__ x, int d, int a, const uint32_t* __restrict__ sorted, int64_t n,
-                            unsigned long long* __restrict__ stats) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint64_t kp = okey(x[(int64_t)sorted[p] * d + a]);
-    if (p > 0 && okey(x[(int64_t)sorted[p - 1] * d + a]) == kp) return;
-    int64_t q = p + 1;
-    while (q < n && q - p <= kTieGroupMax && okey(x[(int64_t)sorted[q] * d + a]) == kp) ++q;
-    const int64_t L = q - p;
-    if (L > kTieGroupMax) {
-        atomicOr(stats + 1, 1ull);
-        return;
-    }
-    if (L > 1) atomicAdd(stats, (unsigned long long)(L * (L - 1) / 2));
-}
-
-struct CTabW { uint32_t* c[256]; };
-
-// For target j at sorted position p of axis a: the later members i of its tie
-// group (i > j) that the engine missed, for every subset A containing a on
-// which x_i <= x_j and whose axes below a do not tie.
-template <class T>
-__global__ void k_tie_fix(const T* __restrict__ x, int d, int a, const uint32_t* __restrict__ sorted, int64_t n,
-                          CTabW ct) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t j = sorted[p];
-    uint64_t kj[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) kj[b] = (b < d) ? okey(x[(int64_t)j * d + b]) : 0ull;
-    const uint32_t abit = 1u << a;
-    for (int64_t q = p + 1; q < n && q - p <= kTieGroupMax; ++q) {
-        const uint32_t i = sorted[q];
-        if (okey(x[(int64_t)i * d + a]) != kj[a]) break;
-        uint32_t le = 0, eq = 0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            if (b < d) {
-                const uint64_t ki = okey(x[(int64_t)i * d + b]);
-                le |= (ki <= kj[b] ? 1u : 0u) << b;
-                eq |= (ki == kj[b] ? 1u : 0u) << b;
-            }
-        }
-        const uint32_t rest = le & ~(eq & (abit - 1u)) & ~abit;
-        uint32_t S = 0;
-        while (true) {
-            atomicAdd(ct.c[S | abit] + j, 1u);
-            if (S == rest) break;
-            S = (S - rest) & rest;
-        }
-    }
-}
-}  // namespace
-
+// source and a target (half the items of the source/target-copy layout);
+// the ties this misses are corrected by tie_fix_counts (fk_ties.cu).
 fk_status dom_self_counts(int d, int64_t n, const uint32_t* const* P, const void* x, fk_dtype xd,
                           const uint32_t* mask, int64_t* out, Arena& ar, cudaStream_t st, bool* fallback) {
     const int nsub = 1 << d;
@@ -941,36 +862,14 @@ fk_status dom_self_counts(int d, int64_t n, const uint32_t* const* P, const void
     unsigned long long* stats = ar.take<unsigned long long>(2);
     if (!ar.sizing) {
         if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
-        // tie statistics of every axis; the host decides on the layout
-        FK_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), st));
-        const unsigned g = grid_for(n, 256);
-        for (int a = 0; a < d; ++a) {
-            k_seq_from_pos<<<g, 256, 0, st>>>(P[a], n, sorted);
-            FK_LAUNCH_CHECK();
-            if (xd == FK_F32) k_tie_stats<float><<<g, 256, 0, st>>>((const float*)x, d, a, sorted, n, stats);
-            else k_tie_stats<double><<<g, 256, 0, st>>>((const double*)x, d, a, sorted, n, stats);
-            FK_LAUNCH_CHECK();
-        }
-        unsigned long long hs[2] = {0, 0};
-        FK_CUDA(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-        FK_CUDA(cudaStreamSynchronize(st));
-        *fallback = hs[1] != 0 || hs[0] > (unsigned long long)(4 * n + 4096);
+        FK_TRY(tie_check(x, xd, d, n, P, sorted, stats, st, fallback));
         if (*fallback) return FK_OK;
     }
     uint32_t* Cs[256] = {};
     Items im{n, 0, n, 0u, nullptr, 0};
     FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams));
     if (ar.sizing) return FK_OK;
-    CTabW cw = {};
-    for (int A = 1; A < nsub; ++A) cw.c[A] = Cs[A];
-    const unsigned g = grid_for(n, 256);
-    for (int a = 0; a < d; ++a) {
-        k_seq_from_pos<<<g, 256, 0, st>>>(P[a], n, sorted);
-        FK_LAUNCH_CHECK();
-        if (xd == FK_F32) k_tie_fix<float><<<g, 256, 0, st>>>((const float*)x, d, a, sorted, n, cw);
-        else k_tie_fix<double><<<g, 256, 0, st>>>((const double*)x, d, a, sorted, n, cw);
-        FK_LAUNCH_CHECK();
-    }
+    FK_TRY(tie_fix_counts(x, xd, d, n, P, sorted, Cs, st));
     dc::SelMap sel;
     sel.n = 0;
     for (int o = 0; o < nsub; ++o)

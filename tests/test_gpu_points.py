@@ -302,3 +302,42 @@ def test_counts_long_tie_groups_fall_back(d):
     x = r.integers(0, 4, size=(3000, d)).astype(np.float32)
     got = _fk().ecdf_points(_t(x)).cpu().numpy()
     assert np.array_equal(got, oracle.orthant_sums(x))
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_weighted_sums_with_short_ties_and_duplicates(d, dtype, path):
+    """Weighted orthant sums at the sample points with short tie groups and
+    exact duplicates (tied on every axis); error against the oracle relative
+    to the orthant sums of |y| (exact zeros where an orthant holds no point);
+    an orthant mask selects a subset of rows; the ESF."""
+    r = np.random.default_rng(1000 + d)
+    n = 3000
+    x = r.standard_normal((n, d))
+    m = r.random((n, d)) < 0.5
+    x[m] = np.round(x[m] * 256) / 256
+    dup = r.choice(n, size=n // 20, replace=False)
+    x[dup] = x[r.integers(0, n, size=dup.size)]
+    x = x.astype(dtype)
+    y = r.standard_normal(n).astype(dtype)
+    got = _fk().ecdf_points(_t(x), y=_t(y), path=path).cpu().numpy()
+    ref = oracle.orthant_sums(x, y=y)
+    absw = oracle.orthant_sums(x, y=np.abs(y))
+    assert _rel_signed(got, ref, absw) <= TOL[path]
+    sel = [0, (1 << d) - 1, 1]
+    g2 = _fk().ecdf_points(_t(x), y=_t(y), orthants=sel, path=path).cpu().numpy()
+    assert _rel_signed(g2, ref[sorted(sel)], absw[sorted(sel)]) <= TOL[path]
+    esf = _fk().esf_points(_t(x), y=_t(y), path=path).cpu().numpy()
+    assert _rel_signed(esf.reshape(-1), ref[-1], absw[-1]) <= TOL[path]
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+def test_weighted_sums_integer_lattice(path):
+    r = np.random.default_rng(1100)
+    x = r.integers(0, 5, size=(2500, 3)).astype(np.float64)
+    y = r.standard_normal(2500)
+    got = _fk().ecdf_points(_t(x), y=_t(y), path=path).cpu().numpy()
+    ref = oracle.orthant_sums(x, y=y)
+    absw = oracle.orthant_sums(x, y=np.abs(y))
+    assert _rel_signed(got, ref, absw) <= TOL[path]
