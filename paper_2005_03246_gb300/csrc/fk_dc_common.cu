@@ -127,11 +127,6 @@ __device__ __forceinline__ double as_f64(uint32_t v) { return (double)v; }
 __device__ __forceinline__ double as_f64(double v) { return v; }
 __device__ __forceinline__ double as_f64(FF v) { return ff_to_double(v); }
 
-__global__ void k_fin_counts(const uint32_t* __restrict__ acc, int64_t n_tgt, SelMap sel, int64_t* __restrict__ out) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tgt) return;
-    for (int r = 0; r < sel.n; ++r) out[(int64_t)r * n_tgt + t] = (int64_t)acc[(int64_t)sel.o[r] * n_tgt + t];
-}
 template <class A>
 __global__ void k_fin_sums(const A* __restrict__ acc, int64_t n_tgt, SelMap sel, double* __restrict__ out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -397,7 +392,6 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
     if (ar.sizing) return run();
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (kernel sums)");
     const unsigned g = grid_for(n, 256);
-    const double* zz = nullptr;
     if (xd == FK_F32) {
         if (fp64) k_factors<float, FacD><<<g, 256, 0, st>>>((const float*)x, (const float*)z, d, d_eff, N, n, hv, (FacD*)fac);
         else k_factors<float, FacF><<<g, 256, 0, st>>>((const float*)x, (const float*)z, d, d_eff, N, n, hv, (FacF*)fac);
@@ -405,7 +399,6 @@ fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void
         if (fp64) k_factors<double, FacD><<<g, 256, 0, st>>>((const double*)x, (const double*)z, d, d_eff, N, n, hv, (FacD*)fac);
         else k_factors<double, FacF><<<g, 256, 0, st>>>((const double*)x, (const double*)z, d, d_eff, N, n, hv, (FacF*)fac);
     }
-    (void)zz;
     FK_LAUNCH_CHECK();
     if (w) {
         const unsigned gw = grid_for(N, 256);

@@ -14,7 +14,6 @@ struct SelMap { int n; int o[256]; };   // output row r <- internal orthant o[r]
 #define FK_DC_SWEEP_DECL(NAME, POL)                                                              \
     fk_status NAME(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,    \
                    const POL& pol, Arena& ar, cudaStream_t st, int levels = -1, int opts = 0);
-FK_DC_SWEEP_DECL(sweep_count, PolCount)
 FK_DC_SWEEP_DECL(sweep_w64, PolW64)
 FK_DC_SWEEP_DECL(sweep_wff, PolWFF)
 FK_DC_SWEEP_DECL(sweep_kf1, PolKF<1>)
