@@ -36,11 +36,15 @@
  *   inputs must not change before then.  With any pageable host array the
  *   call returns only after the host outputs are written.  The caller owns
  *   every buffer; the library never frees caller memory and keeps no state
- *   between calls other than the per-device error word (fk_device_status).
+ *   between calls other than the per-device error word (fk_device_status),
+ *   its own streams, and the memory its pool caches (fk_release_cached_memory).
  * Workspace.  `ws`/`ws_bytes` is caller-owned device scratch of at least the
  *   size returned by the matching *_workspace function (256-byte aligned).
  *   If ws == NULL the library allocates and frees its scratch itself
  *   (stream-ordered).  A non-NULL ws that is too small returns FK_ERR_WORKSPACE.
+ *   The library's own allocations (scratch and host-array staging) come from
+ *   a stream-ordered memory pool per device that keeps freed memory for later
+ *   calls; fk_release_cached_memory() returns it to the driver.
  * Limits.  1 <= d <= 8 for the grid call and for orthant counts at the
  *   sample points (fk_ecdf_points / fk_esf_points with y == NULL; the work
  *   grows as N log^(d-1) N); 1 <= d <= 4 for the other sample-point
@@ -435,6 +439,14 @@ fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xdtype
 fk_status fk_ecdf_grid_counts_noalloc(const void* x, fk_dtype xdtype, int64_t N, int d, const double* z_axes,
                                       const int64_t* M, const uint32_t* orthant_mask, int64_t* out,
                                       fk_stream_t stream);
+
+/*
+ * fk_release_cached_memory -- returns the memory the library's pool of the
+ * current device keeps between calls (scratch and staging buffers freed by
+ * earlier calls) to the driver.  Call it when no library call is in flight on
+ * the device.
+ */
+fk_status fk_release_cached_memory(void);
 
 /*
  * fk_device_status -- synchronises `stream` and returns (and clears) the

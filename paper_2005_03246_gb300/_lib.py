@@ -73,6 +73,7 @@ SIGNATURES = {
     "fk_kreg_loclin_laplace_workspace": (SZ, [I64, I, I64, I, I]),
     "fk_kreg_loclin_laplace": (I, [P, I, I64, I, P, P, I64, P, U, P, I, P, SZ, P]),
     "fk_ecdf_grid_counts_noalloc": (I, [P, I, I64, I, P, P, P, P, P]),
+    "fk_release_cached_memory": (I, []),
     "fk_kernel_launches": (ctypes.c_uint64, []),
     "fk_profile_enable": (None, [I]),
     "fk_profile_reset": (None, []),

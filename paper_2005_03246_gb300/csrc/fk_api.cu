@@ -110,6 +110,40 @@ fk_status device_error_word(int** ptr) {
     return FK_OK;
 }
 
+// Library-owned stream-ordered memory pool of each device, for staging
+// buffers and internal workspaces.  Freed blocks stay in the pool for the next
+// call (the default pool would hand them back to the driver at every
+// synchronisation and map them again); fk_release_cached_memory() trims it.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static fk_status lib_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(FK_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        FK_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t keep = UINT64_MAX;
+        FK_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[dev] = p;
+    }
+    *out = g_pool[dev];
+    return FK_OK;
+}
+
+static fk_status pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    FK_TRY(lib_pool(&pool));
+    FK_CUDA(cudaMallocFromPoolAsync(p, bytes, pool, st));
+    return FK_OK;
+}
+
 // Stages caller arrays that live in host memory through device buffers.  The
 // staging buffers are allocated and freed in stream order.  If every host
 // array of the call is page-locked the copies stay asynchronous and so does
@@ -130,7 +164,7 @@ struct Stager {
         if (!p || bytes == 0 || is_device_pointer(p)) return FK_OK;
         if (!is_pinned_host_pointer(p)) any_pageable = true;
         void* d = nullptr;
-        FK_CUDA(cudaMallocAsync(&d, bytes, st));
+        FK_TRY(pool_alloc(&d, bytes, st));
         allocs.push_back(d);
         FK_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, st));
         *dev = d;
@@ -142,7 +176,7 @@ struct Stager {
         if (!p || bytes == 0 || is_device_pointer(p)) return FK_OK;
         if (!is_pinned_host_pointer(p)) any_pageable = true;
         void* d = nullptr;
-        FK_CUDA(cudaMallocAsync(&d, bytes, st));
+        FK_TRY(pool_alloc(&d, bytes, st));
         allocs.push_back(d);
         outs.push_back(Out{d, p, bytes});
         *dev = d;
@@ -176,7 +210,7 @@ struct Workspace {
             ar.cap = ws_bytes;
             return FK_OK;
         }
-        if (need > 0) FK_CUDA(cudaMallocAsync(&owned, need, st));
+        if (need > 0) FK_TRY(pool_alloc(&owned, need, st));
         ar.base = (char*)owned;
         ar.cap = need;
         return FK_OK;
@@ -230,6 +264,18 @@ fk_status fk_profile_read(int family, double* total_ms, uint64_t* launches, doub
     if (total_ms) *total_ms = ms;
     if (launches) *launches = cnt;
     if (alg_bytes) *alg_bytes = by;
+    return FK_OK;
+}
+
+fk_status fk_release_cached_memory(void) {
+    int dev = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (dev >= 0 && dev < 64) p = g_pool[dev];
+    }
+    if (p) FK_CUDA(cudaMemPoolTrimTo(p, 0));
     return FK_OK;
 }
 

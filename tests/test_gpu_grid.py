@@ -128,3 +128,22 @@ def test_pinned_host_buffers_are_asynchronous_and_correct():
     assert np.array_equal(op.numpy(), oracle.orthant_sums(data["x"]))
     ref = oracle.kde_laplace(data["x"], h)
     assert np.max(np.abs(of.numpy() - ref) / ref) <= 1e-12
+
+
+def test_pool_memory_reuse_and_release():
+    """Calls without a workspace allocate from the library's pool; the cached
+    memory can be released between calls and later calls still work."""
+    import ctypes
+    from paper_2005_03246_gb300 import _lib
+    lib = _lib.load()
+    data = datagen.ecdf_small(n=2000)
+    x = np.ascontiguousarray(data["x"])
+    ref = oracle.orthant_sums(x)
+    for k in range(3):
+        out = np.zeros((4, 2000), dtype=np.int64)
+        rc = lib.fk_ecdf_points(x.ctypes.data_as(ctypes.c_void_p), _lib.FK_F64, 2000, 2, None, None, 0, None,
+                                out.ctypes.data_as(ctypes.c_void_p), 0, None, 0, None)
+        _lib.check(rc, "fk_ecdf_points(host)")
+        assert np.array_equal(out, ref)
+        if k == 1:
+            _lib.check(lib.fk_release_cached_memory(), "fk_release_cached_memory")
