@@ -47,6 +47,11 @@ struct MergeArgs {
     uint32_t* meta_out;
     int64_t n;
     int logR;     // input runs of length R = 2^logR, output runs 2R
+    // Optional [2 x CTAs] merge-path co-ranks of each CTA's first and last
+    // output in runs longer than a tile: the totals pass of a level finds and
+    // writes them (co_read == 0), the sweep pass of the same level reads them.
+    int64_t* co = nullptr;
+    int co_read = 0;
 };
 
 // ------------------------------------------------------------ generic shuffles
@@ -274,15 +279,29 @@ __device__ __forceinline__ MergeTile merge_tile_load(const MergeArgs& a, uint32_
     t.big = R2 > MTILE;
     t.lc = t.cs = t.ds = t.ldd = 0;
     if (t.big) {
-        if (threadIdx.x < 64) {
+        if (a.co && a.co_read) {
+            if (threadIdx.x == 0) {
+                const int64_t bs = (o0 / R2) * R2;
+                const int64_t cl = min(R, n - bs);
+                const int64_t q0 = o0 - bs;
+                const int64_t iq0 = a.co[2 * (int64_t)blockIdx.x], iq1 = a.co[2 * (int64_t)blockIdx.x + 1];
+                s_co[0] = bs + iq0; s_co[2] = bs + cl + (q0 - iq0); s_co[4] = iq0; s_co[5] = iq1;
+            }
+        } else if (threadIdx.x < 64) {
             const int64_t bs = (o0 / R2) * R2;
             const int64_t cl = min(R, n - bs);
             const int64_t dl = max((int64_t)0, min(R2, n - bs) - cl);
             const int64_t q0 = o0 - bs, q1 = o1 - bs;
             const int64_t iq = merge_path_warp(a.key_in + bs, cl, a.key_in + bs + cl, dl,
                                                threadIdx.x < 32 ? q0 : q1);
-            if (threadIdx.x == 0) { s_co[0] = bs + iq; s_co[2] = bs + cl + (q0 - iq); s_co[4] = iq; }
-            if (threadIdx.x == 32) s_co[5] = iq;
+            if (threadIdx.x == 0) {
+                s_co[0] = bs + iq; s_co[2] = bs + cl + (q0 - iq); s_co[4] = iq;
+                if (a.co) a.co[2 * (int64_t)blockIdx.x] = iq;
+            }
+            if (threadIdx.x == 32) {
+                s_co[5] = iq;
+                if (a.co) a.co[2 * (int64_t)blockIdx.x + 1] = iq;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {

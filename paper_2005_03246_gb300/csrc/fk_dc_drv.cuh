@@ -599,6 +599,7 @@ struct DCBuffers {
     uint32_t* m[2];   // inner sort ping-pong metas
     void* totals;
     void* carries;
+    int64_t* co;      // merge-path co-ranks of a level, shared by its totals and sweep passes
     // folded kernel sums: record arrays (fm, fs, wt, fa) of each ping-pong side
     void* rec[2][4];
     // kernel sums: per-item base factors of this buffer set's sorts (levels
@@ -688,6 +689,7 @@ fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cu
         const int last = (m == E - 1) ? 1 : 0;
         const int64_t R2 = (int64_t)2 << m;
         const V* carries = nullptr;
+        if (R2 > MTILE) a.co = b.co;          // the totals pass finds the co-ranks
         if (R2 > MTILE) {
             {
                 ProfScope ps(PF_MERGE_TOTALS, (rec_bytes - Pol::kNW * sizeof(typename Pol::FA)) * n, st);
@@ -702,6 +704,7 @@ fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cu
             FK_LAUNCH_CHECK();
             carries = (const V*)b.carries;
         }
+        a.co_read = 1;                        // and the sweep reuses them
         ProfScope ps(PF_MERGE_SWEEP, rec_bytes * n * (last ? 0.5 : 1.0) + (last ? 8.0 * pol.n_tgt : 0.0), st);
         k_merge_fold<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, rin, rout, pol, nullptr, carries, last);
         FK_LAUNCH_CHECK();
@@ -737,6 +740,7 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
         MergeArgs a{b.k[cur], b.m[cur], b.k[cur ^ 1], b.m[cur ^ 1], n, m};
         const int64_t R2 = (int64_t)2 << m;
         if (R2 > MTILE) {
+            a.co = b.co;                      // found by the totals pass, reused by the sweep
             {
                 ProfScope ps(PF_MERGE_TOTALS, 8.0 * n + (double)pol.n_src * Pol::kSrcBytes, st);
                 k_merge<Pol, CLSB, PH_TOTALS><<<ctas, MT, 0, st>>>(a, pol, (V*)b.totals, nullptr);
@@ -747,6 +751,7 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
             k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
                                                                               (V*)b.carries, n, m);
             FK_LAUNCH_CHECK();
+            a.co_read = 1;
             ProfScope ps(PF_MERGE_SWEEP, sweep_bytes, st);
             k_merge<Pol, CLSB, PH_SWEEP><<<ctas, MT, 0, st>>>(a, pol, nullptr, (const V*)b.carries);
             FK_LAUNCH_CHECK();
@@ -871,6 +876,7 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
         for (int q = 0; q < 2; ++q) { ib[s].k[q] = ar.take<uint32_t>(n); ib[s].m[q] = ar.take<uint32_t>(n); }
         ib[s].totals = ar.take<V>((size_t)ctas * 2 * NCH);
         ib[s].carries = ar.take<V>((size_t)ctas * 2 * NCH);
+        ib[s].co = ar.take<int64_t>((size_t)ctas * 2);
         for (int q = 0; q < 2; ++q)
             for (int j = 0; j < 4; ++j) ib[s].rec[q][j] = nullptr;
         ib[s].base = nullptr;
