@@ -415,6 +415,9 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = _e2e(lib, x_np, grid, args, dev)
+        # whole job: the slowest rank's step time, the points of all ranks
+        ms_e2e, e2e["value"] = aggregate_replicas(e2e["ms_per_step"], 1, n, ws, dev)
+        e2e["ms_per_step"] = ms_e2e
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
