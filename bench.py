@@ -29,6 +29,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -63,6 +64,9 @@ def _args(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serial", action="store_true",
                     help="run the step's three calls one after another on one stream")
+    ap.add_argument("--scaling", action="store_true",
+                    help="time the sample-point counts, the KDE and the grid counts over d and N (the "
+                         "paper's runtime-versus-N study) and print one JSON line")
     ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
                     help="run one operation per step (profiling of a single kernel family)")
     return ap.parse_args(argv)
@@ -586,10 +590,64 @@ def _e2e(lib, x_np, grid, args, dev):
             "ms_per_step": t * 1e3, "streams": 3}
 
 
+def run_scaling(args):
+    """Runtime versus N at d = 2, 3, 4 on correlated Gaussian data (S_ij = 0.5,
+    FP32): all 2^d orthant counts at the sample points, the mixed-path KDE at
+    h = 0.1, and the grid counts on a grid of ~N points; each time divided by
+    N log2^(d-1) N (the divide-and-conquer cost the paper states, Sec. 2.2)
+    and, for the grid, by N.  Median of 3 runs with L2 flushed; CUDA events."""
+    import torch
+    import paper_2005_03246_gb300 as fk
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        v = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            r = fn()
+            b.record(st)
+            b.synchronize()
+            v.append(a.elapsed_time(b))
+            del r
+        return statistics.median(v)
+
+    rows = []
+    r = np.random.default_rng(9)
+    for d in (2, 3, 4):
+        S = np.full((d, d), 0.5) + 0.5 * np.eye(d)
+        L = np.linalg.cholesky(S)
+        for n in (100_000, 300_000, 1_000_000, 3_000_000):
+            xn = (r.standard_normal((n, d)) @ L.T).astype(np.float32)
+            x = torch.as_tensor(xn, device=dev)
+            m = max(2, int(round(n ** (1.0 / d))))
+            axes = [np.linspace(float(xn[:, k].min()), float(xn[:, k].max()), m) for k in range(d)]
+            t_pts = timed(lambda: fk.ecdf_points(x))
+            t_kde = timed(lambda: fk.kde_laplace(x, 0.1, path="mixed"))
+            t_grid = timed(lambda: fk.ecdf_grid(x, axes))
+            shape = n * math.log2(n) ** (d - 1)
+            rows.append({"d": d, "n": n, "points_ms": t_pts, "kde_mixed_ms": t_kde, "grid_ms": t_grid,
+                         "grid_points": m ** d, "points_ns_per_NlogN": t_pts * 1e6 / shape,
+                         "kde_ns_per_NlogN": t_kde * 1e6 / shape, "grid_ns_per_N": t_grid * 1e6 / n})
+            del x
+            torch.cuda.empty_cache()
+    print(json.dumps({"scaling": rows, "data": "synthetic correlated Gaussian, FP32",
+                      "shape": "N log2^(d-1) N for the sample-point calls, N for the grid"}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.scaling:
+        return run_scaling(args)
     return run_ours(args)
 
 
