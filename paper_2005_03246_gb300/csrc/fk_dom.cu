@@ -743,12 +743,38 @@ static fk_status dom_recurse(int k, const uint32_t* seq, int64_t n, int E, const
 // The dominance problems of the subsets with |A| >= 2 are independent: with
 // streams > 1 they run concurrently on forked streams, each stream with its
 // own engine buffers.
+// Subsets A of the d axes (bitmasks) whose counts C_A an orthant selection
+// needs: orthant o reads C_{pos(o) | T} for every subset T of neg(o).
+struct SubsetSet {
+    uint32_t w[8];
+    bool has(int A) const { return (w[A >> 5] >> (A & 31)) & 1u; }
+};
+static SubsetSet subsets_for(int d, const uint32_t* mask) {
+    SubsetSet ss = {};
+    const uint32_t full = (1u << d) - 1u;
+    for (int o = 0; o < (1 << d); ++o) {
+        if (mask && !((mask[o >> 5] >> (o & 31)) & 1u)) continue;
+        const uint32_t pos = full & ~(uint32_t)o, neg = (uint32_t)o;
+        uint32_t T = 0;
+        while (true) {
+            const uint32_t A = pos | T;
+            ss.w[A >> 5] |= 1u << (A & 31);
+            if (T == neg) break;
+            T = (T - neg) & neg;
+        }
+    }
+    return ss;
+}
+
 static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32_t* const* P, uint32_t** Cs,
-                                 Arena& ar, cudaStream_t st, int count_tile = 0, int streams = 1) {
+                                 Arena& ar, cudaStream_t st, int count_tile = 0, int streams = 1,
+                                 const SubsetSet* need = nullptr) {
     const int nsub = 1 << d;
     const int64_t n_tgt = im.n_tgt;
     int nbig = 0;
     for (int A = 1; A < nsub; ++A) {
+        Cs[A] = nullptr;
+        if (need && !need->has(A)) continue;      // no selected orthant reads C_A
         Cs[A] = ar.take<uint32_t>((size_t)n_tgt);
         if (__builtin_popcount((unsigned)A) >= 2) ++nbig;
     }
@@ -776,11 +802,12 @@ static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32
     uint32_t* stmp = ar.take<uint32_t>(scan_u32_tmp_words(n));
     if (ar.sizing) return FK_OK;
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (orthant counts)");
-    for (int A = 1; A < nsub; ++A) FK_CUDA(cudaMemsetAsync(Cs[A], 0, (size_t)n_tgt * 4, st));
+    for (int A = 1; A < nsub; ++A)
+        if (Cs[A]) FK_CUDA(cudaMemsetAsync(Cs[A], 0, (size_t)n_tgt * 4, st));
     const unsigned g = grid_for(n, 256);
     // rank counts (|A| = 1) on the caller's stream
     for (int A = 1; A < nsub; ++A) {
-        if (__builtin_popcount((unsigned)A) != 1) continue;
+        if (__builtin_popcount((unsigned)A) != 1 || !Cs[A]) continue;
         const uint32_t* PA = P[__builtin_ctz((unsigned)A)];
         k_src_flags<<<g, 256, 0, st>>>(PA, n, im, flags);
         FK_LAUNCH_CHECK();
@@ -794,7 +821,7 @@ static fk_status dom_counts_core(int d, int64_t n, Items im, int E, const uint32
     int j = 0;
     for (int A = 1; A < nsub && rc == FK_OK; ++A) {
         const int k = __builtin_popcount((unsigned)A);
-        if (k < 2) continue;
+        if (k < 2 || !Cs[A]) continue;
         const int q = j++ % S;
         cudaStream_t ss = fork.s[q];
         const uint32_t* PA[8];
@@ -821,7 +848,8 @@ fk_status dom_orthant_counts(int d, int64_t n, int64_t n_src, int64_t tgt_off, i
     const int nsub = 1 << d;
     uint32_t* Cs[256] = {};
     Items im{n_src, tgt_off, n_tgt, 0u, nullptr, 0};
-    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams));
+    const SubsetSet need = subsets_for(d, mask);
+    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams, &need));
     if (ar.sizing) return FK_OK;
     dc::SelMap sel;
     sel.n = 0;
@@ -867,7 +895,8 @@ fk_status dom_self_counts(int d, int64_t n, const uint32_t* const* P, const void
     }
     uint32_t* Cs[256] = {};
     Items im{n, 0, n, 0u, nullptr, 0};
-    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams));
+    const SubsetSet need = subsets_for(d, mask);
+    FK_TRY(dom_counts_core(d, n, im, dc::ceil_log2(n), P, Cs, ar, st, 0, kCountStreams, &need));
     if (ar.sizing) return FK_OK;
     FK_TRY(tie_fix_counts(x, xd, d, n, P, sorted, Cs, st));
     dc::SelMap sel;

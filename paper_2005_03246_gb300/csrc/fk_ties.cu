@@ -93,8 +93,9 @@ __global__ void k_tie_fix_counts(const T* __restrict__ x, int d, int a, const ui
         masks_of(x, d, i, kj, le, gt, eq);
         const uint32_t rest = le & ~(eq & (abit - 1u)) & ~abit;
         uint32_t S = 0;
-        while (true) {       // every subset S of rest: A = S | a
-            atomicAdd(ct.c[S | abit] + j, 1u);
+        while (true) {       // every subset S of rest: A = S | a (if an orthant reads C_A)
+            uint32_t* c = ct.c[S | abit];
+            if (c) atomicAdd(c + j, 1u);
             if (S == rest) break;
             S = (S - rest) & rest;
         }
