@@ -57,9 +57,8 @@ fk_status dom_self_counts(int d, int64_t n, const uint32_t* const* P, const void
 constexpr int kTieGroupMax = 64;
 fk_status tie_check(const void* x, fk_dtype xd, int d, int64_t n, const uint32_t* const* P, uint32_t* sorted,
                     unsigned long long* stats, cudaStream_t st, bool* fallback);
-// Counts: adds to C_A[j] (Cs[A], A a bitmask over the d axes; NULL where no
-// selected orthant needs C_A) the sources i > j with x_i <= x_j on A and a tie
-// on some axis of A, each pair once per A.
+// Counts: adds to C_A[j] (Cs[A], A a bitmask over the d axes) the sources i > j
+// with x_i <= x_j on A and a tie on some axis of A, each pair once per A.
 fk_status tie_fix_counts(const void* x, fk_dtype xd, int d, int64_t n, const uint32_t* const* P, uint32_t* sorted,
                          uint32_t* const* Cs, cudaStream_t st);
 

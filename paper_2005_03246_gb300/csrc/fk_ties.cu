@@ -122,6 +122,7 @@ fk_status tie_check(const void* x, fk_dtype xd, int d, int64_t n, const uint32_t
     return FK_OK;
 }
 
+// Cs[A] is NULL for the subsets no selected orthant reads; those are skipped.
 fk_status tie_fix_counts(const void* x, fk_dtype xd, int d, int64_t n, const uint32_t* const* P, uint32_t* sorted,
                          uint32_t* const* Cs, cudaStream_t st) {
     CTabW cw = {};
