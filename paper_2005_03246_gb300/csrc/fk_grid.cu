@@ -94,9 +94,10 @@ __global__ void k_axis_pass_cols(const typename Op::A* __restrict__ in, void* __
     int64_t c = rest / outer;
     const A* src = in + ((c * outer + oo) * E) * inner + ii;
     const int64_t M = E - 1;
-    int s_plus = kFinal ? sel.s[2 * c] : 0, s_minus = kFinal ? sel.s[2 * c + 1] : 0;
+    // output row (final pass) or a needed flag (>= 0) of each output channel
+    const int s_plus = sel.s[2 * c], s_minus = sel.s[2 * c + 1];
     // prefix (delta_k = +1)
-    if (!kFinal || s_plus >= 0) {
+    if (s_plus >= 0) {
         A run = Op::zero();
         for (int64_t e = 0; e < M; ++e) {
             run = Op::add(run, src[e * inner]);
@@ -106,7 +107,7 @@ __global__ void k_axis_pass_cols(const typename Op::A* __restrict__ in, void* __
         }
     }
     // strict suffix (delta_k = -1)
-    if (!kFinal || s_minus >= 0) {
+    if (s_minus >= 0) {
         A run = Op::zero();
         for (int64_t e = M; e >= 1; --e) {
             run = Op::add(run, src[e * inner]);
@@ -133,8 +134,8 @@ __global__ void k_axis_pass_rows(const typename Op::A* __restrict__ in, void* __
     const A* src = in + (c * lines_per_ch + line) * E;
     const int64_t M = E - 1;
     for (int dir = 0; dir < 2; ++dir) {
-        int srow = kFinal ? sel.s[2 * c + dir] : 0;
-        if (kFinal && srow < 0) continue;
+        const int srow = sel.s[2 * c + dir];   // output row, or a needed flag before the last pass
+        if (srow < 0) continue;
         A carry = Op::zero();
         const int64_t chunk = 32 * kPer;
         int64_t nchunks = (E + chunk - 1) / chunk;
@@ -209,23 +210,40 @@ fk_status run_passes(typename Op::A* hist, typename Op::A* b1, typename Op::A* b
     int64_t cin = 1;
     for (int k = d - 1; k >= 0; --k) {
         bool fin = (k == 0);
+        // Output channel ch of the pass on axis k holds the directions of axes
+        // k..d-1 (bit i - k for axis i); before the last pass only the channels
+        // that feed a selected orthant o (o >> k == ch) are computed.
+        SelTable need;
+        if (!fin) {
+            for (int ch = 0; ch < 256; ++ch) need.s[ch] = -1;
+            for (int o = 0; o < (1 << d); ++o)
+                if (sel.s[o] >= 0) need.s[o >> k] = 0;
+        }
+        const SelTable& tab = fin ? sel : need;
         int64_t outer = 1, inner = 1;
         for (int a = 0; a < k; ++a) outer *= (M[a] + 1);
         for (int a = k + 1; a < d; ++a) inner *= M[a];
         int64_t E = M[k] + 1;
         // algorithmic bytes: every input cell read once, every output written once
         const double obytes = fin ? (double)sizeof(typename Op::O) : (double)sizeof(A);
-        ProfScope ps(PF_GRID_PASS, (double)cin * outer * inner * ((double)E * sizeof(A) + 2.0 * (E - 1) * obytes), st);
+        int64_t nin = 0, nout = 0;   // input channels read, output channels written
+        for (int64_t c = 0; c < cin; ++c) {
+            const int64_t o = (tab.s[2 * c] >= 0 ? 1 : 0) + (tab.s[2 * c + 1] >= 0 ? 1 : 0);
+            nout += o;
+            nin += o > 0 ? 1 : 0;
+        }
+        ProfScope ps(PF_GRID_PASS, (double)outer * inner * ((double)nin * E * sizeof(A) + (double)nout * (E - 1) * obytes),
+                     st);
         if (inner == 1) {
             int64_t warps = cin * outer;
             unsigned blocks = grid_for(warps * 32, 256);
-            if (fin) k_axis_pass_rows<Op, true><<<blocks, 256, 0, st>>>(cur, out, outer, cin, E, sel, out_row);
-            else k_axis_pass_rows<Op, false><<<blocks, 256, 0, st>>>(cur, nxt, outer, cin, E, sel, 0);
+            if (fin) k_axis_pass_rows<Op, true><<<blocks, 256, 0, st>>>(cur, out, outer, cin, E, tab, out_row);
+            else k_axis_pass_rows<Op, false><<<blocks, 256, 0, st>>>(cur, nxt, outer, cin, E, tab, 0);
         } else {
             int64_t threads = cin * outer * inner;
             unsigned blocks = grid_for(threads, 256);
-            if (fin) k_axis_pass_cols<Op, true><<<blocks, 256, 0, st>>>(cur, out, cin, outer, E, inner, sel, out_row);
-            else k_axis_pass_cols<Op, false><<<blocks, 256, 0, st>>>(cur, nxt, cin, outer, E, inner, sel, 0);
+            if (fin) k_axis_pass_cols<Op, true><<<blocks, 256, 0, st>>>(cur, out, cin, outer, E, inner, tab, out_row);
+            else k_axis_pass_cols<Op, false><<<blocks, 256, 0, st>>>(cur, nxt, cin, outer, E, inner, tab, 0);
         }
         FK_LAUNCH_CHECK();
         cin *= 2;
