@@ -57,8 +57,8 @@ def _digest() -> str:
 # traffic figure of a family stays valid while the digest of these files and
 # of the compile flags is unchanged.
 FAMILY_SOURCES = {
-    "merge_sweep": ["fk_dom.cu", "fk_dc.cuh", "fk_dc_drv.cuh", "fk_dc_ops.cuh", "fk_internal.cuh"],
-    "kernel_local": ["fk_dc.cuh", "fk_dc_drv.cuh", "fk_dc_ops.cuh", "fk_internal.cuh"],
+    "merge_sweep": ["fk_dom.cu", "fk_dc.cuh", "fk_dc_drv.cuh", "fk_dc_ops.cuh", "fk_dc_common.cu", "fk_internal.cuh"],
+    "kernel_local": ["fk_dc.cuh", "fk_dc_drv.cuh", "fk_dc_ops.cuh", "fk_dc_common.cu", "fk_internal.cuh"],
 }
 
 
