@@ -55,7 +55,7 @@ WORKLOAD = "ecdf_gauss3_d3_n1e6_grid256_kde_h0.1"
 def _args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_POINTS)
@@ -99,37 +99,65 @@ def _peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    """Samples nvidia-smi clocks and throttle reasons during the timed region.
+
+    start() launches the sampler and waits (at most `ready_s`) for its first
+    line, so that it is running before the region opens; begin() and stop()
+    bracket the region, and only the lines that arrive inside it (plus
+    `grace_s` for the sample in flight when it closes) are summarised.  When
+    the region is shorter than the sampling period and no line falls inside,
+    the first line after begin() stands for it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=200, cmd=None, ready_s=5.0, grace_s=0.05):
         self.index = index
+        self.period_s = period_ms / 1e3
+        self.cmd = cmd or ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                           "--format=csv,noheader,nounits", "-lms", str(period_ms)]
+        self.ready_s = ready_s
+        self.grace_s = grace_s
         self.proc = None
-        self.lines = []
+        self.lines = []            # (arrival time, line)
         self.thread = None
+        self.first = threading.Event()
+        self.t_begin = None
+        self.t_end = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        self.first.wait(timeout=self.ready_s)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+            self.first.set()
+
+    def begin(self):
+        self.t_begin = time.perf_counter()
 
     def stop(self):
+        self.t_end = time.perf_counter()
         if not self.proc:
             return None
+        if self.t_begin is None:
+            self.t_begin = self.t_end
+        # let the line of a sample taken just before the region closed arrive;
+        # a region shorter than the period waits (at most two periods) for the
+        # first sample after it opened
+        time.sleep(self.grace_s)
+        deadline = time.perf_counter() + 2.0 * self.period_s
+        while time.perf_counter() < deadline and not any(t >= self.t_begin for t, _ in list(self.lines)):
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -137,24 +165,34 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        return self.summary()
+
+    @classmethod
+    def parse(cls, line):
+        """(sm MHz, max sm MHz, set of active reasons) of one CSV line, or None."""
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        try:
+            sm, mx = float(parts[1]), float(parts[2])
+        except ValueError:
+            return None
+        active = {nm for nm, v in zip(cls.REASONS, parts[5:9]) if v.lower().startswith("active")}
+        return sm, mx, active
+
+    def summary(self):
+        parsed = [(t, self.parse(ln)) for t, ln in self.lines]
+        parsed = [(t, p) for t, p in parsed if p is not None]
+        inside = [p for t, p in parsed if self.t_begin <= t <= self.t_end + self.grace_s]
+        if not inside:
+            inside = [p for t, p in parsed if t >= self.t_begin][:1]
+        if not inside:
+            return None
+        reasons = set()
+        for p in inside:
+            reasons |= p[2]
+        return {"sm_mhz": statistics.median(p[0] for p in inside), "sm_max_mhz": max(p[1] for p in inside),
+                "reasons": sorted(reasons), "samples": len(inside)}
 
 
 def _workload(n):
@@ -203,10 +241,12 @@ def run_reference(args):
     import oracle
     oracle.build()
     x, grid = _workload(args.n)
-    # each step: a bounded sample sized for ~3 s of oracle work
+    # each step: a bounded sample of oracle work, sized so that the warm-up and
+    # timed steps together take about 90 s (between 0.3 and 3 s per step)
+    per_step = min(3.0, max(0.3, 90.0 / max(1, args.steps + args.warmup)))
     s = 16
     t = _oracle_sample(x, grid, s)
-    s = int(max(16, min(4096, s * 3.0 / max(t, 1e-3))))
+    s = int(max(16, min(4096, s * per_step / max(t, 1e-3))))
     for w in range(args.warmup):
         _oracle_sample(x, grid, s, seed=100 + w)
     times = [_oracle_sample(x, grid, s, seed=200 + k) for k in range(args.steps)]
@@ -310,6 +350,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    clocks.begin()
     times = []
     for _ in range(args.steps):
         flush.zero_()
