@@ -204,34 +204,84 @@ def _workload(n):
 # ----------------------------------------------------------------------------- CPU oracle
 
 
-def _oracle_sample(x, grid, s, seed=0):
-    """The oracle on s sample points: their 8 orthant counts and density, plus
-    s * (grid points / N) grid points' 8 orthant counts.  Returns seconds."""
+def _oracle_sample(x, grid, s, seed=0, keep=False):
+    """The oracle on s sample points: their orthant counts and density, plus
+    s * (grid points / N) random grid points' orthant counts.  Returns the
+    seconds taken, and with ``keep`` also the sample and the oracle's values."""
     import oracle
     from paper_2005_03246_gb300 import datagen
     n = x.shape[0]
+    dim = len(grid)
+    m = [len(a) for a in grid]
     idx = datagen.sample_targets(n, s, seed=seed)
     r = np.random.default_rng(seed)
-    gcount = max(1, int(round(s * (M_AXIS ** D) / n)))
-    gz = np.stack([grid[k][r.integers(0, M_AXIS, size=gcount)] for k in range(D)], axis=1)
+    gcount = max(1, int(round(s * float(np.prod(m)) / n)))
+    gi = np.stack([r.integers(0, m[k], size=gcount) for k in range(dim)], axis=1)
+    gz = np.stack([grid[k][gi[:, k]] for k in range(dim)], axis=1)
     t0 = time.perf_counter()
-    oracle.orthant_sums(x, z=x[idx])
-    oracle.kde_laplace(x, H, z=x[idx])
-    oracle.orthant_sums(x, z=gz)
-    return time.perf_counter() - t0
+    points = oracle.orthant_sums(x, z=x[idx])
+    kde = oracle.kde_laplace(x, H, z=x[idx])
+    gcounts = oracle.orthant_sums(x, z=gz)
+    t = time.perf_counter() - t0
+    if not keep:
+        return t
+    return t, {"idx": idx, "gi": gi, "points": points, "kde": kde, "grid": gcounts}
 
 
-def _cpu_baseline(x, grid, target_s=15.0):
+def _gather(g, p, f, ref):
+    """The step's GPU outputs (grid counts [2^d, M_1..M_d], sample-point counts
+    [2^d, N], densities [N]) at the oracle's sample, as host arrays."""
+    import torch
+    # host-side bounds checks: no index reaches the device unless it is in range
+    dim = ref["gi"].shape[1]
+    if (p.dim() != 2 or f.dim() != 1 or g.dim() != dim + 1 or g.shape[0] != p.shape[0]
+            or int(ref["idx"].max()) >= min(p.shape[1], f.shape[0]) or int(ref["idx"].min()) < 0
+            or any(int(ref["gi"][:, k].max()) >= g.shape[k + 1] for k in range(dim)) or int(ref["gi"].min()) < 0):
+        raise ValueError("outputs of shapes %s, %s, %s do not cover the sample"
+                         % (tuple(g.shape), tuple(p.shape), tuple(f.shape)))
+    idx = torch.as_tensor(ref["idx"], device=p.device)
+    gi = [torch.as_tensor(ref["gi"][:, k], device=g.device) for k in range(dim)]
+    return {"points": p[:, idx].cpu().numpy(), "kde": f[idx.to(f.device)].cpu().numpy(),
+            "grid": g[(slice(None), *gi)].cpu().numpy()}
+
+
+def _accuracy(ref, got, kde_tol=1e-5):
+    """Agreement of the GPU outputs with the oracle on the sample: count
+    mismatches (counts are exact, so any is an error) and the mixed-path KDE's
+    largest relative error on values >= 1e-6 of the sample's largest."""
+    fr = np.asarray(ref["kde"], dtype=np.float64)
+    fg = np.asarray(got["kde"], dtype=np.float64)
+    sel = fr >= 1e-6 * fr.max() if fr.size else np.zeros(0, dtype=bool)
+    rel = float((np.abs(fg[sel] - fr[sel]) / fr[sel]).max()) if sel.any() else 0.0
+    return {"reference": "oracle (brute force, FP64 / exact int64) on the cpu_baseline sample",
+            "sample_points": int(len(ref["idx"])), "grid_points": int(ref["gi"].shape[0]),
+            "points_count_mismatches": int(np.count_nonzero(ref["points"] != got["points"])),
+            "grid_count_mismatches": int(np.count_nonzero(ref["grid"] != got["grid"])),
+            "kde_mixed_max_rel_err": rel, "kde_tolerance": kde_tol}
+
+
+def _cpu_baseline(x, grid, target_s=15.0, gpu_out=None):
+    """The oracle timed on a bounded sample of the workload.  With the step's
+    GPU outputs (g, p, f) it also reports their agreement with the oracle's
+    values on that sample (``accuracy``)."""
     import oracle
     oracle.build()
+    n = x.shape[0]
+    gcount = lambda s: max(1, int(round(s * float(np.prod([len(a) for a in grid])) / n)))
     s = 16
     t = _oracle_sample(x, grid, s)
     s = int(max(16, min(4096, s * target_s / max(t, 1e-3) * 0.8)))
-    t = _oracle_sample(x, grid, s, seed=1)
-    return {"value": s / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "%d of the %d sample points (8 orthant counts + density each, h=%g) and %d "
-                      "random grid points (8 orthant counts each), all against the full N sources; "
-                      "%.1f s" % (s, x.shape[0], H, max(1, int(round(s * M_AXIS ** D / x.shape[0]))), t)}
+    t, ref = _oracle_sample(x, grid, s, seed=1, keep=True)
+    out = {"value": s / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": "%d of the %d sample points (%d orthant counts + density each, h=%g) and %d "
+                     "random grid points (%d orthant counts each), all against the full N sources; "
+                     "%.1f s" % (s, n, 1 << len(grid), H, gcount(s), 1 << len(grid), t)}
+    if gpu_out is not None:
+        try:
+            out["accuracy"] = _accuracy(ref, _gather(*gpu_out, ref))
+        except Exception as e:   # the check must not cost the bench line
+            out["accuracy"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    return out
 
 
 def run_reference(args):
@@ -466,7 +516,15 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = _cpu_baseline(x_np, grid)
+        # one more (untimed) step whose outputs are checked against the
+        # oracle's values on the CPU sample
+        try:
+            outs = step()
+            torch.cuda.synchronize()
+        except Exception:
+            outs = None
+        cpu = _cpu_baseline(x_np, grid, gpu_out=outs)
+        del outs
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
