@@ -21,6 +21,7 @@
  * Orthant selection.  `orthant_mask` is a HOST bitset of ceil(2^d/32) uint32
  *   words (bit o of word o/32 selects orthant o); NULL selects all orthants.
  *   Outputs hold the selected orthants in increasing index, one row each.
+ *   A mask that selects no orthant writes nothing and returns FK_OK.
  * Normalisation.  Orthant outputs are UNNORMALISED sums (Remark 1, Sec. 2.1):
  *   divide by N for F_N.  Counts (y == NULL) are exact int64.
  * Precision.  FK_PATH_MIXED accumulates bulk sums in FP32 with compensated
