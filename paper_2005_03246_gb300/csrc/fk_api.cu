@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fk_dc_ops.cuh"
+#include "fk_nvtx.cuh"
 
 namespace fk {
 fk_status kde_backward_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
@@ -324,6 +325,7 @@ size_t fk_ecdf_grid_workspace(int64_t N, int d, const int64_t* M, int weighted, 
 fk_status fk_ecdf_grid(const void* x, fk_dtype xd, int64_t N, int d, const void* y,
                        const double* z_axes, const int64_t* M, const uint32_t* orthant_mask,
                        void* out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_ecdf_grid");
     cudaStream_t st = (cudaStream_t)stream;
     FK_TRY(grid_validate(x, xd, N, d, M, path));
     if (!z_axes) return set_error(FK_ERR_INVALID_ARG, "z_axes is NULL");
@@ -399,6 +401,7 @@ size_t fk_kde_grid_workspace(int64_t N, int d, const int64_t* M, fk_path path) {
 fk_status fk_kde_grid(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* z_axes,
                       const int64_t* M, const double* h, double* out, fk_path path, void* ws, size_t ws_bytes,
                       fk_stream_t stream) {
+    FK_RANGE("fk_kde_grid");
     cudaStream_t st = (cudaStream_t)stream;
     FK_TRY(grid_validate(x, xd, N, d, M, path));
     FK_TRY(check_h(h, d));
@@ -437,6 +440,7 @@ size_t fk_grid_interp_workspace(void) {
 
 fk_status fk_grid_interp(const double* f, int d, const double* z_axes, const int64_t* M, const void* q,
                          fk_dtype qd, int64_t Q, double* out, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_grid_interp");
     cudaStream_t st = (cudaStream_t)stream;
     if (qd != FK_F32 && qd != FK_F64) return set_error(FK_ERR_INVALID_ARG, "qdtype must be FK_F32 or FK_F64");
     if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "grid_interp supports d in [1, 8]");
@@ -530,11 +534,13 @@ static fk_status ecdf_points_impl(const void* x, fk_dtype xd, int64_t N, int d, 
 fk_status fk_ecdf_points(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
                          const uint32_t* orthant_mask, void* out, fk_path path, void* ws, size_t ws_bytes,
                          fk_stream_t stream) {
+    FK_RANGE("fk_ecdf_points");
     return ecdf_points_impl(x, xd, N, d, y, z, M, orthant_mask, out, path, ws, ws_bytes, stream);
 }
 
 fk_status fk_esf_points(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
                         void* out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_esf_points");
     if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "d out of range");
     uint32_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int o = (1 << d) - 1;
@@ -602,12 +608,14 @@ static fk_status kernel_impl(const void* x, fk_dtype xd, int64_t N, int d, const
 fk_status fk_kde_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                          const double* h, unsigned flags, double* out, double* orthant_terms, fk_path path,
                          void* ws, size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_kde_laplace");
     return kernel_impl(x, xd, N, d, w, z, M, h, flags, 1, out, orthant_terms, path, ws, ws_bytes, stream);
 }
 
 fk_status fk_kreg_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z, int64_t M,
                           const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
                           fk_stream_t stream) {
+    FK_RANGE("fk_kreg_laplace");
     return kernel_impl(x, xd, N, d, y, z, M, h, flags, 2, out, nullptr, path, ws, ws_bytes, stream);
 }
 
@@ -633,6 +641,7 @@ fk_status fk_kde_laplace_backward(const void* x, fk_dtype xd, int64_t N, int d, 
                                   int64_t M, const double* h, unsigned flags, const double* grad_out,
                                   double* grad_w, double* grad_z, double* grad_h, fk_path path, void* ws,
                                   size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_kde_laplace_backward");
     cudaStream_t st = (cudaStream_t)stream;
     FK_TRY(points_validate(x, xd, N, d, z, M, path, false));
     FK_TRY(check_h(h, d));
@@ -684,6 +693,7 @@ size_t fk_loo_laplace_workspace(int64_t N, int d, fk_path path) {
 fk_status fk_loo_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const double* h,
                          double* loglik, double* grad_h, fk_path path, void* ws, size_t ws_bytes,
                          fk_stream_t stream) {
+    FK_RANGE("fk_loo_laplace");
     cudaStream_t st = (cudaStream_t)stream;
     FK_TRY(points_validate(x, xd, N, d, nullptr, 0, path, false));
     FK_TRY(check_h(h, d));
@@ -782,6 +792,7 @@ static void jacobi_eigen(const double* H, int d, double* V, double* ev) {
 }
 
 fk_status fk_hmatrix_factor(const double* H, int d, double* R, double* h) {
+    FK_RANGE("fk_hmatrix_factor");
     if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "d out of range");
     if (!H || !R || !h) return set_error(FK_ERR_INVALID_ARG, "NULL argument");
     double amax = 0.0;
@@ -863,6 +874,7 @@ size_t fk_kde_uniform_workspace(int64_t N, int d, int64_t M, int sample_points, 
 fk_status fk_kde_uniform(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                          const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
                          fk_stream_t stream) {
+    FK_RANGE("fk_kde_uniform");
     return kfam_impl(KF_UNIFORM, x, xd, N, d, w, z, M, h, nullptr, flags, out, path, ws, ws_bytes, stream);
 }
 size_t fk_kde_matern32_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
@@ -871,6 +883,7 @@ size_t fk_kde_matern32_workspace(int64_t N, int d, int64_t M, int sample_points,
 fk_status fk_kde_matern32(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                           const double* h, unsigned flags, double* out, fk_path path, void* ws, size_t ws_bytes,
                           fk_stream_t stream) {
+    FK_RANGE("fk_kde_matern32");
     return kfam_impl(KF_MATERN, x, xd, N, d, w, z, M, h, nullptr, flags, out, path, ws, ws_bytes, stream);
 }
 size_t fk_kde_laplace_hmatrix_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
@@ -879,6 +892,7 @@ size_t fk_kde_laplace_hmatrix_workspace(int64_t N, int d, int64_t M, int sample_
 fk_status fk_kde_laplace_hmatrix(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z,
                                  int64_t M, const double* H, unsigned flags, double* out, fk_path path, void* ws,
                                  size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_kde_laplace_hmatrix");
     return kfam_impl(KF_HMATRIX, x, xd, N, d, w, z, M, nullptr, H, flags, out, path, ws, ws_bytes, stream);
 }
 size_t fk_kreg_loclin_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
@@ -887,6 +901,7 @@ size_t fk_kreg_loclin_laplace_workspace(int64_t N, int d, int64_t M, int sample_
 fk_status fk_kreg_loclin_laplace(const void* x, fk_dtype xd, int64_t N, int d, const void* y, const void* z,
                                  int64_t M, const double* h, unsigned flags, double* out, fk_path path, void* ws,
                                  size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_kreg_loclin_laplace");
     return kfam_impl(KF_LOCLIN, x, xd, N, d, y, z, M, h, nullptr, flags, out, path, ws, ws_bytes, stream);
 }
 
@@ -964,6 +979,7 @@ static fk_status batched_check(const fk_dataset* sets, int count, fk_dtype xd, u
 fk_status fk_batched_ex(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
                         double* kde_out, fk_path path, const fk_batch_config* cfg, void* ws, size_t ws_bytes,
                         fk_stream_t stream) {
+    FK_RANGE("fk_batched_ex");
     cudaStream_t st = (cudaStream_t)stream;
     BatchCfg c;
     FK_TRY(batch_cfg(cfg, c));
@@ -977,6 +993,7 @@ fk_status fk_batched_ex(const fk_dataset* sets, int count, fk_dtype xd, unsigned
 
 fk_status fk_batched(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h, int64_t* ecdf_out,
                      double* kde_out, fk_path path, void* ws, size_t ws_bytes, fk_stream_t stream) {
+    FK_RANGE("fk_batched");
     return fk_batched_ex(sets, count, xd, what, h, ecdf_out, kde_out, path, nullptr, ws, ws_bytes, stream);
 }
 
@@ -1006,6 +1023,7 @@ size_t fk_batched_autotune_workspace(const fk_dataset* sets, int count, fk_dtype
 fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xd, unsigned what, double h,
                               int64_t* ecdf_out, double* kde_out, fk_path path, void* ws, size_t ws_bytes,
                               fk_stream_t stream, fk_batch_config* best, double* best_ms) {
+    FK_RANGE("fk_batched_autotune");
     cudaStream_t st = (cudaStream_t)stream;
     if (!best) return set_error(FK_ERR_INVALID_ARG, "best is NULL");
     FK_TRY(batched_check(sets, count, xd, what, h, ecdf_out, kde_out, path));

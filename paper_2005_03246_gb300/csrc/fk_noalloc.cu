@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "fk_internal.cuh"
+#include "fk_nvtx.cuh"
 
 namespace fk {
 
@@ -55,6 +56,7 @@ extern "C" {
 fk_status fk_ecdf_grid_counts_noalloc(const void* x, fk_dtype xdtype, int64_t N, int d, const double* z_axes,
                                       const int64_t* M, const uint32_t* orthant_mask, int64_t* out,
                                       fk_stream_t stream) {
+    FK_RANGE("fk_ecdf_grid_counts_noalloc");
     cudaStream_t st = (cudaStream_t)stream;
     if (xdtype != FK_F32 && xdtype != FK_F64) return set_error(FK_ERR_INVALID_ARG, "xdtype must be FK_F32 or FK_F64");
     if (d < 1 || d > 8) return set_error(FK_ERR_UNSUPPORTED, "d must be in [1, 8]");
