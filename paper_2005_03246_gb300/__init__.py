@@ -20,6 +20,7 @@ __all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplac
            "kde_grid", "grid_interp", "kde_uniform", "kde_matern32", "kde_laplace_hmatrix", "hmatrix_factor",
            "kreg_loclin",
            "kde_laplace_backward", "loo_laplace", "select_bandwidth_loo",
+           "tune_key", "tune_cache_get", "tune_cache_put",
            "FastEcdfError", "mask_words"]
 
 
@@ -523,6 +524,57 @@ def select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, w=None, path="mixed", per_
 # ----------------------------------------------------------------------------- batching
 
 
+def tune_key(cc, dtype_code, path_code, what, shapes):
+    """Key of a tuned batch configuration: the GPU's compute capability, the
+    dtype, the precision path and the request, and the shape of the batch (the
+    dataset count, the datasets per dimension, and the power-of-two buckets of
+    the total and the largest N).  shapes: iterable of (N_b, d_b)."""
+    shapes = [(int(n), int(d)) for n, d in shapes]
+    per_d = {}
+    for _, d in shapes:
+        per_d[d] = per_d.get(d, 0) + 1
+    ntot = sum(n for n, _ in shapes)
+    nmax = max([n for n, _ in shapes] + [0])
+    return "sm%d%d|dtype%d|path%d|what%d|sets%d|%s|ntot~2^%d|nmax~2^%d" % (
+        int(cc[0]), int(cc[1]), int(dtype_code), int(path_code), int(what), len(shapes),
+        ",".join("d%d:%d" % (d, per_d[d]) for d in sorted(per_d)),
+        int(round(np.log2(max(ntot, 1)))), int(round(np.log2(max(nmax, 1)))))
+
+
+def tune_cache_get(path, key):
+    """The cached entry {"config": {...}, "ms": t} for key, or None.  A missing
+    or unreadable cache file is a miss."""
+    import json
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = cache.get(key) if isinstance(cache, dict) else None
+    if not isinstance(e, dict) or not isinstance(e.get("config"), dict):
+        return None
+    return e
+
+
+def tune_cache_put(path, key, config, ms):
+    """Store a tuned configuration under key (the file is rewritten atomically;
+    other keys are kept, an unreadable file is replaced)."""
+    import json
+    import os
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+        if not isinstance(cache, dict):
+            cache = {}
+    except (OSError, ValueError):
+        cache = {}
+    cache[key] = {"config": {k: int(v) for k, v in dict(config).items()}, "ms": float(ms)}
+    tmp = "%s.tmp%d" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Batched:
     """Many independent datasets in one call (fk_batched): all orthant counts at
     each dataset's sample points and/or its Laplacian KDE (bandwidth h on every
@@ -537,9 +589,15 @@ class Batched:
     config: a dict of fk_batch_config fields (streams, coarsen, kernel_tile,
     count_tile), "tune" to let fk_batched_autotune choose it by measurement on
     these datasets, or None for the default; ``self.config`` holds the one
-    used (and ``self.tune_ms`` the tuned time)."""
+    used (and ``self.tune_ms`` the tuned time).
 
-    def __init__(self, xs, ys=None, h=0.1, ecdf=True, kde=True, path="mixed", graph=True, config=None):
+    tune_cache: with config="tune", the path of a JSON file of tuned
+    configurations keyed by ``tune_key`` (GPU, dtype, path, request and the
+    batch's shape buckets).  A hit skips the tuning (``self.tune_cached`` is
+    True); a miss tunes and stores the result."""
+
+    def __init__(self, xs, ys=None, h=0.1, ecdf=True, kde=True, path="mixed", graph=True, config=None,
+                 tune_cache=None):
         torch = _torch()
         lib = _lib.load()
         if not xs:
@@ -576,7 +634,20 @@ class Batched:
         self.cfg = _lib.BatchConfig()
         lib.fk_batched_config_default(ctypes.byref(self.cfg))
         self.tune_ms = None
-        if config == "tune":
+        self.tune_cached = False
+        cached = None
+        if config == "tune" and tune_cache is not None:
+            key = tune_key(torch.cuda.get_device_capability(dev), self.dtype_code, self.path, self.what,
+                           [tuple(x.shape) for x in self.xs])
+            cached = tune_cache_get(tune_cache, key)
+        if cached is not None:
+            fields = [f for f, _ in _lib.BatchConfig._fields_]
+            for k in fields:
+                if k in cached["config"]:
+                    setattr(self.cfg, k, int(cached["config"][k]))
+            self.tune_ms = float(cached.get("ms", 0.0))
+            self.tune_cached = True
+        elif config == "tune":
             need = lib.fk_batched_autotune_workspace(self.sets, n, self.dtype_code, self.what, self.path)
             tws, twsb = _workspace(need, dev)
             ms = ctypes.c_double(0.0)
@@ -586,6 +657,8 @@ class Batched:
             _lib.check(rc, "fk_batched_autotune")
             self.tune_ms = ms.value
             del tws
+            if tune_cache is not None:
+                tune_cache_put(tune_cache, key, self.cfg.as_dict(), self.tune_ms)
         elif config is not None:
             for k, v in dict(config).items():
                 setattr(self.cfg, k, int(v))

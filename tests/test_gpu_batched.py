@@ -145,3 +145,23 @@ def test_batched_autotune_512_datasets():
         assert np.array_equal(e1[b].cpu().numpy(), e0[b].cpu().numpy()), b
         a, r = k1[b].cpu().numpy(), k0[b].cpu().numpy()
         assert np.max(np.abs(a - r)) <= 2e-5 * np.abs(r).max(), b
+
+
+def test_batched_tune_cache(tmp_path):
+    """A second tuned construction with the same cache file skips the tuning,
+    takes the stored configuration, and gives the same results."""
+    fk = _fk()
+    xs, ys = _sets(24, 9, nmax=4000)
+    xs, ys = [_t(x) for x in xs], [_t(y) for y in ys]
+    path = str(tmp_path / "tune.json")
+    b1 = fk.Batched(xs, ys, h=0.1, graph=False, config="tune", tune_cache=path)
+    b2 = fk.Batched(xs, ys, h=0.1, graph=False, config="tune", tune_cache=path)
+    assert not b1.tune_cached and b2.tune_cached
+    assert b2.config == b1.config and b2.tune_ms == b1.tune_ms
+    e1, k1 = b1.run()
+    e2, k2 = b2.run()
+    for b in range(len(xs)):
+        assert np.array_equal(e1[b].cpu().numpy(), e2[b].cpu().numpy()), b
+        a, r = k1[b].cpu().numpy(), k2[b].cpu().numpy()
+        if r.size:
+            assert np.max(np.abs(a - r)) <= 2e-5 * np.abs(r).max(), b
