@@ -336,6 +336,26 @@ def test_kde_grad_matches_finite_differences():
     np.testing.assert_allclose(gh, _fd(lambda v: L(hh=v), h, 1e-6), rtol=1e-6)
 
 
+def test_kde_grad_w_dot_product_adjoint():
+    """The KDE is linear in w, f = A w, and grad_w is the transposed sum A^T g:
+    <g, A w> = <A^T g, w> for any g and w, and A^T g is the same whatever w
+    it was computed at."""
+    r = np.random.default_rng(21)
+    n, m, d = 80, 30, 3
+    x = r.standard_normal((n, d))
+    z = r.standard_normal((m, d))
+    h = np.array([0.3, 0.6, 0.9])
+    g = r.standard_normal(m)
+    w1, w2 = r.standard_normal(n), r.random(n)
+    gw1 = oracle.kde_grad(x, h, g, w=w1, z=z)[0]
+    gw2 = oracle.kde_grad(x, h, g, w=w2, z=z)[0]
+    np.testing.assert_allclose(gw1, gw2, rtol=1e-13, atol=0)
+    for w in (w1, w2):
+        lhs = float(g @ oracle.kde_laplace(x, h, w=w, z=z))
+        bound = float(np.abs(g) @ oracle.kde_laplace(x, h, w=np.abs(w), z=z))
+        assert abs(lhs - float(gw1 @ w)) <= 1e-12 * bound
+
+
 def test_kde_grad_loo_sample_points():
     r = np.random.default_rng(13)
     x = r.standard_normal((40, 3))
