@@ -67,3 +67,27 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("LOCAL_RANK", "1")
     args = bench._args([])
     assert bench.run_reference(args) == 0
+
+
+def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the base keys,
+    impl "reference", a cpu_baseline describing the run and an e2e with no
+    host-device bytes (a small N keeps this to a second or two)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    assert bench.run_reference(bench._args(["--impl", "reference", "--n", "3000", "--steps", "1",
+                                            "--warmup", "0"])) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["steps"] == 1 and line["value"] > 0
+    assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC and line["higher_is_better"] is True
+    assert line["config"]["workload"] == bench.WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
