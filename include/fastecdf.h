@@ -433,6 +433,10 @@ fk_status fk_batched_autotune(const fk_dataset* sets, int count, fk_dtype xdtype
  * arrays as for fk_ecdf_grid.  The first call on a device does a one-time
  * set-up: it looks up the scratch's device address on that device (make it
  * the current device), so make that first call before any stream capture.
+ * That address is kept for the rest of the process: it does not survive a
+ * reset of the device's primary context (cudaDeviceReset or a release of the
+ * context by another owner), after which this call must not be used.
+ * An orthant selection with no orthant returns FK_OK and writes nothing.
  * Every call uses the same scratch and zeroes the part it accumulates into;
  * calls whose work overlaps on the GPU (concurrent streams, or several host
  * threads on one device) race on it and must be serialised by the caller.

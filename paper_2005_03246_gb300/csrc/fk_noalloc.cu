@@ -64,6 +64,21 @@ fk_status fk_ecdf_grid_counts_noalloc(const void* x, fk_dtype xdtype, int64_t N,
     if (!M) return set_error(FK_ERR_INVALID_ARG, "M is NULL");
     for (int k = 0; k < d; ++k)
         if (M[k] < 1) return set_error(FK_ERR_INVALID_ARG, "M[%d] must be >= 1", k);
+    // Cap the histogram's cell count before any size arithmetic: the histogram
+    // alone takes 4 bytes per cell, so a grid with more cells than the scratch
+    // holds 4-byte entries can never fit.  Checked factor by factor (no
+    // product is formed that could wrap), which also bounds every product the
+    // planner forms below (pass buffers <= 2^7 cells, outputs <= 2^8 cells).
+    const int64_t kMaxCells = (int64_t)(kNoAllocScratchBytes / 4);
+    int64_t cells = 1;
+    for (int k = 0; k < d; ++k) {
+        if (M[k] + 1 > kMaxCells / cells)
+            return set_error(FK_ERR_UNSUPPORTED,
+                             "grid too large: its histogram exceeds the %zu-byte static scratch of "
+                             "fk_ecdf_grid_counts_noalloc",
+                             kNoAllocScratchBytes);
+        cells *= M[k] + 1;
+    }
     if (!z_axes || !out || (N > 0 && !x)) return set_error(FK_ERR_INVALID_ARG, "NULL array argument");
     // Host arrays would need staging buffers, i.e. an allocation.
     if (!is_device_pointer(z_axes) || !is_device_pointer(out) || (N > 0 && !is_device_pointer(x)))

@@ -76,6 +76,14 @@ CASES = [
      UNSUPPORTED, "grid too large"),
     ("noalloc host pointers", lambda: _lib.load().fk_ecdf_grid_counts_noalloc(p(X), 0, N, D, p(Z), p(M), None, p(G),
                                                                                None), INVALID, "device pointers"),
+    # cell counts whose int64 product wraps (65536^4 = 2^64, 512^7 = 2^63): refused before any size arithmetic
+    ("noalloc cells wrap d=4", lambda: _lib.load().fk_ecdf_grid_counts_noalloc(
+        p(X), 0, N, 4, p(Z), p(np.full(4, 65535, dtype=np.int64)), None, p(G), None), UNSUPPORTED, "grid too large"),
+    ("noalloc cells wrap d=7", lambda: _lib.load().fk_ecdf_grid_counts_noalloc(
+        p(X), 0, N, 7, p(Z), p(np.full(7, 511, dtype=np.int64)), None, p(G), None), UNSUPPORTED, "grid too large"),
+    ("noalloc histogram beyond scratch", lambda: _lib.load().fk_ecdf_grid_counts_noalloc(
+        p(X), 0, N, 2, p(Z), p(np.array([2048, 2048], dtype=np.int64)), None, p(G), None), UNSUPPORTED,
+     "grid too large"),
     ("kde_grid h<0", lambda: _lib.load().fk_kde_grid(p(X), 0, N, D, None, p(Z), p(M), p(np.array([0.1, -1.0, 0.1])),
                                                      p(F), 0, None, 0, None), INVALID, "h[1] must be finite and > 0"),
     ("interp d=9", lambda: _lib.load().fk_grid_interp(p(F), 9, p(Z), p(M), p(X), 0, N, p(OUT), None, 0, None),
