@@ -54,9 +54,15 @@
  *   points, which doubles each point into a source and a target copy).
  *   Other values return FK_ERR_UNSUPPORTED.
  * Errors.  Each call returns an fk_status; fk_last_error() gives a thread-local
- *   message.  Nothing is thrown across the ABI.  Non-finite inputs are not
- *   checked on the asynchronous path; they do not fault, and make the outputs
- *   undefined.
+ *   message.  Nothing is thrown across the ABI.  Argument errors the host can
+ *   see are returned at once.  Errors found on the device are recorded in the
+ *   device's error word instead (the call itself stays asynchronous and
+ *   returns FK_OK); fk_device_status() returns and clears the first one.
+ *   Non-finite coordinates: a NaN or +-inf in x, in explicit targets z, or
+ *   in the interpolation points q is detected by the kernel that first reads
+ *   that coordinate (no extra pass over the data) and recorded as
+ *   FK_ERR_NONFINITE; the outputs of that call are undefined, and no memory
+ *   outside the call's buffers is touched.
  */
 #ifndef FASTECDF_H
 #define FASTECDF_H

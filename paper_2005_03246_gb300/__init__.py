@@ -21,7 +21,7 @@ __all__ = ["ecdf_grid", "ecdf_points", "esf_points", "kde_laplace", "kreg_laplac
            "kreg_loclin",
            "kde_laplace_backward", "loo_laplace", "select_bandwidth_loo",
            "tune_key", "tune_cache_get", "tune_cache_put",
-           "FastEcdfError", "mask_words"]
+           "FastEcdfError", "mask_words", "device_status"]
 
 
 def _torch():
@@ -39,6 +39,15 @@ def mask_words(d: int, orthants=None):
             raise ValueError("orthant index %d out of range for d=%d" % (o, d))
         w[o >> 5] |= np.uint32(1 << (o & 31))
     return w
+
+
+def device_status(device=None):
+    """Synchronise the current stream of `device` and raise FastEcdfError if a
+    kernel recorded an error since the last check (for example
+    FK_ERR_NONFINITE: a NaN or infinite coordinate in x or z); clears it."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    _lib.check(_lib.load().fk_device_status(_stream_ptr(dev)), "fk_device_status")
 
 
 def _dtype_code(t):

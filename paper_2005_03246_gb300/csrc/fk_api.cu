@@ -292,7 +292,8 @@ fk_status fk_device_status(fk_stream_t stream) {
     switch (v) {
         case 0: return FK_OK;
         case DEV_TIMEOUT: return set_error(FK_ERR_TIMEOUT, "a bounded device wait ran out");
-        case 3: return set_error(FK_ERR_INVALID_ARG, "grid axis not strictly increasing (device check)");
+        case DEV_AXIS: return set_error(FK_ERR_INVALID_ARG, "grid axis not strictly increasing (device check)");
+        case DEV_NONFINITE: return set_error(FK_ERR_NONFINITE, "non-finite coordinate in x or z (device check)");
         default: return set_error(FK_ERR_CUDA, "device error code %d", v);
     }
 }

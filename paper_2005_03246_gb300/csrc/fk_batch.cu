@@ -71,7 +71,7 @@ __global__ void k_tbase(GroupTab t, int ns) {
 }
 
 template <class T>
-__global__ void k_batch_gather(GroupTab t, int64_t n, int E, int d, int doubled, T* __restrict__ xg) {
+__global__ void k_batch_gather(GroupTab t, int64_t n, int E, int d, int doubled, T* __restrict__ xg, int* err) {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n) return;
     const int64_t s = it >> E, loc = it & (((int64_t)1 << E) - 1);
@@ -82,7 +82,9 @@ __global__ void k_batch_gather(GroupTab t, int64_t n, int E, int d, int doubled,
     const T* xb = (const T*)t.x[s];
     for (int k = 0; k < d; ++k) {
         // padding slots sort after every real point of their segment
-        xg[it * d + k] = (pt >= 0) ? xb[pt * d + k] : (T)__int_as_float(0x7f800000);
+        const T v = (pt >= 0) ? xb[pt * d + k] : (T)__int_as_float(0x7f800000);
+        if (pt >= 0 && !isfinite(v)) note_nonfinite(err);
+        xg[it * d + k] = v;
     }
 }
 
@@ -279,8 +281,10 @@ static fk_status run_group(const fk_dataset* sets, const Grp& g, fk_dtype xd, do
     k_tbase<<<1, 1, 0, st>>>(t, ns);
     FK_LAUNCH_CHECK();
     const unsigned gg = grid_for(n, 256);
-    if (xd == FK_F32) k_batch_gather<float><<<gg, 256, 0, st>>>(t, n, E, d, doubled ? 1 : 0, (float*)xg);
-    else k_batch_gather<double><<<gg, 256, 0, st>>>(t, n, E, d, doubled ? 1 : 0, (double*)xg);
+    int* errw = nullptr;
+    FK_TRY(device_error_word(&errw));
+    if (xd == FK_F32) k_batch_gather<float><<<gg, 256, 0, st>>>(t, n, E, d, doubled ? 1 : 0, (float*)xg, errw);
+    else k_batch_gather<double><<<gg, 256, 0, st>>>(t, n, E, d, doubled ? 1 : 0, (double*)xg, errw);
     FK_LAUNCH_CHECK();
     // positions: sort every axis by (segment, coordinate), sources first on ties
     int segbits = 0;

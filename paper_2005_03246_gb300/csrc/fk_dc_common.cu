@@ -29,17 +29,22 @@ __device__ __forceinline__ T coord_of(const T* x, const T* z, int d, int k, int6
 
 template <class T>
 __global__ void k_make_keys32(const T* __restrict__ x, const T* __restrict__ z, int d, int k, int64_t n_x,
-                              int64_t n, uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+                              int64_t n, uint32_t* __restrict__ key, uint32_t* __restrict__ val, int* err) {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n) return;
-    key[it] = ordered_bits32((float)coord_of(x, z, d, k, n_x, it));
+    const float v = (float)coord_of(x, z, d, k, n_x, it);
+    if (!isfinite(v)) note_nonfinite(err);
+    key[it] = ordered_bits32(v);
     val[it] = (uint32_t)it;
 }
 __global__ void k_make_keys64(const double* __restrict__ x, const double* __restrict__ z, int d, int k,
-                              int64_t n_x, int64_t n, uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+                              int64_t n_x, int64_t n, uint64_t* __restrict__ key, uint32_t* __restrict__ val,
+                              int* err) {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n) return;
-    key[it] = ordered_bits64(coord_of(x, z, d, k, n_x, it));
+    const double v = coord_of(x, z, d, k, n_x, it);
+    if (!isfinite(v)) note_nonfinite(err);
+    key[it] = ordered_bits64(v);
     val[it] = (uint32_t)it;
 }
 
@@ -236,9 +241,11 @@ static fk_status plan_positions(const void* x, const void* z, fk_dtype xd, int64
     if (ar.sizing) return FK_OK;
     if (ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (rank transform)");
     const unsigned g = grid_for(n, 256);
+    int* errw = nullptr;
+    FK_TRY(device_error_word(&errw));
     for (int k = 0; k < d; ++k) {
-        if (k64) k_make_keys64<<<g, 256, 0, st>>>((const double*)x, (const double*)z, d, k, n_x, n, (uint64_t*)key0, val0);
-        else k_make_keys32<float><<<g, 256, 0, st>>>((const float*)x, (const float*)z, d, k, n_x, n, (uint32_t*)key0, val0);
+        if (k64) k_make_keys64<<<g, 256, 0, st>>>((const double*)x, (const double*)z, d, k, n_x, n, (uint64_t*)key0, val0, errw);
+        else k_make_keys32<float><<<g, 256, 0, st>>>((const float*)x, (const float*)z, d, k, n_x, n, (uint32_t*)key0, val0, errw);
         FK_LAUNCH_CHECK();
         bool alt = false;
         if (k64) FK_TRY(radix_sort_pairs_u64((uint64_t*)key0, val0, (uint64_t*)key1, val1, n, 64, tmp, tmpb, st, &alt));

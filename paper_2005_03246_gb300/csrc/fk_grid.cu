@@ -22,12 +22,14 @@ __device__ __forceinline__ double as_double(T v) { return (double)v; }
 
 template <class T>
 __global__ void k_grid_hist_count(const T* __restrict__ x, int64_t n, GridGeom g,
-                                  uint32_t* __restrict__ hist) {
+                                  uint32_t* __restrict__ hist, int* err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t cell = 0;
     for (int k = 0; k < g.d; ++k) {
-        int64_t j = bin_of(as_double(x[i * g.d + k]), g.z[k], g.M[k], g.info[k].uniform, g.info[k].z0, g.info[k].inv_dz);
+        const double v = as_double(x[i * g.d + k]);
+        if (!isfinite(v)) note_nonfinite(err);     // binned in range all the same (bin_of never leaves [0, M])
+        int64_t j = bin_of(v, g.z[k], g.M[k], g.info[k].uniform, g.info[k].z0, g.info[k].inv_dz);
         cell = cell * (g.M[k] + 1) + j;
     }
     atomicAdd(&hist[cell], 1u);
@@ -35,12 +37,14 @@ __global__ void k_grid_hist_count(const T* __restrict__ x, int64_t n, GridGeom g
 
 template <class T>
 __global__ void k_grid_hist_weighted(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
-                                     GridGeom g, double* __restrict__ hist) {
+                                     GridGeom g, double* __restrict__ hist, int* err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t cell = 0;
     for (int k = 0; k < g.d; ++k) {
-        int64_t j = bin_of(as_double(x[i * g.d + k]), g.z[k], g.M[k], g.info[k].uniform, g.info[k].z0, g.info[k].inv_dz);
+        const double v = as_double(x[i * g.d + k]);
+        if (!isfinite(v)) note_nonfinite(err);
+        int64_t j = bin_of(v, g.z[k], g.M[k], g.info[k].uniform, g.info[k].z0, g.info[k].inv_dz);
         cell = cell * (g.M[k] + 1) + j;
     }
     atomicAdd(&hist[cell], as_double(y[i]));
@@ -304,11 +308,11 @@ fk_status grid_run(const void* x, fk_dtype xd, int64_t N, int d, const void* y,
     if (N > 0) {
         ProfScope ps(PF_GRID_HIST, (double)N * (d * (xd == FK_F64 ? 8 : 4) + (weighted ? 16 : 8)), st);
         if (!weighted) {
-            if (xd == FK_F32) k_grid_hist_count<float><<<blocks, 256, 0, st>>>((const float*)x, N, g, (uint32_t*)hist);
-            else k_grid_hist_count<double><<<blocks, 256, 0, st>>>((const double*)x, N, g, (uint32_t*)hist);
+            if (xd == FK_F32) k_grid_hist_count<float><<<blocks, 256, 0, st>>>((const float*)x, N, g, (uint32_t*)hist, err_word);
+            else k_grid_hist_count<double><<<blocks, 256, 0, st>>>((const double*)x, N, g, (uint32_t*)hist, err_word);
         } else {
-            if (xd == FK_F32) k_grid_hist_weighted<float><<<blocks, 256, 0, st>>>((const float*)x, (const float*)y, N, g, (double*)hist);
-            else k_grid_hist_weighted<double><<<blocks, 256, 0, st>>>((const double*)x, (const double*)y, N, g, (double*)hist);
+            if (xd == FK_F32) k_grid_hist_weighted<float><<<blocks, 256, 0, st>>>((const float*)x, (const float*)y, N, g, (double*)hist, err_word);
+            else k_grid_hist_weighted<double><<<blocks, 256, 0, st>>>((const double*)x, (const double*)y, N, g, (double*)hist, err_word);
         }
         FK_LAUNCH_CHECK();
     }

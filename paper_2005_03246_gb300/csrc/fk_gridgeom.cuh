@@ -62,7 +62,7 @@ static __global__ void k_axis_setup(GridGeom g, AxisInfo* __restrict__ info, int
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (bad) atomicCAS(err, 0, 3);
+        if (bad) atomicCAS(err, 0, (int)DEV_AXIS);
         info[k].uniform = (M > 1 && !nonuni && dz > 0.0) ? 1 : 0;
         info[k].z0 = z0;
         info[k].inv_dz = (dz > 0.0) ? 1.0 / dz : 0.0;

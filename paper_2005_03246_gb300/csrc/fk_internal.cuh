@@ -67,7 +67,14 @@ struct ProfScope {
 };
 
 // Device-side error codes recorded in the per-device error word.
-enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
+enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2, DEV_AXIS = 3, DEV_NONFINITE = 4 };
+
+// Records a non-finite input coordinate (NaN or +-inf) in the error word; the
+// first error recorded since the last fk_device_status is kept.  Called by
+// the kernels that first read each coordinate, so no extra pass over x.
+__device__ __forceinline__ void note_nonfinite(int* err) {
+    if (err && *(volatile int*)err == 0) atomicCAS(err, 0, (int)DEV_NONFINITE);
+}
 
 // Concurrent parts of one call (fk_streams.cu): begin() forks up to k-1
 // library-owned streams from `main` (s[0] == main), end() (or the destructor)

@@ -28,7 +28,7 @@ struct HInv { double v[8]; };
 // or e^{-(x - z_{b-1})/h} (bit set, needs b >= 1).
 template <class T, bool F32EXP>
 __global__ void k_kgrid_hist(const T* __restrict__ x, const T* __restrict__ w, int64_t n, GridGeom g, HInv hinv,
-                             int64_t cells, double* __restrict__ hist) {
+                             int64_t cells, double* __restrict__ hist, int* err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int d = g.d;
@@ -36,6 +36,7 @@ __global__ void k_kgrid_hist(const T* __restrict__ x, const T* __restrict__ w, i
     double lo[8], hi[8];      // factors towards the lower / upper line (0 if that line does not exist)
     for (int k = 0; k < d; ++k) {
         const double v = (double)x[i * d + k];
+        if (!isfinite(v)) note_nonfinite(err);
         const int64_t b = bin_of(v, g.z[k], g.M[k], g.info[k].uniform, g.info[k].z0, g.info[k].inv_dz);
         cell = cell * (g.M[k] + 1) + b;
         const double au = (b < g.M[k]) ? (g.z[k][b] - v) * hinv.v[k] : -1.0;        // >= 0 when it exists
@@ -109,7 +110,7 @@ __global__ void k_kgrid_combine(const double* __restrict__ s, int nch, int64_t p
 // [z_0, z_{M-1}] is clamped to the nearest grid line.
 template <class T>
 __global__ void k_grid_interp(const double* __restrict__ f, GridGeom g, const T* __restrict__ q, int64_t nq,
-                              double* __restrict__ out) {
+                              double* __restrict__ out, int* err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nq) return;
     const int d = g.d;
@@ -122,6 +123,7 @@ __global__ void k_grid_interp(const double* __restrict__ f, GridGeom g, const T*
         const double* z = g.z[k];
         const int64_t M = g.M[k];
         double v = (double)q[i * d + k];
+        if (!isfinite(v)) note_nonfinite(err);
         if (!(v >= z[0])) v = z[0];                 // also maps NaN to the first line
         if (v > z[M - 1]) v = z[M - 1];
         if (M == 1) { j0[k] = 0; u[k] = 0.0; continue; }
@@ -187,11 +189,11 @@ fk_status kde_grid_run(const void* x, fk_dtype xd, int64_t N, int d, const void*
         const bool f32 = (path == FK_PATH_MIXED);
         ProfScope ps(PF_GRID_HIST, (double)N * (d * (xd == FK_F64 ? 8 : 4) + (w ? 8 : 0) + nch * 8.0), st);
         if (xd == FK_F32) {
-            if (f32) k_kgrid_hist<float, true><<<blocks, 256, 0, st>>>((const float*)x, (const float*)w, N, g, hinv, cells, b0);
-            else k_kgrid_hist<float, false><<<blocks, 256, 0, st>>>((const float*)x, (const float*)w, N, g, hinv, cells, b0);
+            if (f32) k_kgrid_hist<float, true><<<blocks, 256, 0, st>>>((const float*)x, (const float*)w, N, g, hinv, cells, b0, err_word);
+            else k_kgrid_hist<float, false><<<blocks, 256, 0, st>>>((const float*)x, (const float*)w, N, g, hinv, cells, b0, err_word);
         } else {
-            if (f32) k_kgrid_hist<double, true><<<blocks, 256, 0, st>>>((const double*)x, (const double*)w, N, g, hinv, cells, b0);
-            else k_kgrid_hist<double, false><<<blocks, 256, 0, st>>>((const double*)x, (const double*)w, N, g, hinv, cells, b0);
+            if (f32) k_kgrid_hist<double, true><<<blocks, 256, 0, st>>>((const double*)x, (const double*)w, N, g, hinv, cells, b0, err_word);
+            else k_kgrid_hist<double, false><<<blocks, 256, 0, st>>>((const double*)x, (const double*)w, N, g, hinv, cells, b0, err_word);
         }
         FK_LAUNCH_CHECK();
     }
@@ -232,8 +234,8 @@ fk_status grid_interp_run(const double* f, int d, const double* z_dev, const int
     k_axis_setup<<<d, 256, 0, st>>>(g, info, err_word);
     FK_LAUNCH_CHECK();
     if (nq == 0) return FK_OK;
-    if (qd == FK_F32) k_grid_interp<float><<<grid_for(nq, 256), 256, 0, st>>>(f, g, (const float*)q, nq, out);
-    else k_grid_interp<double><<<grid_for(nq, 256), 256, 0, st>>>(f, g, (const double*)q, nq, out);
+    if (qd == FK_F32) k_grid_interp<float><<<grid_for(nq, 256), 256, 0, st>>>(f, g, (const float*)q, nq, out, err_word);
+    else k_grid_interp<double><<<grid_for(nq, 256), 256, 0, st>>>(f, g, (const double*)q, nq, out, err_word);
     FK_LAUNCH_CHECK();
     return FK_OK;
 }

@@ -94,21 +94,24 @@ def test_backward_matches_finite_differences_of_the_gpu_forward():
         assert abs(fh - gh.cpu().numpy()[k]) <= 1e-4 * abs(fh)
 
 
-def test_autograd_function_matches_backward():
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+def test_autograd_function_matches_backward(path):
+    """torch.autograd through fk.kde: FP64 tensors, so the gradients are held
+    to the adjoint's own tolerance against the oracle."""
     import torch
     fk = _fk()
-    x = _pts(1500, 2, 8)
-    z = _t(_pts(300, 2, 9)).requires_grad_(True)
-    w = _t(np.random.default_rng(1).random(1500).astype(np.float32)).requires_grad_(True)
+    x = _pts(1500, 2, 8).astype(np.float64)
+    z = _t(_pts(300, 2, 9).astype(np.float64)).requires_grad_(True)
+    w = _t(np.random.default_rng(1).random(1500)).requires_grad_(True)
     h = torch.tensor([0.4, 0.7], dtype=torch.float64, requires_grad=True)
-    f = fk.kde(_t(x), h, w=w, z=z, path="fp64")
+    f = fk.kde(_t(x), h, w=w, z=z, path=path)
     loss = (f * torch.linspace(-1, 1, 300, device="cuda:0", dtype=torch.float64)).sum()
     loss.backward()
     g = np.linspace(-1, 1, 300)
     rw, rz, rh = oracle.kde_grad(x, [0.4, 0.7], g, w=w.detach().cpu().numpy(), z=z.detach().cpu().numpy())
-    assert _err(w.grad.double().cpu().numpy(), rw) <= 1e-6
-    assert _err(z.grad.double().cpu().numpy(), rz) <= 1e-6
-    assert _err(h.grad.cpu().numpy(), rh) <= 1e-10
+    assert _err(w.grad.cpu().numpy(), rw) <= TOL[path]
+    assert _err(z.grad.cpu().numpy(), rz) <= TOL[path]
+    assert _err(h.grad.cpu().numpy(), rh) <= TOL[path]
 
 
 @pytest.mark.parametrize("path", ["fp64", "mixed"])
@@ -117,20 +120,27 @@ def test_loo_likelihood_and_gradient(path):
     h = np.array([0.5, 0.45, 0.55, 0.5])
     L, gh = _fk().loo_laplace(_t(x), h, path=path)
     rL, rg = oracle.loo_loglik(x, h)
-    assert abs(float(L.item()) - rL) <= TOL[path] * max(1.0, abs(rL)) * 10
-    assert _err(gh.cpu().numpy(), rg) <= TOL[path] * 10
+    assert abs(float(L.item()) - rL) <= TOL[path] * max(1.0, abs(rL))
+    assert _err(gh.cpu().numpy(), rg) <= TOL[path]
 
 
 def test_bandwidth_selection_steps_match_oracle_gradients():
-    """20 ascent steps on log h from h=0.5 (d=4 copula data): the gradient at
-    every visited h matches the oracle's."""
-    x = datagen.copula_exp4(n=1500)["x"]
+    """20 ascent steps on log h from h=0.5 on a 2e4-point subsample of the d=4
+    copula workload (its first 20000 points): at every visited h the
+    likelihood and its gradient match the oracle's, and the ascent step taken
+    with the oracle's gradient, u <- u + 0.5 sum_k h_k dL/dh_k on u = log h,
+    leads to the next visited h."""
+    x = datagen.copula_exp4()["x"][:20000]
     hist = _fk().select_bandwidth_loo(_t(x), h0=0.5, steps=20, lr=0.5, path="fp64")
     assert len(hist) == 20
-    for h, L, g in hist[::4]:
+    assert np.array_equal(hist[0][0], np.full(4, 0.5))
+    for k, (h, L, g) in enumerate(hist):
         rL, rg = oracle.loo_loglik(x, h)
-        assert abs(L - rL) <= 1e-9 * max(1.0, abs(rL))
-        assert _err(g, rg) <= 1e-9
+        assert abs(L - rL) <= TOL["fp64"] * max(1.0, abs(rL))
+        assert _err(g, rg) <= TOL["fp64"]
+        if k + 1 < len(hist):
+            nxt = np.exp(np.log(h) + 0.5 * float(np.sum(h * rg)))
+            assert np.max(np.abs(nxt - hist[k + 1][0])) <= 1e-12 * np.max(nxt)
     assert hist[-1][1] >= hist[0][1]           # ascent increased the likelihood
 
 

@@ -39,6 +39,19 @@ def _rel_signed(got, ref, absref):
     return np.max(np.abs(got - ref) / np.maximum(absref, 1e-300))
 
 
+def _rel_nw(got, ref, cond):
+    """Nadaraya-Watson error per target, relative to the regression of |y| at
+    that target (the sum of magnitudes of its numerator over its denominator):
+    a ratio of signed kernel sums is only accurate relative to that condition."""
+    return np.max(np.abs(got - ref) / np.maximum(cond, 1e-300))
+
+
+def _c9(got, ref):
+    """|g - o| / max(|o|, 1e-6 max|o|): the signed-output metric applied to
+    every entry, including those near zero."""
+    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max()))
+
+
 def _points(n, d, seed, ties=True, dtype=np.float32):
     r = np.random.default_rng(seed)
     x = r.standard_normal((n, d))
@@ -198,14 +211,38 @@ def test_kde_copula_heavy_tails_no_overflow(h):
 
 
 @pytest.mark.parametrize("path", ["mixed", "fp64"])
-def test_kreg(path):
+@pytest.mark.parametrize("h", [0.05, 0.1, 0.3])
+def test_kreg(path, h):
     d = datagen.copula_t4(n=6000)
     x, y = d["x"], d["y"]
-    h = 0.1
     got = _fk().kreg_laplace(_t(x), _t(y), h, path=path).cpu().numpy()
     ref = oracle.kreg_laplace(x, y, h)
-    # NW is a ratio of two kernel sums; scale the error by the magnitude of y
-    assert np.max(np.abs(got - ref)) <= TOL[path] * 10 * np.abs(y).max()
+    cond = oracle.kreg_laplace(x, np.abs(y), h)
+    assert _rel_nw(got, ref, cond) <= TOL[path]
+    if path == "fp64":
+        assert _c9(got, ref) <= TOL[path]
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_kreg_leave_one_out(path, d):
+    """Leave-one-out NW at the sample points: each target averages y over the
+    other points only (index j dropped, equal-valued duplicates kept)."""
+    r = np.random.default_rng(90 + d)
+    x = r.standard_normal((4000, d))
+    tie = r.random((4000, d)) < 0.2
+    x[tie] = np.round(x[tie] * 4) / 4
+    x = x.astype(np.float32)
+    x[7] = x[11]                                    # an exact duplicate pair
+    y = (np.cos(x.sum(axis=1)) + 0.2 * r.standard_normal(4000)).astype(np.float32)
+    h = np.linspace(0.15, 0.3, d)
+    got = _fk().kreg_laplace(_t(x), _t(y), h, loo=True, path=path).cpu().numpy()
+    ref = oracle.kreg_laplace(x, y, h, loo=True)
+    cond = oracle.kreg_laplace(x, np.abs(y), h, loo=True)
+    assert _rel_nw(got, ref, cond) <= TOL[path]
+    # leave-one-out differs from the estimate that keeps the self pair
+    full = oracle.kreg_laplace(x, y, h)
+    assert np.max(np.abs(ref - full)) > 1e-3
 
 
 @pytest.mark.parametrize("path", ["mixed", "fp64"])
@@ -220,7 +257,8 @@ def test_kreg_explicit_targets(path, d):
     h = np.linspace(0.2, 0.35, d)
     got = _fk().kreg_laplace(_t(x), _t(y), h, z=_t(z), path=path).cpu().numpy()
     ref = oracle.kreg_laplace(x, y, h, z=z)
-    assert np.max(np.abs(got - ref)) <= TOL[path] * 10 * np.abs(y).max()
+    cond = oracle.kreg_laplace(x, np.abs(y), h, z=z)
+    assert _rel_nw(got, ref, cond) <= TOL[path]
 
 
 def test_kde_full_size_d3_sampled():
@@ -253,8 +291,9 @@ def test_kernel_sums_with_zero_weights_and_wide_spread(path):
     y[r.random(n) < 0.4] = 0.0
     gk = _fk().kreg_laplace(_t(x), _t(y), h, path=path).cpu().numpy()
     rk = oracle.kreg_laplace(x, y, h)
+    ck = oracle.kreg_laplace(x, np.abs(y), h)
     ok = np.isfinite(rk)
-    assert np.max(np.abs(gk[ok] - rk[ok])) <= TOL[path] * 10 * np.abs(y).max()
+    assert _rel_nw(gk[ok], rk[ok], ck[ok]) <= TOL[path]
 
 
 @pytest.mark.parametrize("d,n", [(5, 1500), (6, 900), (8, 300)])

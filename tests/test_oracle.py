@@ -307,6 +307,33 @@ def test_kreg_constant_and_ratio():
     assert np.isfinite(far[0])
 
 
+def test_kreg_leave_one_out_hand_worked():
+    """Leave-one-out NW, d=1, x={0,1,3}, y={1,2,4}, h=1, expanded by hand:
+    target j averages y over the two other points with weights e^{-|x_i - x_j|}.
+      j=0: (2 e^-1 + 4 e^-3) / (e^-1 + e^-3) = (2 + 4 e^-2) / (1 + e^-2)
+      j=1: (1 e^-1 + 4 e^-2) / (e^-1 + e^-2) = (1 + 4 e^-1) / (1 + e^-1)
+      j=2: (1 e^-3 + 2 e^-2) / (e^-3 + e^-2) = (e^-1 + 2) / (e^-1 + 1)
+    and, with the self term kept, j=0: (1 + 2 e^-1 + 4 e^-3) / (1 + e^-1 + e^-3)."""
+    e = math.exp
+    x = np.array([[0.0], [1.0], [3.0]])
+    y = np.array([1.0, 2.0, 4.0])
+    loo = oracle.kreg_laplace(x, y, 1.0, loo=True)
+    np.testing.assert_allclose(loo, [(2 + 4 * e(-2)) / (1 + e(-2)), (1 + 4 * e(-1)) / (1 + e(-1)),
+                                     (e(-1) + 2) / (e(-1) + 1)], rtol=1e-15)
+    full = oracle.kreg_laplace(x, y, 1.0)
+    assert full[0] == pytest.approx((1 + 2 * e(-1) + 4 * e(-3)) / (1 + e(-1) + e(-3)), rel=1e-15)
+    # the five tie points of the 2D example, h=(0.5, 1), y = point index:
+    # leave-one-out drops index j only, so the duplicate (1,1) of point 3 stays
+    g = _read_tie_golden()
+    x2 = np.array(g["points"])
+    y2 = np.arange(5.0)
+    w3 = [e(-3), e(-1), e(-2), 1.0]          # weights of points 0, 1, 2, 4 seen from (1,1)
+    m3 = (0 * w3[0] + 1 * w3[1] + 2 * w3[2] + 4 * w3[3]) / sum(w3)
+    assert oracle.kreg_laplace(x2, y2, [0.5, 1.0], loo=True)[3] == pytest.approx(m3, rel=1e-15)
+    # one point: nothing left to average
+    assert np.isnan(oracle.kreg_laplace(np.array([[0.5]]), np.array([3.0]), 1.0, loo=True)[0])
+
+
 # ----------------------------------------------------------------------------- gradients
 
 
