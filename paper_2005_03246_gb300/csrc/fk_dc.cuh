@@ -29,6 +29,9 @@
 // forward and backward scans so that no suffix is ever formed by subtraction.
 #pragma once
 
+#include <climits>
+#include <type_traits>
+
 #include "fk_internal.cuh"
 
 namespace fk {
@@ -570,6 +573,9 @@ struct LocalCfg {
     static constexpr int NT = sizeof(typename Pol::V) * (2 << CLSB) > 128 ? 256 : 512;
     static constexpr int IT = T / NT;                              // items per thread
     static constexpr int TP = T + T / 32;                          // padded rows (bank conflicts)
+    // resident CTAs per SM asked of the compiler: two for the half tile of the
+    // one-channel mixed path (its shared memory allows two; registers decide)
+    static constexpr int kMinBlocks = (FOLD && HALF && CLSB <= 1 && Pol::kNW == 1 && sizeof(typename Pol::M) == 4) ? 2 : 1;
     typedef typename Pol::V V;
     typedef typename Pol::LW LW;
     typedef typename Pol::M M;
@@ -781,8 +787,130 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, false>::NT)
 
 // Folded form (kernel policies without per-orthant terms).  Source weights
 // are rebuilt from the per-item factors when needed instead of being held.
+// ------------------------------------------------------------------ scaled tiles
+// The shifted values of the folded sweep (mantissa and power-of-two shift per
+// value) keep e^{+-x/h} factors in range whatever their spread, at the price
+// of exponent bookkeeping on every addition and product.  Within one tile the
+// factors usually span far less than the FP32 exponent range, so a tile whose
+// factors all lie within 2^{+-kFastL} of a per-tile reference can run the same
+// sweep in plain FP32: each item's factor F(h, dir) of its class c is stored
+// once, scaled by 2^{-R[dir][h][c]}.  A source adds w F(h, dir) 2^{-R} to the
+// running sum of its channel (h, c); a target of the opposite channel
+// (1 - h, ~c) reads that sum with its own factor F(1 - h, 1 - dir), which is
+// stored scaled by 2^{-R[1-dir][1-h][~c]}.  Choosing R[1-dir][1-h][~c] =
+// -R[dir][h][c] makes the two scalings cancel in the product, so the same
+// scaled value serves an item as a source term and as a target factor and
+// the product is the kernel value itself (bounded by the source weight).
+// Bounds: scaled factors lie in [2^{-kFastL-2}, 2^{kFastL+2}] (mantissas of up
+// to four factors carry up to 2^{+-2}); with nonzero weights in
+// [2^{kFastWmin}, 2^{kFastWmax+1}) and at most 2^12 terms per sum, every term
+// and partial sum stays a normal FP32 number.  A tile outside these bounds
+// keeps the shifted arithmetic.
+constexpr int kFastL = 96, kFastWmax = 14, kFastWmin = -26;
+
+template <int NW>
+struct FastLO {
+    struct V { float v[NW]; };
+    __device__ static V zero() {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = 0.f;
+        return r;
+    }
+    __device__ static V add(V a, V b) {
+        V r;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r.v[i] = a.v[i] + b.v[i];
+        return r;
+    }
+};
+
+// Per-tile references of the scaled form.  Returns (uniformly over the CTA)
+// whether the tile qualifies; if so, s_fm[4 i + 2 h + dir] has been replaced
+// by F(h, dir) 2^{-R[dir][h][c]} (c = the item's class) and s_ref[(2 h + dir)
+// * NCLS + c] holds R.  s_fs (the shifts) is left as it was.
+template <int CLSB, int NT>
+__device__ __forceinline__ bool fold_fast_setup(const uint32_t* s_meta, float* s_fm, const int* s_fs,
+                                                const float* s_wt, int ln, int* s_ref) {
+    constexpr int NCLS = 1 << CLSB, NS = 4 * NCLS;
+    __shared__ int s_lo[NS], s_hi[NS], s_wr[2], s_ok;
+    for (int i = threadIdx.x; i < NS; i += NT) { s_lo[i] = INT_MAX; s_hi[i] = INT_MIN; }
+    if (threadIdx.x == 0) { s_wr[0] = INT_MAX; s_wr[1] = INT_MIN; }
+    __syncthreads();
+    int lo[NS], hi[NS], wlo = INT_MAX, whi = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) { lo[q] = INT_MAX; hi[q] = INT_MIN; }
+    for (int i = threadIdx.x; i < ln; i += NT) {
+        const int c = (int)(s_meta[lpd(i)] >> kItemBits);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = s_fs[4 * i + j];
+#pragma unroll
+            for (int cc = 0; cc < NCLS; ++cc) {
+                if (c == cc) { lo[j * NCLS + cc] = min(lo[j * NCLS + cc], e); hi[j * NCLS + cc] = max(hi[j * NCLS + cc], e); }
+            }
+        }
+        const float w = s_wt[i];
+        if (w != 0.f) {
+            const int ew = (int)((__float_as_uint(w) >> 23) & 0xffu) - 127;   // -127: subnormal
+            wlo = min(wlo, ew);
+            whi = max(whi, ew);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        lo[q] = __reduce_min_sync(0xffffffffu, lo[q]);
+        hi[q] = __reduce_max_sync(0xffffffffu, hi[q]);
+    }
+    wlo = __reduce_min_sync(0xffffffffu, wlo);
+    whi = __reduce_max_sync(0xffffffffu, whi);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            if (lo[q] != INT_MAX) { atomicMin(&s_lo[q], lo[q]); atomicMax(&s_hi[q], hi[q]); }
+        }
+        if (wlo != INT_MAX) { atomicMin(&s_wr[0], wlo); atomicMax(&s_wr[1], whi); }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = (s_wr[0] == INT_MAX) || (s_wr[0] >= kFastWmin && s_wr[1] <= kFastWmax);
+        // free references R[+][h][c]; R[-][1-h][~c] = -R[+][h][c]
+        for (int h = 0; h < 2; ++h)
+            for (int c = 0; c < NCLS; ++c) {
+                const int q1 = (2 * h + 0) * NCLS + c;                        // slot (dir +, h, c)
+                const int q2 = (2 * (1 - h) + 1) * NCLS + ((~c) & (NCLS - 1)); // slot (dir -, 1-h, ~c)
+                long long a = -(1ll << 40), b = (1ll << 40);
+                if (s_lo[q1] != INT_MAX) {
+                    a = max(a, (long long)s_hi[q1] - kFastL);
+                    b = min(b, (long long)s_lo[q1] + kFastL);
+                }
+                if (s_lo[q2] != INT_MAX) {
+                    a = max(a, -(long long)s_lo[q2] - kFastL);
+                    b = min(b, (long long)kFastL - (long long)s_hi[q2]);
+                }
+                long long r = 0;
+                if (a > b) ok = false;
+                else if (a > -(1ll << 40) && b < (1ll << 40)) r = (a + b) / 2;
+                else if (a > -(1ll << 40)) r = a;
+                else if (b < (1ll << 40)) r = b;
+                s_ref[q1] = (int)r;
+                s_ref[q2] = (int)(-r);
+            }
+        s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    for (int i = threadIdx.x; i < ln; i += NT) {
+        const int c = (int)(s_meta[lpd(i)] >> kItemBits);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s_fm[4 * i + j] *= pow2f_any(s_fs[4 * i + j] - s_ref[j * NCLS + c]);
+    }
+    __syncthreads();
+    return true;
+}
+
 template <class Pol, int CLSB, bool HALF>
-__global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
+__global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT, (LocalCfg<Pol, CLSB, true, HALF>::kMinBlocks))
     k_local_fold(const uint32_t* __restrict__ seq, int64_t n, const uint32_t* __restrict__ P0, ClassSpecK cs,
                  int levels, Pol pol, uint32_t* __restrict__ key_out, uint32_t* __restrict__ meta_out,
                  int write_out, int rec_out, FoldRecs<Pol> rout) {
@@ -824,88 +952,125 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
         for (int q = 0; q < NW; ++q) s_fa[NW * i + q] = Pol::fa_zero();
     }
     __syncthreads();
-    for (int m = 0; m < levels; ++m) {
-        const int R2 = 2 << m;
-        uint32_t ek[IT], em[IT], eh[IT];
-        const int cnt = local_merge<IT>(s_key, s_meta, s_home, ln, 1 << m, ek, em, eh);
-        // factors F(h, +) (index 0) and F(h, -) (index 1) of each element
-        M f0[IT], f1[IT], wt[IT];
-        int g0[IT], g1[IT];
+    // Scaled FP32 form when the tile's factors allow it (mixed path only).
+    __shared__ int s_ref[4 << CLSB];
+    bool fast = false;
+    if constexpr (Pol::kFastLocal) fast = fold_fast_setup<CLSB, NT>(s_meta, s_fm, s_fs, s_wt, ln, s_ref);
+    auto run_levels = [&](auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        typedef typename std::conditional<FAST, FastLO<NW>, LO>::type LX;
+        typedef typename LX::V VX;
+        // kernel value of a running sum v read with factor (m, s), per weight channel
+        auto value = [&](const VX& v, M mm, int sh, M* c) {
+            if constexpr (FAST) {
 #pragma unroll
-        for (int e = 0; e < IT; ++e) {
-            f0[e] = f1[e] = wt[e] = (M)0;
-            g0[e] = g1[e] = 0;
-            if (e < cnt) {
-                const int b = 4 * (int)(eh[e] & 0xffffu) + 2 * (int)(eh[e] >> 16);
-                f0[e] = s_fm[b];
-                f1[e] = s_fm[b + 1];
-                g0[e] = s_fs[b];
-                g1[e] = s_fs[b + 1];
-                wt[e] = s_wt[eh[e] & 0xffffu];
+                for (int q = 0; q < NW; ++q) c[q] = v.v[q] * mm;
+            } else {
+                Pol::fold_value(v, mm, sh, c);
             }
-        }
-        const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
-        const int p0 = threadIdx.x * IT;
-        // Walks from zero over the thread's elements (a thread's elements lie
-        // in one merged block when ts > 1): kernel values of the thread-local
-        // prefix (forward, with F(h, -) of the target) and suffix (backward,
-        // F(h, +)); the walks end with the thread's channel totals.
-        M cf[IT][NW], cb[IT][NW];
-        V fe[NCH], be[NCH];
+        };
+        // source term of an element (weight channel 1 of two-channel sums: 1 for sources)
+        auto term = [&](M mm, int sh, M w, bool src) -> VX {
+            if constexpr (FAST) {
+                VX r;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) { fe[c] = LO::zero(); be[c] = LO::zero(); }
-#pragma unroll
-        for (int e = 0; e < IT; ++e) {
-#pragma unroll
-            for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
-            if (e < cnt) {
-                if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) fe[c] = LO::zero();
-                }
-                const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
-                Pol::fold_value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
-                add_at<LO>(fe, own, Pol::fold_src(f0[e], g0[e], wt[e], pol.is_src(em[e] & kItemMask)));
+                for (int q = 0; q < NW; ++q) r.v[q] = ((NW == 2 && q == 1) ? (src ? (M)1 : (M)0) : w) * mm;
+                return r;
+            } else {
+                return Pol::fold_src(mm, sh, w, src);
             }
-        }
-#pragma unroll
-        for (int e = IT - 1; e >= 0; --e) {
-#pragma unroll
-            for (int q = 0; q < NW; ++q) cb[e][q] = (M)0;
-            if (e < cnt) {
-                if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) be[c] = LO::zero();
-                }
-                const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
-                Pol::fold_value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
-                add_at<LO>(be, own, Pol::fold_src(f1[e], g1[e], wt[e], pol.is_src(em[e] & kItemMask)));
-            }
-        }
-        // blocks spanning several threads: the exclusive prefix / suffix of
-        // the thread totals joins every element (the fold is linear)
-        if (ts > 1) {
-            seg_scan<LO, NCH, NT>(fe, be, ts, s_scan);
+        };
+        for (int m = 0; m < levels; ++m) {
+            const int R2 = 2 << m;
+            uint32_t ek[IT], em[IT], eh[IT];
+            const int cnt = local_merge<IT>(s_key, s_meta, s_home, ln, 1 << m, ek, em, eh);
+            // factors F(h, +) (index 0) and F(h, -) (index 1) of each element
+            M f0[IT], f1[IT], wt[IT];
+            int g0[IT], g1[IT];
 #pragma unroll
             for (int e = 0; e < IT; ++e) {
+                f0[e] = f1[e] = wt[e] = (M)0;
+                g0[e] = g1[e] = 0;
                 if (e < cnt) {
-                    const int opp = ((int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits)) ^ (NCH - 1);
-                    M xf[NW], xb[NW];
-                    Pol::fold_value(pick(fe, opp), f1[e], g1[e], xf);
-                    Pol::fold_value(pick(be, opp), f0[e], g0[e], xb);
-#pragma unroll
-                    for (int q = 0; q < NW; ++q) { cf[e][q] += xf[q]; cb[e][q] += xb[q]; }
+                    const int b = 4 * (int)(eh[e] & 0xffffu) + 2 * (int)(eh[e] >> 16);
+                    f0[e] = s_fm[b];
+                    f1[e] = s_fm[b + 1];
+                    if constexpr (!FAST) {
+                        g0[e] = s_fs[b];
+                        g1[e] = s_fs[b + 1];
+                    }
+                    wt[e] = s_wt[eh[e] & 0xffffu];
                 }
             }
-        }
+            const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
+            const int p0 = threadIdx.x * IT;
+            // Walks from zero over the thread's elements (a thread's elements lie
+            // in one merged block when ts > 1): kernel values of the thread-local
+            // prefix (forward, with F(h, -) of the target) and suffix (backward,
+            // F(h, +)); the walks end with the thread's channel totals.
+            M cf[IT][NW], cb[IT][NW];
+            VX fe[NCH], be[NCH];
 #pragma unroll
-        for (int e = 0; e < IT; ++e)
-            if (e < cnt && pol.is_tgt(em[e] & kItemMask)) {
-                M sf, sb;
-                pol.signs((int)(eh[e] >> 16), em[e] >> kItemBits, sf, sb);
-                Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e], sf, sb);
+            for (int c = 0; c < NCH; ++c) { fe[c] = LX::zero(); be[c] = LX::zero(); }
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+#pragma unroll
+                for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
+                if (e < cnt) {
+                    if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) fe[c] = LX::zero();
+                    }
+                    const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                    value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
+                    add_at<LX>(fe, own, term(f0[e], g0[e], wt[e], pol.is_src(em[e] & kItemMask)));
+                }
             }
-        local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
+#pragma unroll
+            for (int e = IT - 1; e >= 0; --e) {
+#pragma unroll
+                for (int q = 0; q < NW; ++q) cb[e][q] = (M)0;
+                if (e < cnt) {
+                    if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) be[c] = LX::zero();
+                    }
+                    const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                    value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
+                    add_at<LX>(be, own, term(f1[e], g1[e], wt[e], pol.is_src(em[e] & kItemMask)));
+                }
+            }
+            // blocks spanning several threads: the exclusive prefix / suffix of
+            // the thread totals joins every element (the fold is linear)
+            if (ts > 1) {
+                seg_scan<LX, NCH, NT>(fe, be, ts, reinterpret_cast<VX*>(s_scan));
+#pragma unroll
+                for (int e = 0; e < IT; ++e) {
+                    if (e < cnt) {
+                        const int opp = ((int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits)) ^ (NCH - 1);
+                        M xf[NW], xb[NW];
+                        value(pick(fe, opp), f1[e], g1[e], xf);
+                        value(pick(be, opp), f0[e], g0[e], xb);
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) { cf[e][q] += xf[q]; cb[e][q] += xb[q]; }
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < IT; ++e)
+                if (e < cnt && pol.is_tgt(em[e] & kItemMask)) {
+                    M sf, sb;
+                    pol.signs((int)(eh[e] >> 16), em[e] >> kItemBits, sf, sb);
+                    Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e], sf, sb);
+                }
+            local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
+        }
+    };
+    if constexpr (Pol::kFastLocal) {
+        if (fast) run_levels(std::true_type{});
+        else run_levels(std::false_type{});
+    } else {
+        run_levels(std::false_type{});
     }
     // write the tile out for the longer merge levels (as records when they
     // run on records); targets not handed on as records are flushed
@@ -919,9 +1084,14 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT)
             meta_out[d] = m;
         }
         if (rec_out) {
+            const int c = (int)(m >> kItemBits);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                rout.fm[4 * d + j] = s_fm[4 * h + j];
+                M fm = s_fm[4 * h + j];
+                if constexpr (Pol::kFastLocal) {
+                    if (fast) fm *= pow2f_any(s_ref[j * (1 << CLSB) + c] - s_fs[4 * h + j]);   // exact: a power of two
+                }
+                rout.fm[4 * d + j] = fm;
                 rout.fs[4 * d + j] = s_fs[4 * h + j];
             }
             rout.wt[d] = s_wt[h];

@@ -227,6 +227,7 @@ struct PolKF : ItemMap {
     static constexpr bool kCanFold = true;
     static constexpr int kFoldT = NW == 1 ? 4096 : 2048, kNW = NW;
     static constexpr bool kRecords = true;    // longer levels on streamed records
+    static constexpr bool kFastLocal = true;  // tile-local levels may run on scaled FP32 values
     typedef float M;
     typedef FF FA;
     // Tile-local running sums and scans: plain FP32 mantissa with a shift.
@@ -447,6 +448,7 @@ struct PolKD : ItemMap {
     // folded local form (targets turn their sums into kernel values)
     static constexpr bool kCanFold = true;
     static constexpr int kFoldT = NW == 1 ? 2048 : 1024, kNW = NW;
+    static constexpr bool kFastLocal = false;
     // longer levels gather the factors per item (measured faster on the FP64
     // path, whose cost is FP64 arithmetic rather than memory latency)
     static constexpr bool kRecords = false;

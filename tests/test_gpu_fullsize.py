@@ -71,7 +71,7 @@ def test_c3_kde_and_regression_at_sampled_points(c3, h):
         assert _rel_kde(f[idx], ref_f) <= TOL[path], (path, h)
         m = fk.kreg_laplace(_t(x), _t(y), h, path=path).cpu().numpy()
         # a ratio of signed kernel sums: error relative to the regression of |y|
-        err = np.abs(m[idx] - ref_m) / np.maximum(cond_m, 1e-300)
+        err = np.abs(m[idx] - ref_m) / np.maximum(cond_m, 1e-6 * np.abs(ref_m).max())
         assert np.max(err) <= TOL[path], (path, h)
 
 
@@ -177,7 +177,7 @@ def test_c5_likelihood_gradient_full_size(c5):
 def test_c5_bandwidth_steps_mixed_follow_fp64(c5):
     """Two ascent steps on log h at full size: the mixed path follows the FP64
     path (h, L and dL/dh per step)."""
-    x, _ = c5
+    x, idx = c5
     fk = _fk()
     hm = fk.select_bandwidth_loo(_t(x), h0=0.5, steps=2, lr=0.5, path="mixed")
     hd = fk.select_bandwidth_loo(_t(x), h0=0.5, steps=2, lr=0.5, path="fp64")
