@@ -67,6 +67,8 @@ def _args(argv=None):
     ap.add_argument("--scaling", action="store_true",
                     help="time the sample-point counts, the KDE and the grid counts over d and N (the "
                          "paper's runtime-versus-N study) and print one JSON line")
+    ap.add_argument("--no-c5", action="store_true", help="skip the d=4, N=4e6 leave-one-out workload")
+    ap.add_argument("--no-c5-search", action="store_true", help="skip its 20-step bandwidth search")
     ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
                     help="run one operation per step (profiling of a single kernel family)")
     return ap.parse_args(argv)
@@ -80,12 +82,28 @@ def _dist():
 
 
 # Families whose work is counted in floating-point operations (the tile-local
-# kernel-sum sweep is bound by instruction issue, not by HBM), and the FP32
-# peak they are held against: 152 SMs x 128 FP32 lanes x 2.07 GHz, one
-# non-fused operation per lane and clock.
+# kernel-sum sweep is bound by instruction issue, not by HBM); they are held
+# against the FP32 lane peak: SMs (read from the device) x 128 FP32 lanes x
+# the maximum SM clock (the sampled clocks.max.sm, else the measured-peaks
+# file, else 2070 MHz), one non-fused operation per lane and clock.
 ALU_FAMILIES = ("kernel_local",)
-FP32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 1e12
-FP32_PEAK_SOURCE = "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"
+
+
+def fp32_peak(sms, max_mhz, clock_source):
+    """(TFLOP/s, description) of the FP32 lane peak."""
+    return (sms * 128 * max_mhz * 1e6 / 1e12,
+            "derived: %d SMs (device properties) x 128 FP32 lanes x %.0f MHz max SM clock (%s)"
+            % (sms, max_mhz, clock_source))
+
+
+def _max_sm_mhz(clk):
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"]), "nvidia-smi clocks.max.sm"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json"
+    except Exception:
+        return 2070.0, "nominal"
 
 
 def _peaks():
@@ -260,10 +278,91 @@ def _accuracy(ref, got, kde_tol=1e-5):
             "kde_mixed_max_rel_err": rel, "kde_tolerance": kde_tol}
 
 
-def _cpu_baseline(x, grid, target_s=15.0, gpu_out=None):
+def _rel_pos(got, ref):
+    """Largest relative error on entries >= 1e-6 of the largest reference."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    sel = np.abs(ref) >= 1e-6 * np.abs(ref).max() if ref.size else np.zeros(0, dtype=bool)
+    return float((np.abs(got[sel] - ref[sel]) / np.abs(ref[sel])).max()) if sel.any() else 0.0
+
+
+def _rel_cond(got, ref, cond):
+    """Error of signed results relative to their condition (the same quantity
+    computed from magnitudes), with the scale floored at 1e-6 of the largest
+    reference value."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.maximum(np.abs(np.asarray(cond, dtype=np.float64)), 1e-6 * np.abs(ref).max())
+    return float((np.abs(got - ref) / scale).max()) if ref.size else 0.0
+
+
+def _c9(got, ref):
+    """|g - o| / max(|o|, 1e-6 max|o|) over every entry."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float((np.abs(got - ref) / np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())).max()) if ref.size else 0.0
+
+
+def _accuracy_extras(samples, x_step):
+    """The oracle's error for every other result the bench times: the batched
+    outputs, the adjoint, the d=2 copula KDE / Nadaraya-Watson / adjoint, the
+    weighted d=3 sums and the d=4 leave-one-out densities."""
+    import oracle
+    acc = {}
+    if "batched_mixed" in samples:
+        for path in ("mixed", "fp64"):
+            cm, ke, kc = 0, 0.0, 0.0
+            for xb, yb, e, k in samples["batched_" + path]:
+                cm += int(np.count_nonzero(oracle.orthant_sums(xb) != e))
+                ref = oracle.kde_laplace(xb, H, w=yb)
+                cond = oracle.kde_laplace(xb, H, w=np.abs(yb))
+                ke = max(ke, _rel_cond(k, ref, cond))
+                kc = max(kc, _c9(k, ref))
+            acc["batched_" + path] = {"datasets_checked": len(samples["batched_" + path]),
+                                      "count_mismatches": cm, "kde_err_rel_to_abs_weights": ke, "kde_c9": kc}
+    if "backward_d3" in samples:
+        b = samples["backward_d3"]
+        ref = oracle.kde_laplace(x_step, H, z=x_step[b["idx"]])
+        acc["kde_backward_d3_grad_w"] = {"targets": len(b["idx"]), "max_rel_err": _rel_pos(b["grad_w"], ref)}
+    if "c3" in samples:
+        c = samples["c3"]
+        xs, ys, idx = c["x"], c["y"], c["idx"]
+        z = xs[idx]
+        rows = {}
+        for (h, path), (f, m) in c["values"].items():
+            rf = oracle.kde_laplace(xs, h, z=z)
+            rm = oracle.kreg_laplace(xs, ys, h, z=z)
+            cm = oracle.kreg_laplace(xs, np.abs(ys), h, z=z)
+            rows["h%g_%s" % (h, path)] = {"kde_max_rel_err": _rel_pos(f, rf), "nw_err_rel_to_abs_y": _rel_cond(m, rm, cm),
+                                          "nw_c9": _c9(m, rm)}
+        a = c["adjoint"]
+        rw, rz, rh = oracle.kde_grad(xs, a["h"], a["g"], z=a["z"])
+        for path in ("mixed", "fp64"):
+            sw, gw, gz, gh = a[path]
+            rows["adjoint_%s" % path] = {
+                "grad_w_err_rel_max": float(np.abs(gw - rw[sw]).max() / np.abs(rw).max()),
+                "grad_z_err_rel_max": float(np.abs(gz - rz).max() / np.abs(rz).max()),
+                "grad_h_err_rel_max": float(np.abs(gh - rh).max() / np.abs(rh).max())}
+        rows["targets"] = len(idx)
+        acc["c3_copula_d2"] = rows
+    if "c2w" in samples:
+        c = samples["c2w"]
+        ref = oracle.orthant_sums(x_step, y=c["y"], z=x_step[c["idx"]])
+        acc["c2_weighted_d3"] = {"targets": len(c["idx"]), **{
+            "%s_max_rel_err" % path: _rel_pos(c[path], ref) for path in ("mixed", "fp64")}}
+    if "c5" in samples:
+        c = samples["c5"]
+        ref = oracle.kde_at_points(c["x"], c["h"], c["idx"], loo=True)
+        acc["c5_loo_d4"] = {"targets": len(c["idx"]), **{
+            "%s_loo_density_max_rel_err" % path: _rel_pos(c[path], ref) for path in ("mixed", "fp64")}}
+    return acc
+
+
+def _cpu_baseline(x, grid, target_s=15.0, gpu_out=None, extra_samples=None):
     """The oracle timed on a bounded sample of the workload.  With the step's
-    GPU outputs (g, p, f) it also reports their agreement with the oracle's
-    values on that sample (``accuracy``)."""
+    GPU outputs (g, p, f, f64) it also reports their agreement with the
+    oracle's values on that sample (``accuracy``), and with the samples of the
+    other workloads their errors too."""
     import oracle
     oracle.build()
     n = x.shape[0]
@@ -278,9 +377,16 @@ def _cpu_baseline(x, grid, target_s=15.0, gpu_out=None):
                      "%.1f s" % (s, n, 1 << len(grid), H, gcount(s), 1 << len(grid), t)}
     if gpu_out is not None:
         try:
-            out["accuracy"] = _accuracy(ref, _gather(*gpu_out, ref))
+            g, p, f, f64 = gpu_out
+            out["accuracy"] = _accuracy(ref, _gather(g, p, f, ref))
+            out["accuracy"]["kde_fp64_max_rel_err"] = _rel_pos(_gather(g, p, f64, ref)["kde"], ref["kde"])
         except Exception as e:   # the check must not cost the bench line
             out["accuracy"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if extra_samples:
+        try:
+            out.setdefault("accuracy", {})["other_workloads"] = _accuracy_extras(extra_samples, x)
+        except Exception as e:
+            out.setdefault("accuracy", {})["other_workloads"] = {"error": "%s: %s" % (type(e).__name__, e)}
     return out
 
 
@@ -363,20 +469,20 @@ def run_ours(args):
     # statistics back once.
     side = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
 
-    def step():
+    def step(kde_path="mixed"):
         if args.only:
             return only[args.only]()
         if args.serial:
             g = fk.ecdf_grid(x, grid)
             p = fk.ecdf_points(x)
-            f = fk.kde_laplace(x, H, path="mixed")
+            f = fk.kde_laplace(x, H, path=kde_path)
             return g, p, f
         fork = torch.cuda.Event()
         fork.record(stream)
         for s in side:
             s.wait_event(fork)
         with torch.cuda.stream(side[0]):
-            f = fk.kde_laplace(x, H, path="mixed")
+            f = fk.kde_laplace(x, H, path=kde_path)
         with torch.cuda.stream(side[1]):
             g = fk.ecdf_grid(x, grid)
         p = fk.ecdf_points(x)
@@ -432,6 +538,8 @@ def run_ours(args):
             fams[name] = (tot.value, cnt.value, by.value, busy.value)
     lib.fk_profile_reset()
     peak, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE = fp32_peak(sms, *_max_sm_mhz(clk))
     dom = max(fams.items(), key=lambda kv: kv[1][3]) if fams else None
     roofline = None
     if dom:
@@ -501,10 +609,64 @@ def run_ours(args):
     fp64 = {"kde_fp64_ms": kde64, "kde_mixed_ms": split["kde_mixed_ms"],
             "mixed_speedup": kde64 / split["kde_mixed_ms"]}
 
+    # ---- roofline of each call: the algorithmic bytes of all its profiled
+    # passes (each pass reading its inputs once and writing its outputs once,
+    # as the library records them) over the call's own time
+    def call_bytes(fn):
+        lib.fk_profile_reset()
+        lib.fk_profile_enable(1)
+        r = fn()
+        torch.cuda.synchronize()
+        lib.fk_profile_enable(0)
+        tot = 0.0
+        for fid in _lib.PROFILE_FAMILIES.values():
+            b = ctypes.c_double(0)
+            lib.fk_profile_read_bytes(fid, ctypes.byref(b))
+            tot += b.value
+        lib.fk_profile_reset()
+        del r
+        return tot
+
+    per_call = {}
+    for key, fn, ms in (("ecdf_points", lambda: fk.ecdf_points(x), split["ecdf_points_ms"]),
+                        ("kde_laplace_mixed", lambda: fk.kde_laplace(x, H, path="mixed"), split["kde_mixed_ms"]),
+                        ("kde_laplace_fp64", lambda: fk.kde_laplace(x, H, path="fp64"), kde64),
+                        ("ecdf_grid", lambda: fk.ecdf_grid(x, grid), split["ecdf_grid_ms"])):
+        b = call_bytes(fn)
+        a = b / (ms / 1e3) / 1e9
+        per_call[key] = {"alg_bytes": b, "ms": ms, "achieved": a, "unit": "GB/s", "peak": peak,
+                         "peak_source": peak_kind, "frac": a / peak}
+
+    # ---- the same step with the KDE on the all-FP64 path (the paper's precision)
+    fp64_step = None
+    if not args.only:
+        def step64():
+            return step(kde_path="fp64")
+        for _ in range(2):
+            r = step64()
+        del r
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = step64()
+            b.record(stream)
+            b.synchronize()
+            t64.append(a.elapsed_time(b))
+            del r
+        ms64 = float(sum(t64)) / len(t64)
+        ms64, v64 = aggregate_replicas(ms64 * len(t64), len(t64), n, ws, dev)
+        fp64_step = {"ms_per_step": ms64, "value": v64, "unit": UNIT, "steps": len(t64),
+                     "dtype": "u32/i64 counts; f64 KDE", "mixed_over_fp64": value / v64}
+
     # ---- other hot-path rows on their own workloads (reported beside the step)
     extras = {}
+    samples = {}
     if not args.no_extras:
-        extras = _extras(fk, torch, dev, x, stream, flush, timed)
+        extras, samples = _extras(fk, torch, dev, x, stream, flush, timed, args)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -519,11 +681,11 @@ def run_ours(args):
         # one more (untimed) step whose outputs are checked against the
         # oracle's values on the CPU sample
         try:
-            outs = step()
+            outs = tuple(step()) + (fk.kde_laplace(x, H, path="fp64"),)
             torch.cuda.synchronize()
         except Exception:
             outs = None
-        cpu = _cpu_baseline(x_np, grid, gpu_out=outs)
+        cpu = _cpu_baseline(x_np, grid, gpu_out=outs, extra_samples=samples)
         del outs
 
     if rank == 0:
@@ -535,21 +697,27 @@ def run_ours(args):
                            "calls": "one after another" if args.serial else
                                     "independent calls on three streams (KDE, grid counts, sample-point counts)",
                            "parallelism": "replicas" if ws > 1 else "single"},
-                "gpu_launches": int(launches), "roofline": roofline, "io_floor": io_floor,
-                "kernel_families": breakdown,
-                "split": split, "fp64_path": fp64, "extras": extras, "e2e": e2e, "cpu_baseline": cpu,
-                "clocks": clk}
+                "gpu_launches": int(launches), "roofline": roofline, "roofline_per_call": per_call,
+                "io_floor": io_floor, "kernel_families": breakdown,
+                "split": split, "fp64_path": fp64, "fp64_step": fp64_step, "extras": extras, "e2e": e2e,
+                "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def _extras(fk, torch, dev, x, stream, flush, timed):
-    """Batched 512-dataset workload (graph replay; mixed vs FP64 path) and the
-    KDE adjoint (grad w, grad h) at N=1e6, d=3."""
+def _extras(fk, torch, dev, x, stream, flush, timed, args):
+    """The other hot-path workloads, timed beside the step (ms, CUDA events,
+    L2 flushed): the 512-dataset batch (graph replay; mixed vs FP64), the KDE
+    adjoint at N=1e6, d=3, the d=2 copula workload (KDE and Nadaraya-Watson at
+    three bandwidths, both paths, and the adjoint), the weighted d=3 orthant
+    sums, the d=4 leave-one-out likelihood and bandwidth search, the grid KDE
+    study and the other estimators.  Returns (timings, samples): `samples`
+    holds GPU outputs at seeded indices, which the cpu_baseline leg compares
+    with the oracle."""
     from paper_2005_03246_gb300 import datagen
-    out = {}
+    out, samples = {}, {}
     sets = datagen.batched()
     xs = [torch.as_tensor(s["x"], device=dev) for s in sets]
     ys = [torch.as_tensor(s["y"], device=dev) for s in sets]
@@ -566,12 +734,141 @@ def _extras(fk, torch, dev, x, stream, flush, timed):
                       "points": pts, "mixed_ms": tm, "fp64_ms": td, "points_per_s": pts / (tm / 1e3),
                       "mixed_speedup": td / tm, "mixed_config": bm.config, "fp64_config": bd.config,
                       "mixed_default_config_ms": tm0}
+    # outputs of six datasets (three of each dimension, the smallest first) for the oracle
+    chk = sorted(range(len(sets)), key=lambda b: sets[b]["n"])
+    chk = [b for b in chk if sets[b]["d"] == 2][:3] + [b for b in chk if sets[b]["d"] == 3][:3]
+    for name, bb in (("mixed", bm), ("fp64", bd)):
+        e, k = bb.run()
+        torch.cuda.synchronize()
+        samples["batched_" + name] = [(sets[b]["x"], sets[b]["y"], e[b].cpu().numpy(), k[b].cpu().numpy())
+                                      for b in chk]
+    del bm, bd, bm0
+    # KDE adjoint (grad w, grad h) at N=1e6, d=3, upstream gradient 1: grad_w[i]
+    # is the unweighted kernel sum at x_i (the kernel is symmetric)
     g = torch.ones(x.shape[0], dtype=torch.float64, device=dev)
     out["kde_backward_ms"] = timed(lambda: fk.kde_laplace_backward(x, H, g, need_w=True, need_z=False,
                                                                    need_h=True, path="mixed"), reps=3)
+    gw, _, gh = fk.kde_laplace_backward(x, H, g, need_w=True, need_z=False, need_h=True, path="mixed")
+    idx = datagen.sample_targets(x.shape[0], 128, seed=77)
+    samples["backward_d3"] = {"idx": idx, "grad_w": gw[torch.as_tensor(idx, device=dev)].cpu().numpy()}
+    del gw, gh
+    out["c3_copula_d2"] = _c3(fk, torch, dev, timed, samples)
+    out["c2_weighted_d3"] = _c2_weighted(fk, torch, dev, x, timed, samples)
+    if not args.no_c5:
+        out["c5_loo_d4"] = _c5(fk, torch, dev, timed, samples, search=not args.no_c5_search)
     out["kde_grid"] = _grid_kde_study(fk, torch, x, timed)
     out["other_estimators"] = _other_estimators(fk, torch, x, timed)
-    return out
+    return out, samples
+
+
+def _c3(fk, torch, dev, timed, samples):
+    """d=2 Gaussian copula with Student-t4 marginals, N=1e6: KDE and
+    Nadaraya-Watson at the sample points for h in {0.05, 0.1, 0.3}, mixed and
+    FP64 paths; the adjoint (grad w, z, h) at 4096 explicit targets."""
+    from paper_2005_03246_gb300 import datagen
+    d = datagen.copula_t4()
+    xn, yn = d["x"], d["y"]
+    x = torch.as_tensor(xn, device=dev)
+    y = torch.as_tensor(yn, device=dev)
+    n = xn.shape[0]
+    idx = datagen.sample_targets(n, 256, seed=31)
+    it = torch.as_tensor(idx, device=dev)
+    res = {"workload": "d=2 Gaussian copula rho=0.7, t4 marginals, N=1e6, FP32; y = sin(x1+x2) + 0.1 N(0,1)"}
+    smp = {"x": xn, "y": yn, "idx": idx, "values": {}}
+    for h in (0.05, 0.1, 0.3):
+        row = {}
+        for path in ("mixed", "fp64"):
+            row["kde_%s_ms" % path] = timed(lambda: fk.kde_laplace(x, h, path=path), reps=3)
+            row["nw_%s_ms" % path] = timed(lambda: fk.kreg_laplace(x, y, h, path=path), reps=3)
+            f = fk.kde_laplace(x, h, path=path)
+            m = fk.kreg_laplace(x, y, h, path=path)
+            smp["values"][(h, path)] = (f[it].cpu().numpy(), m[it].cpu().numpy())
+            del f, m
+        row["kde_mixed_speedup"] = row["kde_fp64_ms"] / row["kde_mixed_ms"]
+        row["nw_mixed_speedup"] = row["nw_fp64_ms"] / row["nw_mixed_ms"]
+        row["kde_points_per_s_mixed"] = n / (row["kde_mixed_ms"] / 1e3)
+        res["h%g" % h] = row
+    r = np.random.default_rng(33)
+    m = 4096
+    zn = (xn[r.choice(n, m, replace=False)] + r.normal(0.0, 0.05, (m, 2))).astype(np.float32)
+    gn = r.standard_normal(m)
+    z = torch.as_tensor(zn, device=dev)
+    g = torch.as_tensor(gn, device=dev)
+    hv = np.array([0.1, 0.12])
+    adj = {"targets": m, "h": hv.tolist()}
+    for path in ("mixed", "fp64"):
+        adj["%s_ms" % path] = timed(lambda: fk.kde_laplace_backward(x, hv, g, z=z, path=path), reps=3)
+    adj["mixed_speedup"] = adj["fp64_ms"] / adj["mixed_ms"]
+    res["adjoint"] = adj
+    # a 512-target slice of the same adjoint for the oracle
+    zs, gs = zn[:512], gn[:512]
+    smp["adjoint"] = {"z": zs, "g": gs, "h": hv}
+    for path in ("mixed", "fp64"):
+        gw, gz, gh = fk.kde_laplace_backward(x, hv, torch.as_tensor(gs, device=dev),
+                                             z=torch.as_tensor(zs, device=dev), path=path)
+        sw = datagen.sample_targets(n, 128, seed=34)
+        smp["adjoint"][path] = (sw, gw[torch.as_tensor(sw, device=dev)].cpu().numpy(), gz.cpu().numpy(),
+                                gh.cpu().numpy())
+    samples["c3"] = smp
+    return res
+
+
+def _c2_weighted(fk, torch, dev, x, timed, samples):
+    """All 8 weighted orthant sums at the N=1e6 sample points of the d=3
+    workload, y ~ U[0,1], both paths."""
+    from paper_2005_03246_gb300 import datagen
+    d = datagen.ecdf_gauss3()
+    yn = d["y"]
+    y = torch.as_tensor(yn, device=dev)
+    idx = datagen.sample_targets(x.shape[0], 128, seed=21)
+    it = torch.as_tensor(idx, device=dev)
+    res = {"workload": "d=3 correlated Gaussian N=1e6, y ~ U[0,1], all 8 orthants at the sample points"}
+    smp = {"y": yn, "idx": idx}
+    for path in ("mixed", "fp64"):
+        res["%s_ms" % path] = timed(lambda: fk.ecdf_points(x, y=y, path=path), reps=3)
+        o = fk.ecdf_points(x, y=y, path=path)
+        smp[path] = o[:, it].cpu().numpy()
+        del o
+    res["mixed_speedup"] = res["fp64_ms"] / res["mixed_ms"]
+    res["points_per_s_mixed"] = x.shape[0] / (res["mixed_ms"] / 1e3)
+    samples["c2w"] = smp
+    return res
+
+
+def _c5(fk, torch, dev, timed, samples, search=True):
+    """d=4 Gaussian copula (equicorrelation 0.3, exponential(1) marginals
+    centred), N=4e6: one leave-one-out likelihood-and-gradient evaluation on
+    each path, and the 20-step bandwidth search (ascent on log h from h=0.5,
+    rate 0.5) on the mixed path, timed on the host around the whole search."""
+    from paper_2005_03246_gb300 import datagen
+    xn = datagen.copula_exp4()["x"]
+    x = torch.as_tensor(xn, device=dev)
+    n = xn.shape[0]
+    h0 = np.full(4, 0.5)
+    res = {"workload": "d=4 copula N=4e6, exponential marginals, FP32; LOO likelihood + dL/dh, 16 orthants"}
+    for path in ("mixed", "fp64"):
+        res["loo_step_%s_ms" % path] = timed(lambda: fk.loo_laplace(x, h0, path=path), reps=1)
+    res["loo_mixed_speedup"] = res["loo_step_fp64_ms"] / res["loo_step_mixed_ms"]
+    hfin = h0
+    if search:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = fk.select_bandwidth_loo(x, h0=0.5, steps=20, lr=0.5, path="mixed")
+        torch.cuda.synchronize()
+        res["search20_mixed_s"] = time.perf_counter() - t0
+        res["search20_fp64_s_estimate"] = 20 * res["loo_step_fp64_ms"] / 1e3
+        res["h_final"] = float(hist[-1][0][0])
+        res["L_first_last"] = [hist[0][1], hist[-1][1]]
+        hfin = hist[-1][0]
+    idx = datagen.sample_targets(n, 48, seed=51)
+    it = torch.as_tensor(idx, device=dev)
+    smp = {"x": xn, "idx": idx, "h": np.asarray(hfin, dtype=np.float64)}
+    for path in ("mixed", "fp64"):
+        f = fk.kde_laplace(x, hfin, loo=True, path=path)
+        smp[path] = f[it].cpu().numpy()
+        del f
+    samples["c5"] = smp
+    return res
 
 
 def _other_estimators(fk, torch, x, timed):

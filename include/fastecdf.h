@@ -494,6 +494,12 @@ fk_status fk_profile_read(int family, double* total_ms, uint64_t* launches, doub
  * (operations run independent parts on several streams, whose launches
  * overlap; total_ms above sums them). */
 fk_status fk_profile_busy(int family, double* busy_ms);
+/* The algorithmic bytes of the family's recorded launches (inputs read once,
+ * outputs written once).  For families 0-7 this equals fk_profile_read's
+ * alg_bytes; for family 8 it is the bytes its launches gather and write,
+ * beside the arithmetic fk_profile_read reports.  Summed over every family it
+ * gives the minimal traffic of the passes a call made. */
+fk_status fk_profile_read_bytes(int family, double* bytes);
 
 #ifdef __cplusplus
 }

@@ -79,6 +79,7 @@ SIGNATURES = {
     "fk_profile_reset": (None, []),
     "fk_profile_read": (I, [I, P, P, P]),
     "fk_profile_busy": (I, [I, P]),
+    "fk_profile_read_bytes": (I, [I, P]),
 }
 
 PROFILE_FAMILIES = {"merge_sweep": 0, "merge_totals": 1, "merge_plain": 2, "grid_pass": 3,

@@ -80,7 +80,7 @@ static bool is_pinned_host_pointer(const void* p) {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-struct ProfRec { int fam; double bytes; cudaEvent_t a, b; };
+struct ProfRec { int fam; double bytes; double mem; cudaEvent_t a, b; };
 static std::mutex g_prof_mu;
 static std::atomic<bool> g_prof_on{false};
 static std::vector<ProfRec> g_prof;
@@ -97,9 +97,9 @@ cudaEvent_t prof_event() {
     cudaEventCreate(&e);
     return e;
 }
-void prof_record(int family, double bytes, cudaEvent_t a, cudaEvent_t b) {
+void prof_record(int family, double work, double bytes, cudaEvent_t a, cudaEvent_t b) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof.push_back(ProfRec{family, bytes, a, b});
+    g_prof.push_back(ProfRec{family, work, bytes, a, b});
 }
 
 // The per-device error word: kernels record the first device-side error here
@@ -247,6 +247,15 @@ void fk_profile_reset(void) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto& r : g_prof) { g_free_events.push_back(r.a); g_free_events.push_back(r.b); }
     g_prof.clear();
+}
+
+fk_status fk_profile_read_bytes(int family, double* bytes) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double by = 0.0;
+    for (auto& r : g_prof)
+        if (r.fam == family) by += r.mem;
+    if (bytes) *bytes = by;
+    return FK_OK;
 }
 
 fk_status fk_profile_read(int family, double* total_ms, uint64_t* launches, double* alg_bytes) {

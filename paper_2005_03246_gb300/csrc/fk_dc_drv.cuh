@@ -655,7 +655,7 @@ fk_status local_levels_t(const uint32_t* seq, int64_t n, int E, const uint32_t* 
     const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
                           (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes) + (E > L0 ? 8.0 * n : 0.0);
     ProfScope ps(Pol::kCanFold ? PF_KLOCAL : PF_LOCAL,
-                 Pol::kCanFold ? (double)n * L0 * kKernelOpsPerItemLevel : lbytes, st);
+                 Pol::kCanFold ? (double)n * L0 * kKernelOpsPerItemLevel : lbytes, st, lbytes);
     if constexpr (FOLD)
         k_local_fold<Pol, CLSB, HALF><<<grid_for(n, Cfg::T), Cfg::NT, smem, st>>>(
             seq, n, P0, cs, L0, pol, b.k[0], b.m[0], E > L0 ? 1 : 0, (E > L0 && Pol::kRecords) ? 1 : 0,

@@ -44,14 +44,15 @@ enum ProfFamily : int { PF_MERGE_SWEEP = 0, PF_MERGE_TOTALS = 1, PF_MERGE_PLAIN 
 // additions into the target's sum, 10 + 1 operations each.
 constexpr double kKernelOpsPerItemLevel = 44.0;
 bool profiling_on();
-void prof_record(int family, double bytes, cudaEvent_t a, cudaEvent_t b);
+void prof_record(int family, double work, double bytes, cudaEvent_t a, cudaEvent_t b);
 cudaEvent_t prof_event();
 struct ProfScope {
     int fam;
-    double bytes;
+    double bytes;     // the family's work (bytes, or operations for PF_KLOCAL)
+    double mem;       // algorithmic bytes (== bytes unless given)
     cudaStream_t st;
     cudaEvent_t a = nullptr;
-    ProfScope(int f, double b, cudaStream_t s) : fam(f), bytes(b), st(s) {
+    ProfScope(int f, double b, cudaStream_t s, double m = -1.0) : fam(f), bytes(b), mem(m < 0.0 ? b : m), st(s) {
         if (profiling_on()) {
             a = prof_event();
             cudaEventRecord(a, st);
@@ -61,7 +62,7 @@ struct ProfScope {
         if (a) {
             cudaEvent_t b2 = prof_event();
             cudaEventRecord(b2, st);
-            prof_record(fam, bytes, a, b2);
+            prof_record(fam, bytes, mem, a, b2);
         }
     }
 };
