@@ -168,7 +168,10 @@ fk_status fk_grid_interp(const double* f, int d, const double* z_axes, const int
  * axes.  The call reads the tie statistics back once (it synchronises
  * `stream` after the rank transform); if some axis has a tie group longer
  * than 64 points it uses a source copy and a target copy of every point
- * instead.  Either way the counts are exact.
+ * instead.  Either way the counts are exact.  On a stream that is being
+ * captured into a CUDA graph the call takes the copy layout directly (no
+ * read-back, so it can be captured; with device arrays and ws given or the
+ * library's stream-ordered pool); the captured graph gives the same counts.
  */
 size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points,
                                 int weighted, fk_path path);

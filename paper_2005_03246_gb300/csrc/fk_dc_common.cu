@@ -328,7 +328,12 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
     // (Weighted sums keep the copy layout: moving a tied term between two
     // floating-point sums after the fact leaves a rounding residue in an
     // orthant that holds no term.)
-    if (kind == 0 && sample && N >= 2) {
+    // The one-item layout reads its tie statistics back to the host, which a
+    // stream under graph capture cannot do: a captured call takes the copy
+    // layout, which needs no host decision (same counts, twice the items).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!ar.sizing) FK_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (kind == 0 && sample && N >= 2 && cap == cudaStreamCaptureStatusNone) {
         const size_t mark = ar.used;
         Positions p1;
         FK_TRY(plan_positions(x, nullptr, xd, N, N, d, d_eff, p1, ar, st));

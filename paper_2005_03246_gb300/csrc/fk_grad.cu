@@ -111,13 +111,99 @@ __global__ void k_grad_signed(const double* __restrict__ a, const double* __rest
     }
 }
 
-// g_j = 1 / (N f_j); L += (1/N) sum_j log f_j
-__global__ void k_loo_prep(const double* __restrict__ f, int64_t n, double* __restrict__ g, double* __restrict__ L) {
+// Leave-one-out densities too small for the sweep's accumulators.  A kernel
+// sum C sum_i w_i e^{-D_ij} is accumulated from terms w_i e^{-D_ij} held in
+// the path's floating-point type; terms below its smallest normal number
+// (2^-126 on the mixed path, 2^-1022 on the FP64 path) are lost.  A density
+// whose sum lies within 2^(mantissa bits + 1) N of that limit may have lost
+// more than the path's tolerance, and its logarithm enters the likelihood:
+// such a target (an isolated point at a small bandwidth) is listed here and
+// evaluated exactly by k_loo_exact instead.
+__global__ void k_loo_flag(const double* __restrict__ f, int64_t n, double thr, uint32_t* __restrict__ list,
+                           uint32_t* __restrict__ count) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && !(f[j] >= thr)) list[atomicAdd(count, 1u)] = (uint32_t)j;   // at most n entries
+}
+
+// Exact leave-one-out log-density and its h-gradient of the listed targets,
+// one CTA per target (grid-stride over the list): a single pass over the N
+// sources keeps, per thread, the smallest distance m seen so far and the
+// sums S0 = sum w e^{-(D - m)}, S1_k = sum w e^{-(D - m)} |x_ik - x_jk|
+// (rescaled when m drops), then merges the threads' states the same way.
+// Distances in FP64; the exponential in FP32 on the mixed path (arguments
+// D - m >= 0, relative error ~1e-7 per term) and in FP64 on the FP64 path.
+//   lf[j] = log C + log S0 - m,
+//   gh[k] += (1/N) (-1/h_k + S1_k / (h_k^2 S0)).
+template <class T, bool F64EXP>
+__global__ void __launch_bounds__(256) k_loo_exact(const T* __restrict__ x, const T* __restrict__ w, int64_t n, int d,
+                                                   dc::HVec hinv, double logC, const uint32_t* __restrict__ list,
+                                                   const uint32_t* __restrict__ count, double* __restrict__ lf,
+                                                   double* __restrict__ gh) {
+    __shared__ double s_m[256], s_s[256][5];
+    const uint32_t cnt = *count;
+    for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+        const int64_t j = list[e];
+        double xj[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xj[k] = (k < d) ? (double)x[j * d + k] : 0.0;
+        double m = INFINITY, S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            if (i == j) continue;
+            double a[4], D = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                a[k] = (k < d) ? fabs((double)x[i * d + k] - xj[k]) : 0.0;
+                D += a[k] * hinv.v[k];
+            }
+            if (D < m) {                                   // rescale the sums to the new minimum
+                const double r = (m == INFINITY) ? 0.0 : (F64EXP ? exp(D - m) : (double)__expf((float)(D - m)));
+#pragma unroll
+                for (int q = 0; q < 5; ++q) S[q] *= r;
+                m = D;
+            }
+            const double t = (w ? (double)w[i] : 1.0) * (F64EXP ? exp(m - D) : (double)__expf((float)(m - D)));
+            S[0] += t;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) S[1 + k] += t * a[k];
+        }
+        s_m[threadIdx.x] = m;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {     // block minimum of m
+            if (threadIdx.x < o) s_m[threadIdx.x] = fmin(s_m[threadIdx.x], s_m[threadIdx.x + o]);
+            __syncthreads();
+        }
+        const double mb = s_m[0];
+        const double r = (m == INFINITY) ? 0.0 : exp(mb - m);   // once per thread: FP64 on both paths
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s_s[threadIdx.x][q] = S[q] * r;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) s_s[threadIdx.x][q] += s_s[threadIdx.x + o][q];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double S0 = s_s[0][0];
+            lf[j] = logC + log(S0) - mb;
+            for (int k = 0; gh && k < d; ++k)
+                atomicAdd(gh + k, (-hinv.v[k] + s_s[0][1 + k] * hinv.v[k] * hinv.v[k] / S0) / (double)n);
+        }
+        __syncthreads();
+    }
+}
+
+// g_j = 1 / (N f_j); L += (1/N) sum_j log f_j.  Targets below `thr` (listed
+// and evaluated by k_loo_exact) take their log-density from lf and get g_j = 0:
+// they add nothing to the sweep's adjoint, their gradient came from k_loo_exact.
+__global__ void k_loo_prep(const double* __restrict__ f, int64_t n, double thr, const double* __restrict__ lf,
+                           double* __restrict__ g, double* __restrict__ L) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (j < n) {
-        g[j] = 1.0 / ((double)n * f[j]);
-        v = log(f[j]) / (double)n;
+        const bool exact = !(f[j] >= thr);
+        g[j] = exact ? 0.0 : 1.0 / ((double)n * f[j]);
+        v = (exact ? lf[j] : log(f[j])) / (double)n;
     }
     const double b = block_sum(v);
     if (threadIdx.x == 0) atomicAdd(L, b);
@@ -280,18 +366,52 @@ fk_status loo_run(const void* x, fk_dtype xd, int64_t N, int d, const void* w, c
     double* T = (gh && !fast) ? ar.take<double>((size_t)no * N) : nullptr;
     double* f = ar.take<double>((size_t)N);
     double* g = ar.take<double>((size_t)N);
+    double* lf = ar.take<double>((size_t)N);
+    uint32_t* list = ar.take<uint32_t>((size_t)N);
+    uint32_t* count = ar.take<uint32_t>(1);
     if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (loo)");
     Nested nest(ar);
     FK_TRY(points_kernel(x, xd, N, d, w, nullptr, 0, h, FK_LOO, 1, f,
                          (gh && !fast) ? (ar.sizing ? (double*)1 : T) : nullptr, path, ar, st));
     nest.done();
     if (!ar.sizing) {
+        // C of the leave-one-out density, and the level below which its sum
+        // is recomputed exactly (see k_loo_flag)
+        double C = ldexp(1.0, -d) / (double)(N - 1);
+        dc::HVec hinv;
+        for (int k = 0; k < 8; ++k) hinv.v[k] = (k < d) ? 1.0 / h[k] : 0.0;
+        for (int k = 0; k < d; ++k) C /= h[k];
+        const int lgN = (int)ceil(log2((double)N));
+        const double thr = C * ldexp(1.0, (path == FK_PATH_FP64 ? -1022 + 54 : -126 + 25) + lgN);
         FK_CUDA(cudaMemsetAsync(L, 0, sizeof(double), st));
-        k_loo_prep<<<grid_for(N, 256), 256, 0, st>>>(f, N, g, L);
+        FK_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t), st));
+        if (gh) FK_CUDA(cudaMemsetAsync(gh, 0, (size_t)d * sizeof(double), st));
+        k_loo_flag<<<grid_for(N, 256), 256, 0, st>>>(f, N, thr, list, count);
+        FK_LAUNCH_CHECK();
+        int dev = 0, sms = 0;
+        FK_CUDA(cudaGetDevice(&dev));
+        FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const unsigned ge = (unsigned)(2 * sms);
+        if (xd == FK_F32) {
+            if (path == FK_PATH_FP64)
+                k_loo_exact<float, true><<<ge, 256, 0, st>>>((const float*)x, (const float*)w, N, d, hinv, log(C), list,
+                                                             count, lf, gh);
+            else
+                k_loo_exact<float, false><<<ge, 256, 0, st>>>((const float*)x, (const float*)w, N, d, hinv, log(C),
+                                                              list, count, lf, gh);
+        } else {
+            if (path == FK_PATH_FP64)
+                k_loo_exact<double, true><<<ge, 256, 0, st>>>((const double*)x, (const double*)w, N, d, hinv, log(C),
+                                                              list, count, lf, gh);
+            else
+                k_loo_exact<double, false><<<ge, 256, 0, st>>>((const double*)x, (const double*)w, N, d, hinv, log(C),
+                                                               list, count, lf, gh);
+        }
+        FK_LAUNCH_CHECK();
+        k_loo_prep<<<grid_for(N, 256), 256, 0, st>>>(f, N, thr, lf, g, L);
         FK_LAUNCH_CHECK();
     }
     if (gh) {
-        if (!ar.sizing) FK_CUDA(cudaMemsetAsync(gh, 0, (size_t)d * sizeof(double), st));
         if (fast) FK_TRY(grad_signed_run(x, xd, N, d, nullptr, 0, h, FK_LOO, g, f, nullptr, gh, path, ar, st));
         else FK_TRY(grad_h_run(x, xd, N, d, w, nullptr, 0, h, FK_LOO, g, f, T, gh, path, ar, st));
         nest.done();

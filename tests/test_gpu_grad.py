@@ -159,3 +159,22 @@ def test_backward_unweighted_explicit_targets_d3(path):
     assert _err(gw.cpu().numpy(), rw) <= TOL[path]
     assert _err(gz.cpu().numpy(), rz) <= TOL[path]
     assert _err(gh.cpu().numpy(), rh) <= TOL[path]
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+@pytest.mark.parametrize("d", [2, 4])
+def test_loo_likelihood_with_isolated_points(path, d):
+    """Isolated points whose leave-one-out density lies below the FP32 range
+    (nearest neighbour 75 to 440 bandwidths away): the likelihood and its
+    gradient stay finite and match the oracle on both paths."""
+    r = np.random.default_rng(120 + d)
+    x = r.standard_normal((3000, d))
+    far = np.array([[8.0 + 3.0 * k] * d for k in range(4)])       # 3 apart per axis from each other
+    near = np.array([[-6.0] * d, [-2.25] + [-6.0] * (d - 1)])      # 75 bandwidths apart
+    x = np.concatenate([x, far, near]).astype(np.float32)
+    h = np.full(d, 0.05)
+    L, gh = _fk().loo_laplace(_t(x), h, path=path)
+    rL, rg = oracle.loo_loglik(x, h)
+    assert np.isfinite(rL) and np.isfinite(float(L.item()))
+    assert abs(float(L.item()) - rL) <= TOL[path] * max(1.0, abs(rL))
+    assert _err(gh.cpu().numpy(), rg) <= TOL[path]
