@@ -485,9 +485,11 @@ fk_status fk_grid_interp(const double* f, int d, const double* z_axes, const int
 
 // ------------------------------------------------------------------ sample-point path
 // max_d: 8 for orthant counts (inclusion-exclusion over dominance counts),
-// 4 for the weighted and kernel sums (2^(d-1) channels per sweep).
+// 6 for the weighted orthant sums, the KDE and Nadaraya-Watson (2^(d-1)
+// channels per sweep), 4 for what needs per-orthant terms or signed sums (the
+// adjoint and the leave-one-out likelihood).
 static fk_status points_validate(const void* x, fk_dtype xd, int64_t N, int d, const void* z, int64_t M,
-                                 fk_path path, bool doubled, int max_d = 4) {
+                                 fk_path path, bool doubled, int max_d = 6) {
     FK_TRY(check_common(x, xd, N, d, path));
     if (d > max_d)
         return set_error(FK_ERR_UNSUPPORTED, "this sample-point call supports d <= %d (counts: d <= 8)", max_d);
@@ -501,7 +503,7 @@ static fk_status points_validate(const void* x, fk_dtype xd, int64_t N, int d, c
 
 size_t fk_ecdf_points_workspace(int64_t N, int d, int64_t M, int sample_points, int weighted, fk_path path) {
     const void* z = sample_points ? nullptr : (const void*)1;
-    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, true, weighted ? 4 : 8) != FK_OK) return 0;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, true, weighted ? 6 : 8) != FK_OK) return 0;
     size_t best = 0;
     for (int t = 0; t < 2; ++t) {   // size for both dtypes (FP64 keys are wider)
         Arena ar;
@@ -516,7 +518,7 @@ static fk_status ecdf_points_impl(const void* x, fk_dtype xd, int64_t N, int d, 
                                   int64_t M, const uint32_t* mask, void* out, fk_path path, void* ws,
                                   size_t ws_bytes, fk_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    FK_TRY(points_validate(x, xd, N, d, z, M, path, true, y ? 4 : 8));
+    FK_TRY(points_validate(x, xd, N, d, z, M, path, true, y ? 6 : 8));
     const int64_t m_out = z ? M : N;
     int nsel = 0;
     for (int o = 0; o < (1 << d); ++o)
@@ -632,7 +634,7 @@ fk_status fk_kreg_laplace(const void* x, fk_dtype xd, int64_t N, int d, const vo
 // ------------------------------------------------------------------ adjoints
 size_t fk_kde_laplace_backward_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path) {
     const void* z = sample_points ? nullptr : (const void*)1;
-    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, false) != FK_OK) return 0;
+    if (points_validate((const void*)1, FK_F32, N, d, z, M, path, false, 4) != FK_OK) return 0;
     double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     // the plan differs with and without weights (terms vs signed sums): the larger
     size_t best = 0;
@@ -653,7 +655,7 @@ fk_status fk_kde_laplace_backward(const void* x, fk_dtype xd, int64_t N, int d, 
                                   size_t ws_bytes, fk_stream_t stream) {
     FK_RANGE("fk_kde_laplace_backward");
     cudaStream_t st = (cudaStream_t)stream;
-    FK_TRY(points_validate(x, xd, N, d, z, M, path, false));
+    FK_TRY(points_validate(x, xd, N, d, z, M, path, false, 4));
     FK_TRY(check_h(h, d));
     if ((flags & FK_LOO) && z) return set_error(FK_ERR_INVALID_ARG, "FK_LOO needs z == NULL");
     if (grad_z && !z) return set_error(FK_ERR_INVALID_ARG, "grad_z needs explicit targets z");
@@ -688,7 +690,7 @@ fk_status fk_kde_laplace_backward(const void* x, fk_dtype xd, int64_t N, int d, 
 }
 
 size_t fk_loo_laplace_workspace(int64_t N, int d, fk_path path) {
-    if (points_validate((const void*)1, FK_F32, N, d, nullptr, 0, path, false) != FK_OK) return 0;
+    if (points_validate((const void*)1, FK_F32, N, d, nullptr, 0, path, false, 4) != FK_OK) return 0;
     double h[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     size_t best = 0;
     for (int t = 0; t < 4; ++t) {
@@ -705,7 +707,7 @@ fk_status fk_loo_laplace(const void* x, fk_dtype xd, int64_t N, int d, const voi
                          fk_stream_t stream) {
     FK_RANGE("fk_loo_laplace");
     cudaStream_t st = (cudaStream_t)stream;
-    FK_TRY(points_validate(x, xd, N, d, nullptr, 0, path, false));
+    FK_TRY(points_validate(x, xd, N, d, nullptr, 0, path, false, 4));
     FK_TRY(check_h(h, d));
     if (N < 2) return set_error(FK_ERR_INVALID_ARG, "leave-one-out needs N >= 2");
     if (!loglik) return set_error(FK_ERR_INVALID_ARG, "loglik is NULL");

@@ -359,11 +359,41 @@ fk_status points_orthant(const void* x, fk_dtype xd, int64_t N, int d, const voi
 }
 
 // ------------------------------------------------------------------ kernel sums
+__global__ void k_ratio(const double* __restrict__ num, const double* __restrict__ den, int64_t n,
+                        double* __restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = num[t] / den[t];
+}
+
 fk_status points_kernel(const void* x, fk_dtype xd, int64_t N, int d, const void* w, const void* z, int64_t M,
                         const double* h, unsigned flags, int nw, double* out, double* terms, fk_path path,
                         Arena& ar, cudaStream_t st, fk_dtype wd, int sgn) {
     if (sgn >= 0 && (nw != 2 || terms)) return set_error(FK_ERR_INVALID_ARG, "signed sums need nw == 2, no terms");
     if ((int)wd < 0) wd = xd;
+    if (d > 4 && (sgn >= 0 || terms))
+        return set_error(FK_ERR_UNSUPPORTED, "per-orthant terms and signed sums support d <= 4");
+    if (d > 4 && nw == 2) {
+        // Nadaraya-Watson beyond d = 4: numerator (weights y) and denominator
+        // (weights 1) as two one-channel kernel sums; C and the self pair enter
+        // both the same way, so their ratio is the estimate
+        const int64_t n_tgt = z ? M : N;
+        double* num = ar.take<double>((size_t)n_tgt);
+        double* den = ar.take<double>((size_t)n_tgt);
+        if (!ar.sizing && ar.overflow()) return set_error(FK_ERR_WORKSPACE, "workspace too small (kernel sums)");
+        const size_t mark = ar.used;
+        FK_TRY(points_kernel(x, xd, N, d, w, z, M, h, flags, 1, ar.sizing ? (double*)1 : num, nullptr, path, ar, st,
+                             wd));
+        const size_t high = ar.used;
+        ar.used = mark;
+        FK_TRY(points_kernel(x, xd, N, d, nullptr, z, M, h, flags, 1, ar.sizing ? (double*)1 : den, nullptr, path,
+                             ar, st, wd));
+        if (ar.used < high) ar.used = high;
+        if (!ar.sizing && n_tgt > 0) {
+            k_ratio<<<grid_for(n_tgt, 256), 256, 0, st>>>(num, den, n_tgt, out);
+            FK_LAUNCH_CHECK();
+        }
+        return FK_OK;
+    }
     const int d_eff = d < 2 ? 2 : d;
     const bool sample = (z == nullptr);
     const bool loo = sample && (flags & FK_LOO);

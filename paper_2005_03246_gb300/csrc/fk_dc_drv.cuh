@@ -722,7 +722,13 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
     constexpr int NCH = 2 << CLSB;
     // tile-local levels (gather fused into the tile load)
     int L0 = 0;
-    if constexpr (Pol::kCanFold) {
+    if constexpr (Pol::kCanFold && CLSB >= 3) {
+        // d > 4: folded sums only (per-orthant terms would take 2^d channels
+        // of target state per item)
+        if (pol.terms) return set_error(FK_ERR_UNSUPPORTED, "per-orthant kernel terms support d <= 4");
+        FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, opts, st)));
+        if constexpr (Pol::kRecords) return fold_levels<Pol, CLSB>(n, E, L0, pol, b, st);
+    } else if constexpr (Pol::kCanFold) {
         if (!pol.terms) {
             FK_TRY((local_levels<Pol, CLSB, true>(seq, n, E, P0, cs, pol, b, L0, opts, st)));
             if constexpr (Pol::kRecords) return fold_levels<Pol, CLSB>(n, E, L0, pol, b, st);
@@ -732,6 +738,9 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
     } else {
         FK_TRY((local_levels<Pol, CLSB, false>(seq, n, E, P0, cs, pol, b, L0, opts, st)));
     }
+    if constexpr (Pol::kCanFold && Pol::kRecords && CLSB >= 3) {
+        return FK_OK;   // not reached: the folded records handled every level above
+    } else {
     int cur = 0;
     const unsigned ctas = grid_for(n, MTILE);
     // algorithmic bytes of one sweep merge: keys+metas in and out, source
@@ -765,6 +774,7 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
         cur ^= 1;
     }
     return FK_OK;
+    }
 }
 
 // Recursion over the tree axes.  `seq` holds the items sorted by P_k inside

@@ -22,6 +22,29 @@ FK_DC_SWEEP_DECL(sweep_kd1, PolKD<1>)
 FK_DC_SWEEP_DECL(sweep_kd2, PolKD<2>)
 #undef FK_DC_SWEEP_DECL
 
+// d = 5 and 6 (3 and 4 enclosing class bits, 16 and 32 channels): one-channel
+// policies only, instantiated in fk_dc_d5.cu and fk_dc_d6.cu; the others refuse.
+#define FK_DC_SWEEP_HD_DECL(POL)                                                                 \
+    fk_status sweep_d5(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top, \
+                       const POL& pol, Arena& ar, cudaStream_t st, int levels, int opts);        \
+    fk_status sweep_d6(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top, \
+                       const POL& pol, Arena& ar, cudaStream_t st, int levels, int opts);
+FK_DC_SWEEP_HD_DECL(PolW64)
+FK_DC_SWEEP_HD_DECL(PolWFF)
+FK_DC_SWEEP_HD_DECL(PolKF<1>)
+FK_DC_SWEEP_HD_DECL(PolKD<1>)
+#undef FK_DC_SWEEP_HD_DECL
+template <class POL>
+fk_status sweep_d5(int, int64_t, const uint32_t* const*, const uint32_t*, const POL&, Arena&, cudaStream_t, int,
+                   int) {
+    return set_error(FK_ERR_UNSUPPORTED, "two-channel kernel sums at the sample points support d <= 4");
+}
+template <class POL>
+fk_status sweep_d6(int, int64_t, const uint32_t* const*, const uint32_t*, const POL&, Arena&, cudaStream_t, int,
+                   int) {
+    return set_error(FK_ERR_UNSUPPORTED, "two-channel kernel sums at the sample points support d <= 4");
+}
+
 #define FK_DC_SWEEP_DEF(NAME, POL)                                                               \
     fk_status NAME(int d_eff, int64_t n, const uint32_t* const* P, const uint32_t* seq_top,    \
                    const POL& pol, Arena& ar, cudaStream_t st, int levels, int opts) {         \
@@ -29,7 +52,9 @@ FK_DC_SWEEP_DECL(sweep_kd2, PolKD<2>)
             case 2: return dc_sweep<POL, 0>(d_eff, n, P, seq_top, pol, ar, st, levels, opts);   \
             case 3: return dc_sweep<POL, 1>(d_eff, n, P, seq_top, pol, ar, st, levels, opts);   \
             case 4: return dc_sweep<POL, 2>(d_eff, n, P, seq_top, pol, ar, st, levels, opts);   \
-            default: return set_error(FK_ERR_UNSUPPORTED, "sample-point path supports d <= 4"); \
+            case 5: return sweep_d5(d_eff, n, P, seq_top, pol, ar, st, levels, opts);           \
+            case 6: return sweep_d6(d_eff, n, P, seq_top, pol, ar, st, levels, opts);           \
+            default: return set_error(FK_ERR_UNSUPPORTED, "sample-point path supports d <= 6"); \
         }                                                                                       \
     }
 

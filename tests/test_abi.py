@@ -91,14 +91,21 @@ def test_batched_config_default_and_validation():
 
 
 def test_sample_point_dimension_limits():
-    """Counts at the sample points accept d <= 8, weighted sums d <= 4."""
+    """Counts at the sample points accept d <= 8; weighted sums, the KDE and
+    Nadaraya-Watson d <= 6; the adjoint and the leave-one-out likelihood d <= 4."""
     from paper_2005_03246_gb300 import _lib
     lib = _lib.load()
-    for d in (5, 8):
+    for d in (5, 6, 8):
         assert lib.fk_ecdf_points_workspace(1000, d, 0, 1, 0, 0) > 0
-        assert lib.fk_ecdf_points_workspace(1000, d, 0, 1, 1, 0) == 0
+    for d in (5, 6):
+        assert lib.fk_ecdf_points_workspace(1000, d, 0, 1, 1, 0) > 0
+        assert lib.fk_kde_laplace_workspace(1000, d, 0, 1, 0, 0) > 0
+        assert lib.fk_kreg_laplace_workspace(1000, d, 0, 1, 0) > 0
+        assert lib.fk_kde_laplace_backward_workspace(1000, d, 0, 1, 0) == 0
+        assert lib.fk_loo_laplace_workspace(1000, d, 0) == 0
+    assert lib.fk_ecdf_points_workspace(1000, 7, 0, 1, 1, 0) == 0
     assert lib.fk_ecdf_points_workspace(1000, 9, 0, 1, 0, 0) == 0
-    assert lib.fk_kde_laplace_workspace(1000, 5, 0, 1, 0, 0) == 0
+    assert lib.fk_kde_laplace_workspace(1000, 7, 0, 1, 0, 0) == 0
 
 
 def test_extra_kernel_workspaces_and_limits():

@@ -48,7 +48,12 @@ def kde(x=X, xd=_lib.FK_F32, n=N, d=D, z=None, m=0, h=H, flags=0, out=OUT, path=
 CASES = [
     ("kde dtype", lambda: kde(xd=7), INVALID, "xdtype"),
     ("kde d=0", lambda: kde(d=0), INVALID, "d must be >= 1"),
-    ("kde d=5", lambda: kde(d=5), UNSUPPORTED, "d <= 4"),
+    ("kde d=7", lambda: kde(d=7), UNSUPPORTED, "d <= 6"),
+    ("backward d=5", lambda: _lib.load().fk_kde_laplace_backward(p(X), 0, N // 5, 5, None, None, 0, p(np.full(5, 0.1)),
+                                                                 0, p(OUT), p(OUT), None, None, 0, None, 0, None),
+     UNSUPPORTED, "d <= 4"),
+    ("loo d=5", lambda: _lib.load().fk_loo_laplace(p(X), 0, N // 5, 5, None, p(np.full(5, 0.1)), p(OUT), None, 0,
+                                                   None, 0, None), UNSUPPORTED, "d <= 4"),
     ("kde N<0", lambda: kde(n=-1), INVALID, "N must be >= 0"),
     ("kde x NULL", lambda: kde(x=None), INVALID, "x is NULL"),
     ("kde h=0", lambda: kde(h=np.array([0.1, 0.0, 0.1])), INVALID, "h[1] must be finite and > 0"),
@@ -59,8 +64,8 @@ CASES = [
     ("kde LOO with z", lambda: kde(z=X, m=N, flags=_lib.FK_LOO), INVALID, "FK_LOO needs z == NULL"),
     ("points d=9", lambda: _lib.load().fk_ecdf_points(p(X), 0, N, 9, None, None, 0, None, p(OUTI), 0, None, 0,
                                                       None), UNSUPPORTED, "d <= 8"),
-    ("points weighted d=5", lambda: _lib.load().fk_ecdf_points(p(X), 0, 20, 5, p(OUT), None, 0, None, p(OUTI), 0,
-                                                               None, 0, None), UNSUPPORTED, "d <= 4"),
+    ("points weighted d=7", lambda: _lib.load().fk_ecdf_points(p(X), 0, 20, 7, p(OUT), None, 0, None, p(OUTI), 0,
+                                                               None, 0, None), UNSUPPORTED, "d <= 6"),
     ("points out NULL", lambda: _lib.load().fk_ecdf_points(p(X), 0, N, D, None, None, 0, None, None, 0, None, 0,
                                                            None), INVALID, "out is NULL"),
     ("esf d=9", lambda: _lib.load().fk_esf_points(p(X), 0, N, 9, None, None, 0, p(OUTI), 0, None, 0, None),

@@ -400,3 +400,47 @@ def test_orthant_subsets_only_what_the_selection_needs(d):
         assert np.array_equal(got, oracle.orthant_sums(x, mask=sorted(sel))), sel
         gz = _fk().ecdf_points(_t(x), z=_t(z), orthants=sel).cpu().numpy()
         assert np.array_equal(gz, oracle.orthant_sums(x, z=z, mask=sorted(sel))), sel
+
+
+# ------------------------------------------------------------------ d = 5, 6
+
+
+@pytest.mark.parametrize("path", ["mixed", "fp64"])
+@pytest.mark.parametrize("d,n", [(5, 1200), (6, 700)])
+def test_high_dimension_kernel_and_weighted_sums(path, d, n):
+    """d = 5, 6 at the sample points (16 and 32 sweep channels): the Laplacian
+    KDE, its leave-one-out form, explicit targets, Nadaraya-Watson (two
+    one-channel sums) and the weighted orthant sums, against the oracle."""
+    r = np.random.default_rng(900 + d)
+    x = _points(n, d, seed=910 + d)
+    h = np.linspace(0.4, 0.7, d)
+    got = _fk().kde_laplace(_t(x), h, path=path).cpu().numpy()
+    assert _rel_kde(got, oracle.kde_laplace(x, h)) <= TOL[path]
+    gl = _fk().kde_laplace(_t(x), h, loo=True, path=path).cpu().numpy()
+    assert _rel_kde(gl, oracle.kde_laplace(x, h, loo=True)) <= TOL[path]
+    z = (r.standard_normal((150, d)) * 0.9).astype(np.float32)
+    gz = _fk().kde_laplace(_t(x), h, z=_t(z), path=path).cpu().numpy()
+    assert _rel_kde(gz, oracle.kde_laplace(x, h, z=z)) <= TOL[path]
+    y = (np.sin(x.sum(axis=1)) + 0.1 * r.standard_normal(n)).astype(np.float32)
+    gk = _fk().kreg_laplace(_t(x), _t(y), h, path=path).cpu().numpy()
+    assert _rel_nw(gk, oracle.kreg_laplace(x, y, h), oracle.kreg_laplace(x, np.abs(y), h)) <= TOL[path]
+    w = r.random(n).astype(np.float32)
+    gw = _fk().ecdf_points(_t(x), y=_t(w), path=path).cpu().numpy()
+    ref = oracle.orthant_sums(x, y=w)
+    absref = oracle.orthant_sums(x, y=np.abs(w))
+    assert gw.shape == (1 << d, n)
+    assert _rel_signed(gw, ref, absref) <= TOL[path]
+
+
+def test_high_dimension_refusals():
+    """What needs per-orthant terms or two weight channels in one sweep stays
+    at d <= 4: refused with FK_ERR_UNSUPPORTED."""
+    import torch
+    fk = _fk()
+    x = _t(_points(300, 5, seed=5))
+    with pytest.raises(fk.FastEcdfError, match="d <= 4"):
+        fk.kde_laplace_backward(x, 0.5, torch.ones(300, dtype=torch.float64, device="cuda:0"))
+    with pytest.raises(fk.FastEcdfError, match="d <= 4"):
+        fk.loo_laplace(x, 0.5)
+    with pytest.raises(fk.FastEcdfError, match="d <= 4"):
+        fk.kde_laplace(x, 0.5, terms=True)
