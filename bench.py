@@ -50,6 +50,9 @@ D = 3
 M_AXIS = 256
 H = 0.1
 WORKLOAD = "ecdf_gauss3_d3_n1e6_grid256_kde_h0.1"
+# sizes of the d = 5, 6 rows of the runtime-versus-N study (the sweep has 16
+# and 32 channels there; the paper's Tables 2 and 4 go to N = 1.28e6 at d = 6)
+SCALING_HIGH_D = {5: (10_000, 30_000, 100_000, 300_000), 6: (10_000, 30_000, 100_000)}
 
 
 def _args(argv=None):
@@ -69,6 +72,7 @@ def _args(argv=None):
                          "paper's runtime-versus-N study) and print one JSON line")
     ap.add_argument("--no-c5", action="store_true", help="skip the d=4, N=4e6 leave-one-out workload")
     ap.add_argument("--no-c5-search", action="store_true", help="skip its 20-step bandwidth search")
+    ap.add_argument("--no-scaling", action="store_true", help="skip the d = 5, 6 runtime-versus-N rows")
     ap.add_argument("--only", default=None, choices=["grid", "points", "kde", "kde64", "kreg"],
                     help="run one operation per step (profiling of a single kernel family)")
     return ap.parse_args(argv)
@@ -758,6 +762,12 @@ def _extras(fk, torch, dev, x, stream, flush, timed, args):
         out["c5_loo_d4"] = _c5(fk, torch, dev, timed, samples, search=not args.no_c5_search)
     out["kde_grid"] = _grid_kde_study(fk, torch, x, timed)
     out["other_estimators"] = _other_estimators(fk, torch, x, timed)
+    if not args.no_scaling:
+        out["scaling_high_d"] = {
+            "data": "correlated Gaussian S_ij = 0.5, FP32; all 2^d orthant counts and the mixed KDE (h = 0.1) "
+                    "at the sample points; ms and ns / (N log2^(d-1) N)",
+            "rows": _scaling_rows(fk, torch, dev, [(5, SCALING_HIGH_D[5][:3]), (6, SCALING_HIGH_D[6][:3])],
+                                  lambda fn, reps: timed(lambda: fn(), reps=reps), grid=False, reps=2)}
     return out, samples
 
 
@@ -986,12 +996,42 @@ def _e2e(lib, x_np, grid, args, dev):
             "ms_per_step": t * 1e3, "streams": 3}
 
 
+def _scaling_rows(fk, torch, dev, plan, timed, grid=True, reps=3):
+    """Runtime versus N on correlated Gaussian data (S_ij = 0.5, FP32): all 2^d
+    orthant counts at the sample points, the mixed-path KDE at h = 0.1 and, if
+    asked, the grid counts on a grid of ~N points; each time divided by
+    N log2^(d-1) N (the divide-and-conquer cost of Sec. 2.2) and, for the grid,
+    by N.  plan: [(d, [N, ...]), ...]."""
+    rows = []
+    r = np.random.default_rng(9)
+    for d, sizes in plan:
+        S = np.full((d, d), 0.5) + 0.5 * np.eye(d)
+        L = np.linalg.cholesky(S)
+        for n in sizes:
+            xn = (r.standard_normal((n, d)) @ L.T).astype(np.float32)
+            x = torch.as_tensor(xn, device=dev)
+            shape = n * math.log2(n) ** (d - 1)
+            fk.ecdf_points(x)                     # first calls of a shape: set-up outside the timing
+            fk.kde_laplace(x, 0.1, path="mixed")
+            torch.cuda.synchronize()
+            t_pts = timed(lambda: fk.ecdf_points(x), reps)
+            t_kde = timed(lambda: fk.kde_laplace(x, 0.1, path="mixed"), reps)
+            row = {"d": d, "n": n, "points_ms": t_pts, "kde_mixed_ms": t_kde,
+                   "points_ns_per_NlogN": t_pts * 1e6 / shape, "kde_ns_per_NlogN": t_kde * 1e6 / shape}
+            if grid:
+                m = max(2, int(round(n ** (1.0 / d))))
+                axes = [np.linspace(float(xn[:, k].min()), float(xn[:, k].max()), m) for k in range(d)]
+                t_grid = timed(lambda: fk.ecdf_grid(x, axes), reps)
+                row.update({"grid_ms": t_grid, "grid_points": m ** d, "grid_ns_per_N": t_grid * 1e6 / n})
+            rows.append(row)
+            del x
+            torch.cuda.empty_cache()
+    return rows
+
+
 def run_scaling(args):
-    """Runtime versus N at d = 2, 3, 4 on correlated Gaussian data (S_ij = 0.5,
-    FP32): all 2^d orthant counts at the sample points, the mixed-path KDE at
-    h = 0.1, and the grid counts on a grid of ~N points; each time divided by
-    N log2^(d-1) N (the divide-and-conquer cost the paper states, Sec. 2.2)
-    and, for the grid, by N.  Median of 3 runs with L2 flushed; CUDA events."""
+    """Runtime versus N at d = 2 ... 6 (the paper's runtime-versus-N study,
+    Sec. 4, Tables 1-4); median of 3 runs with L2 flushed; CUDA events."""
     import torch
     import paper_2005_03246_gb300 as fk
     dev = torch.device("cuda", 0)
@@ -1014,25 +1054,9 @@ def run_scaling(args):
             del r
         return statistics.median(v)
 
-    rows = []
-    r = np.random.default_rng(9)
-    for d in (2, 3, 4):
-        S = np.full((d, d), 0.5) + 0.5 * np.eye(d)
-        L = np.linalg.cholesky(S)
-        for n in (100_000, 300_000, 1_000_000, 3_000_000):
-            xn = (r.standard_normal((n, d)) @ L.T).astype(np.float32)
-            x = torch.as_tensor(xn, device=dev)
-            m = max(2, int(round(n ** (1.0 / d))))
-            axes = [np.linspace(float(xn[:, k].min()), float(xn[:, k].max()), m) for k in range(d)]
-            t_pts = timed(lambda: fk.ecdf_points(x))
-            t_kde = timed(lambda: fk.kde_laplace(x, 0.1, path="mixed"))
-            t_grid = timed(lambda: fk.ecdf_grid(x, axes))
-            shape = n * math.log2(n) ** (d - 1)
-            rows.append({"d": d, "n": n, "points_ms": t_pts, "kde_mixed_ms": t_kde, "grid_ms": t_grid,
-                         "grid_points": m ** d, "points_ns_per_NlogN": t_pts * 1e6 / shape,
-                         "kde_ns_per_NlogN": t_kde * 1e6 / shape, "grid_ns_per_N": t_grid * 1e6 / n})
-            del x
-            torch.cuda.empty_cache()
+    big = (100_000, 300_000, 1_000_000, 3_000_000)
+    plan = [(2, big), (3, big), (4, big), (5, SCALING_HIGH_D[5]), (6, SCALING_HIGH_D[6])]
+    rows = _scaling_rows(fk, torch, dev, plan, timed)
     print(json.dumps({"scaling": rows, "data": "synthetic correlated Gaussian, FP32",
                       "shape": "N log2^(d-1) N for the sample-point calls, N for the grid"}), flush=True)
     return 0

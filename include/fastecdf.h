@@ -48,8 +48,12 @@
  *   calls; fk_release_cached_memory() returns it to the driver.
  * Limits.  1 <= d <= 8 for the grid call and for orthant counts at the
  *   sample points (fk_ecdf_points / fk_esf_points with y == NULL; the work
- *   grows as N log^(d-1) N); 1 <= d <= 4 for the other sample-point
- *   (divide-and-conquer) calls; N + M must be below 2^26 items on the
+ *   grows as N log^(d-1) N); 1 <= d <= 6 for the weighted orthant sums,
+ *   fk_kde_laplace without orthant_terms and fk_kreg_laplace; 1 <= d <= 4 for
+ *   per-orthant terms, the adjoint (fk_kde_laplace_backward), the
+ *   leave-one-out likelihood (fk_loo_laplace) and the other kernels (uniform
+ *   kernel with weights, Matern-3/2, full bandwidth matrix, locally linear);
+ *   N + M must be below 2^26 items on the
  *   sample-point path (2N + ... when orthant sums are taken at the sample
  *   points, which doubles each point into a source and a target copy).
  *   Other values return FK_ERR_UNSUPPORTED.
@@ -203,7 +207,8 @@ fk_status fk_esf_points(const void* x, fk_dtype xdtype, int64_t N, int d, const 
  *   flags  : FK_LOO (only with z == NULL).
  *   out    : [M'] double.
  *   orthant_terms : optional [2^d][M'] double; receives the per-orthant terms
- *            C e^{-delta.z/h} S_delta (their sum is out).
+ *            C e^{-delta.z/h} S_delta (their sum is out); d <= 4.
+ * 1 <= d <= 6 (d = 5, 6 run the same sweep with 16 and 32 channels).
  */
 size_t fk_kde_laplace_workspace(int64_t N, int d, int64_t M, int sample_points,
                                 int want_terms, fk_path path);
@@ -216,8 +221,9 @@ fk_status fk_kde_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const
  * fk_kreg_laplace -- Nadaraya-Watson kernel regression with the Laplacian
  * kernel (the weights of eq. localdens carrying the response, Sec. 3.1 and
  * Sec. 4): m(z_j) = sum_i y_i K_ij / sum_i K_ij, both sums taken by the same
- * orthant decomposition as fk_kde_laplace.  out : [M'] double; NaN where the
- * denominator underflows to zero.
+ * orthant decomposition as fk_kde_laplace (for d = 5, 6 as two one-channel
+ * sums, numerator and denominator).  out : [M'] double; NaN where the
+ * denominator underflows to zero.  1 <= d <= 6.
  * Workspace: fk_kde_laplace_workspace(N, d, M, sample_points, 0, path) * 2.
  */
 size_t fk_kreg_laplace_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path);
@@ -239,7 +245,7 @@ fk_status fk_kreg_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, cons
  *                 the distance sums taken from d extra orthant-term passes with
  *                 weights w_i x_ik (|x - z|-weighted orthant sums).
  * Any of the three outputs may be NULL.  Same flags (FK_LOO), precision paths
- * and conventions as fk_kde_laplace.
+ * and conventions as fk_kde_laplace; 1 <= d <= 4.
  */
 size_t fk_kde_laplace_backward_workspace(int64_t N, int d, int64_t M, int sample_points, fk_path path);
 fk_status fk_kde_laplace_backward(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w,
@@ -252,7 +258,12 @@ fk_status fk_kde_laplace_backward(const void* x, fk_dtype xdtype, int64_t N, int
  * sample points, L(h) = (1/N) sum_j log f_{-j}(x_j) with f_{-j} the density of
  * the other N-1 points (normalised by N-1), and its gradient dL/dh [d]
  * (grad_h may be NULL): the forward pass with FK_LOO followed by the h-adjoint
- * with g_j = 1/(N f_{-j}).  loglik: [1] double.  N >= 2.
+ * with g_j = 1/(N f_{-j}).  loglik: [1] double.  N >= 2, 1 <= d <= 4.
+ * Densities too small for the path's accumulators (within 2^25 N of FP32's
+ * smallest normal number on the mixed path, 2^54 N of FP64's on the FP64
+ * path: isolated points at a small h) are evaluated exactly by a separate
+ * kernel (FP64 distances, one-pass log-sum-exp over all sources), which also
+ * gives their part of the gradient, so the likelihood stays finite.
  */
 size_t fk_loo_laplace_workspace(int64_t N, int d, fk_path path);
 fk_status fk_loo_laplace(const void* x, fk_dtype xdtype, int64_t N, int d, const void* w, const double* h,
