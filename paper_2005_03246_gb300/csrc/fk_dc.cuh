@@ -1132,134 +1132,6 @@ __device__ __forceinline__ void rec_move(const FoldRecs<Pol>& in, int64_t s, con
     if (d >= 0) out.wt[d] = wt;
 }
 
-// Exponent field of a float as a power of two (normal numbers; -127 for
-// zero and subnormals).
-__device__ __forceinline__ int fexp2(float t) { return (int)((__float_as_uint(t) >> 23) & 0xffu) - 127; }
-
-// Per-CTA channel totals of a merge level on the mixed path, without
-// per-addition shift bookkeeping.  Every source term w m 2^s of a slot
-// (direction, channel, weight channel) is scaled by 2^-R, R the largest
-// exponent among the slot's terms in this CTA, so that every scaled term is at
-// most 2 in magnitude; terms more than 2^126 below the slot's largest vanish,
-// which changes the total by less than 2^-115 of it.  The scaled terms are
-// summed in compensated FP32 (per thread, then a shuffle tree and a pass over
-// the warps), and each total is written as a shifted value (mantissa in
-// [1, 2), exponent R + its own).  Two passes over the records: the first finds
-// R, the second sums (the CTA's records are in L1/L2 by then).
-template <class Pol, int CLSB>
-__device__ __forceinline__ void merge_totals_scaled(const MergeTile& mt, const uint32_t* s_meta,
-                                                    const FoldRecs<Pol>& rin, const Pol& pol,
-                                                    typename Pol::V* __restrict__ totals) {
-    typedef typename Pol::M M;
-    constexpr int NW = Pol::kNW, NCH = 2 << CLSB, NS = 2 * NCH * NW;   // slot (dir * NCH + ch) * NW + q
-    constexpr int NWARP = MT / 32;
-    __shared__ int s_R[NS];
-    __shared__ FF s_red[NS][NWARP];
-    for (int i = threadIdx.x; i < NS; i += MT) s_R[i] = INT_MIN;
-    __syncthreads();
-    const int64_t ln = mt.ln, lc = mt.lc;
-    const int64_t p0 = (int64_t)threadIdx.x * MI;
-    int emax[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) emax[i] = INT_MIN;
-#pragma unroll
-    for (int e = 0; e < MI; ++e) {
-        const int64_t q = p0 + e;
-        if (q < ln) {
-            const uint32_t m = s_meta[mpd(q)];
-            if (pol.is_src(m & kItemMask)) {
-                const int half = (q >= lc) ? 1 : 0;
-                const int64_t g = half ? mt.ds + (q - lc) : mt.cs + q;
-                M f0, f1, wt;
-                int g0, g1;
-                rec_move<Pol>(rin, g, rin, -1, half, f0, f1, g0, g1, wt);
-                const int ch = (half << CLSB) | (int)(m >> kItemBits);
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const float wv = (NW == 2 && w == 1) ? 1.f : wt;
-                    const float t0 = wv * f0, t1 = wv * f1;
-                    const int e0 = (t0 != 0.f) ? g0 + fexp2(t0) : INT_MIN;
-                    const int e1 = (t1 != 0.f) ? g1 + fexp2(t1) : INT_MIN;
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        if (c == ch) {
-                            emax[(0 * NCH + c) * NW + w] = max(emax[(0 * NCH + c) * NW + w], e0);
-                            emax[(1 * NCH + c) * NW + w] = max(emax[(1 * NCH + c) * NW + w], e1);
-                        }
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const int v = __reduce_max_sync(0xffffffffu, emax[i]);
-        if ((threadIdx.x & 31) == 0 && v != INT_MIN) atomicMax(&s_R[i], v);
-    }
-    __syncthreads();
-    FF acc[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) acc[i] = ff_zero();
-#pragma unroll
-    for (int e = 0; e < MI; ++e) {
-        const int64_t q = p0 + e;
-        if (q < ln) {
-            const uint32_t m = s_meta[mpd(q)];
-            if (pol.is_src(m & kItemMask)) {
-                const int half = (q >= lc) ? 1 : 0;
-                const int64_t g = half ? mt.ds + (q - lc) : mt.cs + q;
-                M f0, f1, wt;
-                int g0, g1;
-                rec_move<Pol>(rin, g, rin, -1, half, f0, f1, g0, g1, wt);
-                const int ch = (half << CLSB) | (int)(m >> kItemBits);
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const float wv = (NW == 2 && w == 1) ? 1.f : wt;
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        const int i0 = (0 * NCH + c) * NW + w, i1 = (1 * NCH + c) * NW + w;
-                        const float t0 = (c == ch) ? wv * f0 * pow2f_any(g0 - s_R[i0]) : 0.f;
-                        const float t1 = (c == ch) ? wv * f1 * pow2f_any(g1 - s_R[i1]) : 0.f;
-                        acc[i0] = ff_add_f(acc[i0], t0);
-                        acc[i1] = ff_add_f(acc[i1], t1);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            FF y;
-            y.hi = __shfl_down_sync(0xffffffffu, acc[i].hi, o);
-            y.lo = __shfl_down_sync(0xffffffffu, acc[i].lo, o);
-            acc[i] = ff_add(acc[i], y);
-        }
-        if ((threadIdx.x & 31) == 0) s_red[i][threadIdx.x >> 5] = acc[i];
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * NCH) {
-        const int dc = threadIdx.x;                         // dir * NCH + ch
-        typename Pol::V out;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int i = dc * NW + w;
-            FF t = s_red[i][0];
-#pragma unroll
-            for (int k = 1; k < NWARP; ++k) t = ff_add(t, s_red[i][k]);
-            if (t.hi == 0.f || s_R[i] == INT_MIN) {
-                out.v[w] = sff_zero();
-            } else {
-                const int k = fexp2(t.hi);
-                const float sc = pow2f_any(-k);
-                out.v[w] = SFF{t.hi * sc, t.lo * sc, s_R[i] + k};
-            }
-        }
-        totals[(int64_t)blockIdx.x * 2 * NCH + dc] = out;
-    }
-}
-
 // Merge level of the folded records.  PH_TOTALS: per-CTA channel totals of
 // the source weights (runs longer than a tile).  PH_SWEEP: merge, payload
 // move and the sweep; each thread walks its elements from zero, the
@@ -1271,11 +1143,7 @@ __device__ __forceinline__ void merge_totals_scaled(const MergeTile& mt, const u
 template <class Pol, int CLSB, int PHASE>
 struct FoldOcc {
     static constexpr size_t bytes = sizeof(typename Pol::V) * (2 << CLSB);
-    // the scaled totals of the mixed path keep no shifted sums: four CTAs
-    // per SM (one wave of a 1e6-item level) for up to four channels
-    static constexpr int totals = (Pol::kFastLocal && (2 << CLSB) * Pol::kNW <= 4) ? 4
-                                  : (bytes <= 48 ? 3 : bytes <= 64 ? 2 : 1);
-    static constexpr int value = PHASE == PH_TOTALS ? totals : (bytes <= 48 ? 2 : 1);
+    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= 64 ? 2 : 1) : (bytes <= 48 ? 2 : 1);
 };
 
 template <class Pol, int CLSB, int PHASE>
@@ -1302,10 +1170,6 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
     const bool big = mt.big;
 
     if (PHASE == PH_TOTALS) {
-        if constexpr (Pol::kFastLocal) {
-            merge_totals_scaled<Pol, CLSB>(mt, s_meta, rin, pol, totals);
-            return;
-        }
         V tf[NCH], tb[NCH];
 #pragma unroll
         for (int c = 0; c < NCH; ++c) { tf[c] = Pol::zero(); tb[c] = Pol::zero(); }

@@ -227,7 +227,7 @@ struct PolKF : ItemMap {
     static constexpr bool kCanFold = true;
     static constexpr int kFoldT = NW == 1 ? 4096 : 2048, kNW = NW;
     static constexpr bool kRecords = true;    // longer levels on streamed records
-    static constexpr bool kFastLocal = true;  // tile-local levels and merge totals may run on scaled FP32 values
+    static constexpr bool kFastLocal = true;  // tile-local levels may run on scaled FP32 values
     typedef float M;
     typedef FF FA;
     // Tile-local running sums and scans: plain FP32 mantissa with a shift.

@@ -72,6 +72,75 @@ struct Items {
     }
 };
 
+// One merge level of the propagated-prefix dominance merge on padded
+// shared-memory arrays (key, meta, pref, acc): every thread produces NI
+// consecutive outputs starting at p0.  The thread keeps the heads of both
+// runs in registers -- key and prefix of C's next element (or C's total
+// once C is exhausted) and the same for D -- so an output needs only its own
+// meta and count from shared memory, plus the key and prefix of the head it
+// advances.  An output's new prefix is always the sum of the two head
+// prefixes; a receiving target from D adds C's head prefix (the active C
+// sources merged before it, C first on equal keys).  Returns the outputs made.
+// whole: the tile is one merged block whose C part is [0, wcl), D part
+// [wcl, ln), and whose runs' totals (w_ct, w_dt) come from outside the tile
+// (a global merge level with runs longer than a tile); otherwise the tile
+// holds whole merged blocks of 2^(m+1).
+template <int NI, class SrcF, class TgtF>
+__device__ __forceinline__ int dom_merge_level(const uint32_t* ik, const uint32_t* imt, const uint32_t* ip,
+                                               const uint32_t* ia, int ln, int m, int p0, uint32_t (&ok)[NI],
+                                               uint32_t (&om)[NI], uint32_t (&op)[NI], uint32_t (&oa)[NI],
+                                               SrcF src_active, TgtF tgt_active, bool whole = false, int wcl = 0,
+                                               uint32_t w_ct = 0, uint32_t w_dt = 0) {
+    const int R = whole ? 0 : 1 << m, R2 = whole ? 1 : 2 << m;
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0, cnt = 0;
+    uint32_t ctot = 0, dtot = 0, kc = 0, kd = 0, pcv = 0, pdv = 0;
+#pragma unroll
+    for (int e = 0; e < NI; ++e) {
+        const int p = p0 + e;
+        if (p < ln) {
+            if (e == 0 || (!whole && (p % R2) == 0)) {
+                if (whole) {
+                    bsl = 0; cl = wcl; dl = ln - wcl;
+                    ctot = w_ct; dtot = w_dt;
+                } else {
+                    bsl = (p / R2) * R2;
+                    cl = min(R, ln - bsl);
+                    dl = min(R2, ln - bsl) - cl;
+                    ctot = ip[pd(bsl + cl - 1)] + (src_active(imt[pd(bsl + cl - 1)]) ? 1u : 0u);
+                    dtot = dl > 0 ? ip[pd(bsl + cl + dl - 1)] + (src_active(imt[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
+                }
+                SAccP A{ik, bsl}, B{ik, bsl + cl};
+                i = (int)merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+                kc = (i < cl) ? ik[pd(bsl + i)] : 0u;
+                pcv = (i < cl) ? ip[pd(bsl + i)] : ctot;
+                kd = (j < dl) ? ik[pd(bsl + cl + j)] : 0u;
+                pdv = (j < dl) ? ip[pd(bsl + cl + j)] : dtot;
+            }
+            const bool tc = (i < cl) && (j >= dl || kc <= kd);
+            const int s = tc ? pd(bsl + i) : pd(bsl + cl + j);
+            const uint32_t mt = imt[s], ac = ia[s];
+            ok[e] = tc ? kc : kd;
+            om[e] = mt;
+            op[e] = pcv + pdv;
+            oa[e] = ac + ((!tc && tgt_active(mt)) ? pcv : 0u);
+            // advance the head that was taken
+            i += tc ? 1 : 0;
+            j += tc ? 0 : 1;
+            const bool v = tc ? (i < cl) : (j < dl);
+            const int q = tc ? pd(bsl + i) : pd(bsl + cl + j);
+            const uint32_t nk = v ? ik[q] : 0u;
+            const uint32_t np = v ? ip[q] : (tc ? ctot : dtot);
+            kc = tc ? nk : kc;
+            pcv = tc ? np : pcv;
+            kd = tc ? kd : nk;
+            pdv = tc ? pdv : np;
+            cnt = e + 1;
+        }
+    }
+    return cnt;
+}
+
 constexpr int LNT = 256;          // threads of the tile-local kernel (tiles of 1024, 2048 or 4096 items)
 
 // Tile-local merge levels.  Input: the enclosing state (items sorted by the
@@ -120,46 +189,11 @@ __global__ void __launch_bounds__(LNT) k_dom_local(const uint32_t* __restrict__ 
     __syncthreads();
     int b = 0;
     for (int m = 0; m < levels; ++m) {
-        const int R = 1 << m, R2 = 2 << m;
-        const uint32_t* ik = s_key[b];
-        const uint32_t* imt = s_meta[b];
-        const uint32_t* ip = s_pref[b];
-        const uint32_t* ia = s_acc[b];
         uint32_t ok[LIT], om[LIT], op[LIT], oa[LIT];
-        int cnt = 0;
         const int p0 = threadIdx.x * LIT;
-        int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
-        uint32_t ctot = 0, dtot = 0;
-#pragma unroll
-        for (int e = 0; e < LIT; ++e) {
-            const int p = p0 + e;
-            if (p < ln) {
-                if (e == 0 || (p % R2) == 0) {
-                    bsl = (p / R2) * R2;
-                    cl = min(R, ln - bsl);
-                    dl = min(R2, ln - bsl) - cl;
-                    SAccP A{ik, bsl}, B{ik, bsl + cl};
-                    i = (int)merge_path(A, cl, B, dl, p - bsl);
-                    j = (p - bsl) - i;
-                    ctot = ip[pd(bsl + cl - 1)] + (im.src_active(imt[pd(bsl + cl - 1)]) ? 1u : 0u);
-                    dtot = dl > 0 ? ip[pd(bsl + cl + dl - 1)] + (im.src_active(imt[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
-                }
-                const bool takeC = (i < cl) && (j >= dl || ik[pd(bsl + i)] <= ik[pd(bsl + cl + j)]);
-                if (takeC) {
-                    const int s = pd(bsl + i);
-                    const uint32_t other = (j < dl) ? ip[pd(bsl + cl + j)] : dtot;
-                    ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other; oa[e] = ia[s];
-                    ++i;
-                } else {
-                    const int s = pd(bsl + cl + j);
-                    const uint32_t other = (i < cl) ? ip[pd(bsl + i)] : ctot;
-                    ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other;
-                    oa[e] = ia[s] + (im.tgt_active(imt[s]) ? other : 0u);
-                    ++j;
-                }
-                cnt = e + 1;
-            }
-        }
+        const int cnt = dom_merge_level<LIT>(s_key[b], s_meta[b], s_pref[b], s_acc[b], ln, m, p0, ok, om, op, oa,
+                                            [&](uint32_t mt) { return im.src_active(mt); },
+                                            [&](uint32_t mt) { return im.tgt_active(mt); });
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < LIT; ++e) {
@@ -212,46 +246,10 @@ struct DomSmem {
 // slot and class bits through the two predicates.
 template <class SrcF, class TgtF>
 __device__ __forceinline__ void dom_level_smem(DomSmem S, int b, int ln, int m, SrcF src_active, TgtF tgt_active) {
-    const int R = 1 << m, R2 = 2 << m;
-    const uint32_t* ik = S.key + b * NTP;
-    const uint32_t* imt = S.meta + b * NTP;
-    const uint32_t* ip = S.pref + b * NTP;
-    const uint32_t* ia = S.acc + b * NTP;
     uint32_t ok[NTI], om[NTI], op[NTI], oa[NTI];
-    int cnt = 0;
     const int p0 = threadIdx.x * NTI;
-    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
-    uint32_t ctot = 0, dtot = 0;
-#pragma unroll
-    for (int e = 0; e < NTI; ++e) {
-        const int p = p0 + e;
-        if (p < ln) {
-            if (e == 0 || (p % R2) == 0) {
-                bsl = (p / R2) * R2;
-                cl = min(R, ln - bsl);
-                dl = min(R2, ln - bsl) - cl;
-                SAccP A{ik, bsl}, B{ik, bsl + cl};
-                i = (int)merge_path(A, cl, B, dl, p - bsl);
-                j = (p - bsl) - i;
-                ctot = ip[pd(bsl + cl - 1)] + (src_active(imt[pd(bsl + cl - 1)]) ? 1u : 0u);
-                dtot = dl > 0 ? ip[pd(bsl + cl + dl - 1)] + (src_active(imt[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
-            }
-            const bool takeC = (i < cl) && (j >= dl || ik[pd(bsl + i)] <= ik[pd(bsl + cl + j)]);
-            if (takeC) {
-                const int s = pd(bsl + i);
-                const uint32_t other = (j < dl) ? ip[pd(bsl + cl + j)] : dtot;
-                ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other; oa[e] = ia[s];
-                ++i;
-            } else {
-                const int s = pd(bsl + cl + j);
-                const uint32_t other = (i < cl) ? ip[pd(bsl + i)] : ctot;
-                ok[e] = ik[s]; om[e] = imt[s]; op[e] = ip[s] + other;
-                oa[e] = ia[s] + (tgt_active(imt[s]) ? other : 0u);
-                ++j;
-            }
-            cnt = e + 1;
-        }
-    }
+    const int cnt = dom_merge_level<NTI>(S.key + b * NTP, S.meta + b * NTP, S.pref + b * NTP, S.acc + b * NTP, ln, m,
+                                         p0, ok, om, op, oa, src_active, tgt_active);
     uint32_t* wk = S.key + (b ^ 1) * NTP;
     uint32_t* wm = S.meta + (b ^ 1) * NTP;
     uint32_t* wp = S.pref + (b ^ 1) * NTP;
@@ -402,7 +400,7 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
     // tile holds several merged blocks each block is handled from smem).
     const bool big = R2 > GTILE;
     int lc = 0, ldd = 0;
-    uint32_t ctot = 0, dtot = 0, cnext = 0, dnext = 0;
+    uint32_t cnext = 0, dnext = 0;
     if (big) {
         if (threadIdx.x < 64) {
             const int64_t bs = (o0 / R2) * R2;
@@ -454,47 +452,14 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
     }
     __syncthreads();
     const int p0 = threadIdx.x * GI;
-    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
     uint32_t rk[GI], rm[GI], rp[GI], ra[GI];
-    int cnt = 0;
+    const int cnt = dom_merge_level<GI>(s_key, s_meta, s_pref, s_acc, ln, big ? 0 : logR, p0, rk, rm, rp, ra,
+                                        [&](uint32_t mt) { return im.src_active(mt); },
+                                        [&](uint32_t mt) { return im.tgt_active(mt); }, big, lc, cnext, dnext);
+    if (last) {
 #pragma unroll
-    for (int e = 0; e < GI; ++e) {
-        const int p = p0 + e;
-        if (p >= ln) break;
-        if (e == 0 || (!big && (p % (int)R2) == 0)) {
-            if (big) {
-                bsl = 0; cl = lc; dl = ldd;
-                ctot = cnext; dtot = dnext;
-            } else {
-                bsl = (int)((p / R2) * R2);
-                cl = (int)min(R, (int64_t)(ln - bsl));
-                dl = (int)min(R2, (int64_t)(ln - bsl)) - cl;
-                ctot = s_pref[pd(bsl + cl - 1)] + (im.src_active(s_meta[pd(bsl + cl - 1)]) ? 1u : 0u);
-                dtot = dl > 0 ? s_pref[pd(bsl + cl + dl - 1)] + (im.src_active(s_meta[pd(bsl + cl + dl - 1)]) ? 1u : 0u) : 0u;
-            }
-            SAccP A{s_key, bsl}, B{s_key, bsl + cl};
-            i = (int)merge_path(A, cl, B, dl, p - bsl);
-            j = (p - bsl) - i;
-        }
-        const bool takeC = (i < cl) && (j >= dl || s_key[pd(bsl + i)] <= s_key[pd(bsl + cl + j)]);
-        uint32_t k, mt, pf, ac;
-        if (takeC) {
-            const int s = pd(bsl + i);
-            const uint32_t other = (j < dl) ? s_pref[pd(bsl + cl + j)] : dtot;
-            k = s_key[s]; mt = s_meta[s]; pf = s_pref[s] + other; ac = s_acc[s];
-            ++i;
-        } else {
-            const int s = pd(bsl + cl + j);
-            const uint32_t other = (i < cl) ? s_pref[pd(bsl + i)] : ctot;
-            k = s_key[s]; mt = s_meta[s]; pf = s_pref[s] + other;
-            ac = s_acc[s] + (im.tgt_active(mt) ? other : 0u);
-            ++j;
-        }
-        if (last) {
-            if (ac) atomicAdd(C + im.tgt_index(mt & kItemMask), ac);
-        }
-        rk[e] = k; rm[e] = mt; rp[e] = pf; ra[e] = ac;
-        cnt = e + 1;
+        for (int e = 0; e < GI; ++e)
+            if (e < cnt && ra[e]) atomicAdd(C + im.tgt_index(rm[e] & kItemMask), ra[e]);
     }
     if (last) return;
     const int64_t ob = o0 + p0;
