@@ -261,6 +261,49 @@ __device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Po
     __syncthreads();
 }
 
+// Merge of a loaded tile (padded rows): every thread takes MI consecutive
+// outputs from p0.  big: the tile is one merged block, C = [0, lc), D =
+// [lc, ln); otherwise it holds whole merged blocks of R2 (> 1) items.  The
+// keys at the heads of C and D stay in registers, so an output reads only
+// its meta and the key of the head it advances.  eh: 0 from C, 1 from D; sl:
+// the output's slot in the tile.  Returns the outputs made.
+__device__ __forceinline__ int tile_merge(const uint32_t* s_key, const uint32_t* s_meta, int ln, int lc, bool big,
+                                          int64_t R2l, int p0, uint32_t (&ek)[MI], uint32_t (&em)[MI], int (&eh)[MI],
+                                          int (&sl)[MI]) {
+    const int R2 = big ? 1 : (int)R2l;      // runs of a tile-sized merge fit an int
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0, cnt = 0;
+    uint32_t kc = 0, kd = 0;
+#pragma unroll
+    for (int e = 0; e < MI; ++e) {
+        const int p = p0 + e;
+        if (p < ln) {
+            if (e == 0 || (!big && (p % R2) == 0)) {
+                if (big) { bsl = 0; cl = lc; dl = ln - lc; }
+                else { bsl = (p / R2) * R2; cl = min(R2 / 2, ln - bsl); dl = min(R2, ln - bsl) - cl; }
+                MAccP A{s_key, bsl}, B{s_key, bsl + cl};
+                i = (int)merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+                kc = (i < cl) ? s_key[mpd(bsl + i)] : 0u;
+                kd = (j < dl) ? s_key[mpd(bsl + cl + j)] : 0u;
+            }
+            const bool takeC = (i < cl) && (j >= dl || kc <= kd);
+            const int slot = takeC ? bsl + i : bsl + cl + j;
+            ek[e] = takeC ? kc : kd;
+            em[e] = s_meta[mpd(slot)];
+            eh[e] = takeC ? 0 : 1;
+            sl[e] = slot;
+            i += takeC ? 1 : 0;
+            j += takeC ? 0 : 1;
+            const bool v = takeC ? (i < cl) : (j < dl);
+            const uint32_t nk = v ? s_key[mpd(takeC ? bsl + i : bsl + cl + j)] : 0u;
+            kc = takeC ? nk : kc;
+            kd = takeC ? kd : nk;
+            cnt = e + 1;
+        }
+    }
+    return cnt;
+}
+
 // The inputs of one CTA of a merge level in shared memory (padded rows).
 // Runs of 2R longer than a tile (big): the CTA's co-ranks are found by a
 // warp-cooperative merge-path search and its C part [cs, cs+lc) and D part
@@ -397,23 +440,8 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     int eh[MI];
     int cnt = 0;
     {
-        const int64_t p0 = (int64_t)threadIdx.x * MI;
-        int64_t bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
-        for (int e = 0; e < MI; ++e) {
-            const int64_t p = p0 + e;
-            if (p >= ln) break;
-            if (e == 0 || (!big && (p % R2) == 0)) {
-                if (big) { bsl = 0; cl = lc; dl = ln - lc; }
-                else { bsl = (p / R2) * R2; cl = min(R2 / 2, ln - bsl); dl = min(R2, ln - bsl) - cl; }
-                MAccP A{s_key, (int)bsl}, B{s_key, (int)(bsl + cl)};
-                i = merge_path(A, cl, B, dl, p - bsl);
-                j = (p - bsl) - i;
-            }
-            bool takeC = (i < cl) && (j >= dl || s_key[mpd(bsl + i)] <= s_key[mpd(bsl + cl + j)]);
-            if (takeC) { ek[e] = s_key[mpd(bsl + i)]; em[e] = s_meta[mpd(bsl + i)]; eh[e] = 0; ++i; }
-            else { ek[e] = s_key[mpd(bsl + cl + j)]; em[e] = s_meta[mpd(bsl + cl + j)]; eh[e] = 1; ++j; }
-            cnt = e + 1;
-        }
+        int sl[MI];
+        cnt = tile_merge(s_key, s_meta, (int)ln, (int)lc, big, R2, threadIdx.x * MI, ek, em, eh, sl);
     }
     // write merged output (the class bits travel unchanged)
     {
@@ -611,6 +639,7 @@ __device__ __forceinline__ int local_merge(const uint32_t* s_key, const uint32_t
     const int R2 = 2 * R;
     const int p0 = threadIdx.x * IT;
     int bsl = 0, cl = 0, dl = 0, i = 0, j = 0, cnt = 0;
+    uint32_t kc = 0, kd = 0;     // keys at the heads of C and D (kept in registers)
 #pragma unroll
     for (int e = 0; e < IT; ++e) {
         const int p = p0 + e;
@@ -622,13 +651,20 @@ __device__ __forceinline__ int local_merge(const uint32_t* s_key, const uint32_t
                 LAccP A{s_key, bsl}, B{s_key, bsl + cl};
                 i = (int)merge_path(A, cl, B, dl, p - bsl);
                 j = (p - bsl) - i;
+                kc = (i < cl) ? s_key[lpd(bsl + i)] : 0u;
+                kd = (j < dl) ? s_key[lpd(bsl + cl + j)] : 0u;
             }
-            const bool takeC = (i < cl) && (j >= dl || s_key[lpd(bsl + i)] <= s_key[lpd(bsl + cl + j)]);
+            const bool takeC = (i < cl) && (j >= dl || kc <= kd);
             const int src = takeC ? lpd(bsl + i) : lpd(bsl + cl + j);
-            ek[e] = s_key[src];
+            ek[e] = takeC ? kc : kd;
             em[e] = s_meta[src];
             eh[e] = (uint32_t)s_home[src] | (takeC ? 0u : 0x10000u);
-            if (takeC) ++i; else ++j;
+            i += takeC ? 1 : 0;
+            j += takeC ? 0 : 1;
+            const bool v = takeC ? (i < cl) : (j < dl);
+            const uint32_t nk = v ? s_key[takeC ? lpd(bsl + i) : lpd(bsl + cl + j)] : 0u;
+            kc = takeC ? nk : kc;
+            kd = takeC ? kd : nk;
             cnt = e + 1;
         }
     }
@@ -1206,28 +1242,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
     int eh[MI], es[MI];      // half, and the shared-memory slot the element came from
     int cnt = 0;
     const int64_t p0 = (int64_t)threadIdx.x * MI;
-    {
-        int64_t bsl = 0, cl = 0, dl = 0, i = 0, j = 0;
-        for (int e = 0; e < MI; ++e) {
-            const int64_t p = p0 + e;
-            if (p >= ln) break;
-            if (e == 0 || (!big && (p % R2) == 0)) {
-                if (big) { bsl = 0; cl = lc; dl = ln - lc; }
-                else { bsl = (p / R2) * R2; cl = min(R2 / 2, ln - bsl); dl = min(R2, ln - bsl) - cl; }
-                MAccP A{s_key, (int)bsl}, B{s_key, (int)(bsl + cl)};
-                i = merge_path(A, cl, B, dl, p - bsl);
-                j = (p - bsl) - i;
-            }
-            const bool takeC = (i < cl) && (j >= dl || s_key[mpd(bsl + i)] <= s_key[mpd(bsl + cl + j)]);
-            const int slot = (int)(takeC ? bsl + i : bsl + cl + j);
-            ek[e] = s_key[mpd(slot)];
-            em[e] = s_meta[mpd(slot)];
-            eh[e] = takeC ? 0 : 1;
-            es[e] = slot;
-            if (takeC) ++i; else ++j;
-            cnt = e + 1;
-        }
-    }
+    cnt = tile_merge(s_key, s_meta, (int)ln, (int)lc, big, R2, (int)p0, ek, em, eh, es);
     if (!last) {
         const int64_t q0 = o0 + p0;
         if (cnt == MI) {
