@@ -863,11 +863,12 @@ struct FastLO {
 
 // Per-tile references of the scaled form.  Returns (uniformly over the CTA)
 // whether the tile qualifies; if so, s_fm[4 i + 2 h + dir] has been replaced
-// by F(h, dir) 2^{-R[dir][h][c]} (c = the item's class) and s_ref[(2 h + dir)
-// * NCLS + c] holds R.  s_fs (the shifts) is left as it was.
-template <int CLSB, int NT>
-__device__ __forceinline__ bool fold_fast_setup(const uint32_t* s_meta, float* s_fm, const int* s_fs,
-                                                const float* s_wt, int ln, int* s_ref) {
+// by F(h, dir) 2^{-R[dir][h][c]} (c = cls_of(i), the class of home slot i)
+// and s_ref[(2 h + dir) * NCLS + c] holds R.  s_fs (the shifts) is left as it
+// was.
+template <int CLSB, int NT, class ClsOf>
+__device__ __forceinline__ bool fold_fast_setup(ClsOf cls_of, float* s_fm, const int* s_fs, const float* s_wt, int ln,
+                                                int* s_ref) {
     constexpr int NCLS = 1 << CLSB, NS = 4 * NCLS;
     __shared__ int s_lo[NS], s_hi[NS], s_wr[2], s_ok;
     for (int i = threadIdx.x; i < NS; i += NT) { s_lo[i] = INT_MAX; s_hi[i] = INT_MIN; }
@@ -877,7 +878,7 @@ __device__ __forceinline__ bool fold_fast_setup(const uint32_t* s_meta, float* s
 #pragma unroll
     for (int q = 0; q < NS; ++q) { lo[q] = INT_MAX; hi[q] = INT_MIN; }
     for (int i = threadIdx.x; i < ln; i += NT) {
-        const int c = (int)(s_meta[lpd(i)] >> kItemBits);
+        const int c = cls_of(i);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int e = s_fs[4 * i + j];
@@ -937,12 +938,146 @@ __device__ __forceinline__ bool fold_fast_setup(const uint32_t* s_meta, float* s
     __syncthreads();
     if (!s_ok) return false;
     for (int i = threadIdx.x; i < ln; i += NT) {
-        const int c = (int)(s_meta[lpd(i)] >> kItemBits);
+        const int c = cls_of(i);
 #pragma unroll
         for (int j = 0; j < 4; ++j) s_fm[4 * i + j] *= pow2f_any(s_fs[4 * i + j] - s_ref[j * NCLS + c]);
     }
     __syncthreads();
     return true;
+}
+
+// The tile-local merge levels of the folded kernel sums on a loaded tile
+// (keys, metas and home slots in padded shared-memory rows; per-home factors,
+// weights and target sums): `levels` merge levels with the forward and
+// backward channel sweeps, each target adding its kernel values to s_fa.
+// FAST: the scaled FP32 form (fold_fast_setup has scaled s_fm); else the
+// shifted form.  Used by k_local_fold and k_nested_fold.
+template <class Pol, int CLSB, int NT, int IT, bool FAST>
+__device__ __forceinline__ void fold_tile_levels(uint32_t* s_key, uint32_t* s_meta, uint16_t* s_home,
+                                                 const typename Pol::M* s_fm, const int* s_fs,
+                                                 const typename Pol::M* s_wt, typename Pol::FA* s_fa, void* s_scan_v,
+                                                 int ln, int levels, const Pol& pol) {
+    typedef typename Pol::LOps LO;
+    typedef typename Pol::M M;
+    constexpr int NW = Pol::kNW;
+    constexpr int NCH = 2 << CLSB;
+    typedef typename std::conditional<FAST, FastLO<NW>, LO>::type LX;
+    typedef typename LX::V VX;
+    VX* s_scan = reinterpret_cast<VX*>(s_scan_v);
+    // kernel value of a running sum v read with factor (m, s), per weight channel
+    auto value = [&](const VX& v, M mm, int sh, M* c) {
+        if constexpr (FAST) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) c[q] = v.v[q] * mm;
+        } else {
+            Pol::fold_value(v, mm, sh, c);
+        }
+    };
+    // source term of an element (weight channel 1 of two-channel sums: 1 for sources)
+    auto term = [&](M mm, int sh, M w, bool src) -> VX {
+        if constexpr (FAST) {
+            VX r;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) r.v[q] = ((NW == 2 && q == 1) ? (src ? (M)1 : (M)0) : w) * mm;
+            return r;
+        } else {
+            return Pol::fold_src(mm, sh, w, src);
+        }
+    };
+    for (int m = 0; m < levels; ++m) {
+        const int R2 = 2 << m;
+        uint32_t ek[IT], em[IT], eh[IT];
+        const int cnt = local_merge<IT>(s_key, s_meta, s_home, ln, 1 << m, ek, em, eh);
+        // factors F(h, +) (index 0) and F(h, -) (index 1) of each element
+        M f0[IT], f1[IT], wt[IT];
+        int g0[IT], g1[IT];
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+            f0[e] = f1[e] = wt[e] = (M)0;
+            g0[e] = g1[e] = 0;
+            if (e < cnt) {
+                // F(h, +) and F(h, -) are adjacent (b even): one vector load each
+                const int b = 4 * (int)(eh[e] & 0xffffu) + 2 * (int)(eh[e] >> 16);
+                if constexpr (sizeof(M) == 4) {
+                    const float2 f = *reinterpret_cast<const float2*>(s_fm + b);
+                    f0[e] = f.x;
+                    f1[e] = f.y;
+                } else {
+                    const double2 f = *reinterpret_cast<const double2*>(s_fm + b);
+                    f0[e] = f.x;
+                    f1[e] = f.y;
+                }
+                if constexpr (!FAST) {
+                    const int2 g = *reinterpret_cast<const int2*>(s_fs + b);
+                    g0[e] = g.x;
+                    g1[e] = g.y;
+                }
+                wt[e] = s_wt[eh[e] & 0xffffu];
+            }
+        }
+        const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
+        const int p0 = threadIdx.x * IT;
+        // Walks from zero over the thread's elements (a thread's elements lie
+        // in one merged block when ts > 1): kernel values of the thread-local
+        // prefix (forward, with F(h, -) of the target) and suffix (backward,
+        // F(h, +)); the walks end with the thread's channel totals.
+        M cf[IT][NW], cb[IT][NW];
+        VX fe[NCH], be[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) { fe[c] = LX::zero(); be[c] = LX::zero(); }
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
+            if (e < cnt) {
+                if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) fe[c] = LX::zero();
+                }
+                const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
+                add_at<LX>(fe, own, term(f0[e], g0[e], wt[e], pol.is_src(em[e] & kItemMask)));
+            }
+        }
+#pragma unroll
+        for (int e = IT - 1; e >= 0; --e) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) cb[e][q] = (M)0;
+            if (e < cnt) {
+                if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) be[c] = LX::zero();
+                }
+                const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
+                value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
+                add_at<LX>(be, own, term(f1[e], g1[e], wt[e], pol.is_src(em[e] & kItemMask)));
+            }
+        }
+        // blocks spanning several threads: the exclusive prefix / suffix of
+        // the thread totals joins every element (the fold is linear)
+        if (ts > 1) {
+            seg_scan<LX, NCH, NT>(fe, be, ts, s_scan);
+#pragma unroll
+            for (int e = 0; e < IT; ++e) {
+                if (e < cnt) {
+                    const int opp = ((int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits)) ^ (NCH - 1);
+                    M xf[NW], xb[NW];
+                    value(pick(fe, opp), f1[e], g1[e], xf);
+                    value(pick(be, opp), f0[e], g0[e], xb);
+#pragma unroll
+                    for (int q = 0; q < NW; ++q) { cf[e][q] += xf[q]; cb[e][q] += xb[q]; }
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < IT; ++e)
+            if (e < cnt && pol.is_tgt(em[e] & kItemMask)) {
+                M sf, sb;
+                pol.signs((int)(eh[e] >> 16), em[e] >> kItemBits, sf, sb);
+                Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e], sf, sb);
+            }
+        local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
+    }
 }
 
 template <class Pol, int CLSB, bool HALF>
@@ -991,122 +1126,17 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT, (LocalCfg
     // Scaled FP32 form when the tile's factors allow it (mixed path only).
     __shared__ int s_ref[4 << CLSB];
     bool fast = false;
-    if constexpr (Pol::kFastLocal) fast = fold_fast_setup<CLSB, NT>(s_meta, s_fm, s_fs, s_wt, ln, s_ref);
-    auto run_levels = [&](auto fast_tag) {
-        constexpr bool FAST = decltype(fast_tag)::value;
-        typedef typename std::conditional<FAST, FastLO<NW>, LO>::type LX;
-        typedef typename LX::V VX;
-        // kernel value of a running sum v read with factor (m, s), per weight channel
-        auto value = [&](const VX& v, M mm, int sh, M* c) {
-            if constexpr (FAST) {
-#pragma unroll
-                for (int q = 0; q < NW; ++q) c[q] = v.v[q] * mm;
-            } else {
-                Pol::fold_value(v, mm, sh, c);
-            }
-        };
-        // source term of an element (weight channel 1 of two-channel sums: 1 for sources)
-        auto term = [&](M mm, int sh, M w, bool src) -> VX {
-            if constexpr (FAST) {
-                VX r;
-#pragma unroll
-                for (int q = 0; q < NW; ++q) r.v[q] = ((NW == 2 && q == 1) ? (src ? (M)1 : (M)0) : w) * mm;
-                return r;
-            } else {
-                return Pol::fold_src(mm, sh, w, src);
-            }
-        };
-        for (int m = 0; m < levels; ++m) {
-            const int R2 = 2 << m;
-            uint32_t ek[IT], em[IT], eh[IT];
-            const int cnt = local_merge<IT>(s_key, s_meta, s_home, ln, 1 << m, ek, em, eh);
-            // factors F(h, +) (index 0) and F(h, -) (index 1) of each element
-            M f0[IT], f1[IT], wt[IT];
-            int g0[IT], g1[IT];
-#pragma unroll
-            for (int e = 0; e < IT; ++e) {
-                f0[e] = f1[e] = wt[e] = (M)0;
-                g0[e] = g1[e] = 0;
-                if (e < cnt) {
-                    const int b = 4 * (int)(eh[e] & 0xffffu) + 2 * (int)(eh[e] >> 16);
-                    f0[e] = s_fm[b];
-                    f1[e] = s_fm[b + 1];
-                    if constexpr (!FAST) {
-                        g0[e] = s_fs[b];
-                        g1[e] = s_fs[b + 1];
-                    }
-                    wt[e] = s_wt[eh[e] & 0xffffu];
-                }
-            }
-            const int ts = R2 / IT;   // threads per merged block (0 or 1: thread-local)
-            const int p0 = threadIdx.x * IT;
-            // Walks from zero over the thread's elements (a thread's elements lie
-            // in one merged block when ts > 1): kernel values of the thread-local
-            // prefix (forward, with F(h, -) of the target) and suffix (backward,
-            // F(h, +)); the walks end with the thread's channel totals.
-            M cf[IT][NW], cb[IT][NW];
-            VX fe[NCH], be[NCH];
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) { fe[c] = LX::zero(); be[c] = LX::zero(); }
-#pragma unroll
-            for (int e = 0; e < IT; ++e) {
-#pragma unroll
-                for (int q = 0; q < NW; ++q) cf[e][q] = (M)0;
-                if (e < cnt) {
-                    if (ts <= 1 && e > 0 && ((p0 + e) % R2) == 0) {
-#pragma unroll
-                        for (int c = 0; c < NCH; ++c) fe[c] = LX::zero();
-                    }
-                    const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
-                    value(pick(fe, own ^ (NCH - 1)), f1[e], g1[e], cf[e]);
-                    add_at<LX>(fe, own, term(f0[e], g0[e], wt[e], pol.is_src(em[e] & kItemMask)));
-                }
-            }
-#pragma unroll
-            for (int e = IT - 1; e >= 0; --e) {
-#pragma unroll
-                for (int q = 0; q < NW; ++q) cb[e][q] = (M)0;
-                if (e < cnt) {
-                    if (ts <= 1 && e < cnt - 1 && ((p0 + e + 1) % R2) == 0) {
-#pragma unroll
-                        for (int c = 0; c < NCH; ++c) be[c] = LX::zero();
-                    }
-                    const int own = (int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits);
-                    value(pick(be, own ^ (NCH - 1)), f0[e], g0[e], cb[e]);
-                    add_at<LX>(be, own, term(f1[e], g1[e], wt[e], pol.is_src(em[e] & kItemMask)));
-                }
-            }
-            // blocks spanning several threads: the exclusive prefix / suffix of
-            // the thread totals joins every element (the fold is linear)
-            if (ts > 1) {
-                seg_scan<LX, NCH, NT>(fe, be, ts, reinterpret_cast<VX*>(s_scan));
-#pragma unroll
-                for (int e = 0; e < IT; ++e) {
-                    if (e < cnt) {
-                        const int opp = ((int)((eh[e] >> 16) << CLSB) | (int)(em[e] >> kItemBits)) ^ (NCH - 1);
-                        M xf[NW], xb[NW];
-                        value(pick(fe, opp), f1[e], g1[e], xf);
-                        value(pick(be, opp), f0[e], g0[e], xb);
-#pragma unroll
-                        for (int q = 0; q < NW; ++q) { cf[e][q] += xf[q]; cb[e][q] += xb[q]; }
-                    }
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < IT; ++e)
-                if (e < cnt && pol.is_tgt(em[e] & kItemMask)) {
-                    M sf, sb;
-                    pol.signs((int)(eh[e] >> 16), em[e] >> kItemBits, sf, sb);
-                    Pol::fold_add(s_fa + NW * (eh[e] & 0xffffu), cf[e], cb[e], sf, sb);
-                }
-            local_store<IT>(s_key, s_meta, s_home, cnt, ek, em, eh);
-        }
-    };
+    if constexpr (Pol::kFastLocal)   // home slot i sits at position i at this point
+        fast = fold_fast_setup<CLSB, NT>([&](int i) { return (int)(s_meta[lpd(i)] >> kItemBits); }, s_fm, s_fs, s_wt,
+                                         ln, s_ref);
     if constexpr (Pol::kFastLocal) {
-        if (fast) run_levels(std::true_type{});
-        else run_levels(std::false_type{});
+        if (fast) fold_tile_levels<Pol, CLSB, NT, IT, true>(s_key, s_meta, s_home, s_fm, s_fs, s_wt, s_fa, s_scan, ln,
+                                                            levels, pol);
+        else fold_tile_levels<Pol, CLSB, NT, IT, false>(s_key, s_meta, s_home, s_fm, s_fs, s_wt, s_fa, s_scan, ln,
+                                                        levels, pol);
     } else {
-        run_levels(std::false_type{});
+        fold_tile_levels<Pol, CLSB, NT, IT, false>(s_key, s_meta, s_home, s_fm, s_fs, s_wt, s_fa, s_scan, ln, levels,
+                                                   pol);
     }
     // write the tile out for the longer merge levels (as records when they
     // run on records); targets not handed on as records are flushed
@@ -1136,6 +1166,158 @@ __global__ void __launch_bounds__(LocalCfg<Pol, CLSB, true, HALF>::NT, (LocalCfg
         } else if (pol.is_tgt(item)) {
             pol.fold_flush(item, s_fa + NW * h);
         }
+    }
+}
+
+// ------------------------------------------------------------------ nested outer levels
+// The outer levels of tree axis 2 whose nodes (2^{l+1} items) fit a tile of
+// NFT items, nested in one launch (the kernel-sum counterpart of the
+// counting engine's k_dom_nested).  A CTA loads its tile once; for each outer
+// level l it merges the outer state by P_1 (the tree of Algorithms 3/4) in
+// shared memory and runs that level's complete inner folded sweep (l + 1
+// merge levels by P_0) on it; the targets' kernel values are summed in shared
+// memory over all these levels and flushed once.  The side bit of axis 2 at
+// level l is bit l of the item's slot in the tile (tiles start at multiples
+// of NFT inside the enclosing nodes); the enclosing axes' bits (class bits
+// 1 and up) are fixed per item.  The per-item factors depend on the class, so
+// they are recomputed for every level.  The outer state itself is built by
+// the regular merges (so the longer levels need not wait for this kernel).
+constexpr int NFT = 1024;          // items per tile
+constexpr int NFN = 256;           // threads
+constexpr int NFI = NFT / NFN;     // items per thread
+
+template <class Pol, int CLSB>
+struct NestedCfg {
+    typedef typename Pol::M M;
+    typedef typename Pol::FA FA;
+    typedef typename Pol::LOps::V V;
+    static constexpr int TP = NFT + NFT / 32;
+    static constexpr size_t a16(size_t x) { return (x + 15) / 16 * 16; }
+    static constexpr size_t o_item = 0;                                   // [NFT] item of each slot
+    static constexpr size_t o_p0 = o_item + 4 * NFT;                      // [NFT] P_0 of each slot
+    static constexpr size_t o_cenc = o_p0 + 4 * NFT;                      // [NFT] enclosing class bits
+    static constexpr size_t o_okey = o_cenc + 4 * NFT;                    // [2][TP] outer state: P_1
+    static constexpr size_t o_oslot = o_okey + 8 * (size_t)TP;            // [2][TP] outer state: slot
+    static constexpr size_t o_key = o_oslot + 8 * (size_t)TP;             // [TP] inner keys
+    static constexpr size_t o_meta = o_key + 4 * (size_t)TP;              // [TP] inner metas
+    static constexpr size_t o_home = o_meta + 4 * (size_t)TP;             // [TP] inner home slots (u16)
+    static constexpr size_t o_fm = a16(o_home + 2 * (size_t)TP);          // [NFT][4] factor mantissas
+    static constexpr size_t o_fs = o_fm + 4 * sizeof(M) * NFT;            // [NFT][4] factor shifts
+    static constexpr size_t o_wt = o_fs + 16 * (size_t)NFT;               // [NFT] source weights
+    static constexpr size_t o_fa = a16(o_wt + sizeof(M) * NFT);           // [NFT][NW] target sums
+    static constexpr size_t o_scan = a16(o_fa + sizeof(FA) * Pol::kNW * NFT);
+    static constexpr size_t bytes = o_scan + 2 * (2 << CLSB) * (NFN / 32) * sizeof(V);
+};
+
+// One plain merge level (runs 2^m -> 2^{m+1}) of (key, slot) pairs in padded
+// shared-memory rows; every thread takes NFI consecutive outputs.
+__device__ __forceinline__ void nested_outer_merge(const uint32_t* ik, const uint32_t* is, uint32_t* wk, uint32_t* ws,
+                                                   int ln, int m) {
+    const int R = 1 << m, R2 = 2 << m;
+    const int p0 = threadIdx.x * NFI;
+    uint32_t ok[NFI], os[NFI];
+    int bsl = 0, cl = 0, dl = 0, i = 0, j = 0, cnt = 0;
+#pragma unroll
+    for (int e = 0; e < NFI; ++e) {
+        const int p = p0 + e;
+        if (p < ln) {
+            if (e == 0 || (p % R2) == 0) {
+                bsl = (p / R2) * R2;
+                cl = min(R, ln - bsl);
+                dl = min(R2, ln - bsl) - cl;
+                LAccP A{ik, bsl}, B{ik, bsl + cl};
+                i = (int)merge_path(A, cl, B, dl, p - bsl);
+                j = (p - bsl) - i;
+            }
+            const bool takeC = (i < cl) && (j >= dl || ik[lpd(bsl + i)] <= ik[lpd(bsl + cl + j)]);
+            const int src = takeC ? lpd(bsl + i) : lpd(bsl + cl + j);
+            ok[e] = ik[src];
+            os[e] = is[src];
+            i += takeC ? 1 : 0;
+            j += takeC ? 0 : 1;
+            cnt = e + 1;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < NFI; ++e)
+        if (e < cnt) { wk[lpd(p0 + e)] = ok[e]; ws[lpd(p0 + e)] = os[e]; }
+}
+
+template <class Pol, int CLSB>
+__global__ void __launch_bounds__(NFN) k_nested_fold(const uint32_t* __restrict__ seq, int64_t n,
+                                                     const uint32_t* __restrict__ P0, const uint32_t* __restrict__ P1,
+                                                     ClassSpecK cs, int levels, Pol pol) {
+    typedef NestedCfg<Pol, CLSB> Cfg;
+    typedef typename Pol::M M;
+    typedef typename Pol::FA FA;
+    constexpr int NW = Pol::kNW;
+    constexpr int TP = Cfg::TP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t* s_item = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_item);
+    uint32_t* s_p0 = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_p0);
+    uint32_t* s_cenc = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_cenc);
+    uint32_t* s_okey = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_okey);
+    uint32_t* s_oslot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_oslot);
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_key);
+    uint32_t* s_meta = reinterpret_cast<uint32_t*>(smem_raw + Cfg::o_meta);
+    uint16_t* s_home = reinterpret_cast<uint16_t*>(smem_raw + Cfg::o_home);
+    M* s_fm = reinterpret_cast<M*>(smem_raw + Cfg::o_fm);
+    int* s_fs = reinterpret_cast<int*>(smem_raw + Cfg::o_fs);
+    M* s_wt = reinterpret_cast<M*>(smem_raw + Cfg::o_wt);
+    FA* s_fa = reinterpret_cast<FA*>(smem_raw + Cfg::o_fa);
+    void* s_scan = smem_raw + Cfg::o_scan;
+    __shared__ int s_ref[4 << CLSB];
+
+    const int64_t t0 = (int64_t)blockIdx.x * NFT;
+    const int ln = (int)min((int64_t)NFT, n - t0);
+    for (int i = threadIdx.x; i < ln; i += NFN) {
+        const uint32_t item = seq[t0 + i];
+        uint32_t c = 0;
+        for (int q = 1; q < cs.nb; ++q) c |= ((cs.idx[q][item] >> cs.lvl[q]) & 1u) << q;
+        s_item[i] = item;
+        s_p0[i] = P0[item];
+        s_cenc[i] = c;
+        s_okey[lpd(i)] = P1[item];
+        s_oslot[lpd(i)] = (uint32_t)i;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) s_fa[NW * i + q] = Pol::fa_zero();
+    }
+    __syncthreads();
+    int ob = 0;
+    for (int l = 0; l < levels; ++l) {
+        nested_outer_merge(s_okey + ob * TP, s_oslot + ob * TP, s_okey + (ob ^ 1) * TP, s_oslot + (ob ^ 1) * TP, ln,
+                           l);
+        __syncthreads();
+        ob ^= 1;
+        // this level's inner tile (outer order) and the factors of its classes
+        for (int p = threadIdx.x; p < ln; p += NFN) {
+            const uint32_t sl = s_oslot[ob * TP + lpd(p)];
+            const uint32_t cls = ((sl >> l) & 1u) | s_cenc[sl];
+            s_key[lpd(p)] = s_p0[sl];
+            s_meta[lpd(p)] = s_item[sl] | (cls << kItemBits);
+            s_home[lpd(p)] = (uint16_t)sl;
+        }
+        for (int i = threadIdx.x; i < ln; i += NFN) {
+            const uint32_t item = s_item[i];
+            const uint32_t cls = (((uint32_t)i >> l) & 1u) | s_cenc[i];
+            M wt;
+            pol.fold_item(item, cls, &s_fm[4 * i], &s_fs[4 * i], wt);
+            s_wt[i] = pol.is_src(item) ? wt : (M)0;
+        }
+        __syncthreads();
+        bool fast = false;
+        if constexpr (Pol::kFastLocal)
+            fast = fold_fast_setup<CLSB, NFN>([&](int i) { return (int)((((uint32_t)i >> l) & 1u) | s_cenc[i]); },
+                                              s_fm, s_fs, s_wt, ln, s_ref);
+        if (fast) fold_tile_levels<Pol, CLSB, NFN, NFI, Pol::kFastLocal>(s_key, s_meta, s_home, s_fm, s_fs, s_wt, s_fa,
+                                                                        s_scan, ln, l + 1, pol);
+        else fold_tile_levels<Pol, CLSB, NFN, NFI, false>(s_key, s_meta, s_home, s_fm, s_fs, s_wt, s_fa, s_scan, ln,
+                                                          l + 1, pol);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ln; i += NFN) {
+        const uint32_t item = s_item[i];
+        if (pol.is_tgt(item)) pol.fold_flush(item, s_fa + NW * i);
     }
 }
 

@@ -813,6 +813,35 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         idx = o.idx;
     }
     FK_TRY(gather_outer(seq, n, P[k - 1], o.k[0], o.m[0], st));
+    // Outer levels of axis 2 whose nodes fit a tile (folded sums on records,
+    // whose flushes are atomic): their inner sorts run in one launch of
+    // k_nested_fold, beside the merges and the inner sorts of the longer
+    // levels (on a stream of its own when the levels run concurrently).
+    int l0 = 0;
+    if constexpr (Pol::kCanFold && Pol::kRecords && CLSB <= 2) {
+        if (k == 2 && !pol.terms) {
+            int lt = 0;
+            while ((2 << lt) <= NFT) ++lt;
+            l0 = E < lt ? E : lt;
+        }
+    }
+    auto launch_nested = [&](cudaStream_t s2) -> fk_status {
+        if constexpr (Pol::kCanFold && Pol::kRecords && CLSB <= 2) {
+            typedef NestedCfg<Pol, CLSB> NC;
+            static bool attr_set = false;
+            if (!attr_set) {
+                FK_CUDA(cudaFuncSetAttribute(k_nested_fold<Pol, CLSB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)NC::bytes));
+                attr_set = true;
+            }
+            const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
+                                  (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes);
+            ProfScope ps(PF_KLOCAL, (double)n * (l0 * (l0 + 1) / 2) * kKernelOpsPerItemLevel, s2, l0 * lbytes);
+            k_nested_fold<Pol, CLSB><<<grid_for(n, NFT), NFN, NC::bytes, s2>>>(seq, n, P[0], P[1], cs, l0, pol);
+            FK_LAUNCH_CHECK();
+        }
+        return FK_OK;
+    };
     auto class_of_level = [&](int l) {
         ClassSpec c2 = cs;
         // the enclosing axes keep their bits; axis k contributes bit (k - 2)
@@ -828,10 +857,11 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         // that last read the state it overwrites.
         const int R = S + 1;
         StreamFork fork;
-        FK_TRY(fork.begin(2, st, S));
+        FK_TRY(fork.begin(2, st, S + (l0 > 0 ? 1 : 0)));
         cudaEvent_t ready = fork.ev[0];
         cudaEvent_t* done = fork.ev + 1;
         fk_status rc = FK_OK;
+        if (l0 > 0) rc = launch_nested(fork.s[S]);
         for (int l = 0; l < E && rc == FK_OK; ++l) {
             const int in = l % R, out = (l + 1) % R;
             if (l >= R) {
@@ -841,6 +871,12 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
             MergeArgs a{o.k[in], o.m[in], o.k[out], o.m[out], n, l};
             rc = plain_merge_level(a, st);
             if (rc != FK_OK) break;
+            if (l < l0) {
+                // inner sort done by k_nested_fold: nothing reads this state
+                const cudaError_t e = cudaEventRecord(done[l % R], st);
+                if (e != cudaSuccess) rc = cuda_error(e, "level done");
+                continue;
+            }
             const int q = l % S;
             cudaError_t e = cudaEventRecord(ready, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(fork.s[q], ready, 0);
@@ -858,11 +894,13 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         const fk_status rj = fork.end();
         return rc != FK_OK ? rc : rj;
     }
+    if (l0 > 0) FK_TRY(launch_nested(st));
     int cur = 0;
     for (int l = 0; l < E; ++l) {
         MergeArgs a{o.k[cur], o.m[cur], o.k[cur ^ 1], o.m[cur ^ 1], n, l};
         FK_TRY(plain_merge_level(a, st));
         cur ^= 1;
+        if (l < l0) continue;   // inner sort done by k_nested_fold
         FK_TRY((recurse<Pol, CLSB>(k - 1, o.m[cur], n, l + 1, P, class_of_level(l), pol, ob, ib, S, opts, st)));
     }
     return FK_OK;
