@@ -996,21 +996,12 @@ __device__ __forceinline__ void fold_tile_levels(uint32_t* s_key, uint32_t* s_me
             f0[e] = f1[e] = wt[e] = (M)0;
             g0[e] = g1[e] = 0;
             if (e < cnt) {
-                // F(h, +) and F(h, -) are adjacent (b even): one vector load each
                 const int b = 4 * (int)(eh[e] & 0xffffu) + 2 * (int)(eh[e] >> 16);
-                if constexpr (sizeof(M) == 4) {
-                    const float2 f = *reinterpret_cast<const float2*>(s_fm + b);
-                    f0[e] = f.x;
-                    f1[e] = f.y;
-                } else {
-                    const double2 f = *reinterpret_cast<const double2*>(s_fm + b);
-                    f0[e] = f.x;
-                    f1[e] = f.y;
-                }
+                f0[e] = s_fm[b];
+                f1[e] = s_fm[b + 1];
                 if constexpr (!FAST) {
-                    const int2 g = *reinterpret_cast<const int2*>(s_fs + b);
-                    g0[e] = g.x;
-                    g1[e] = g.y;
+                    g0[e] = s_fs[b];
+                    g1[e] = s_fs[b + 1];
                 }
                 wt[e] = s_wt[eh[e] & 0xffffu];
             }
