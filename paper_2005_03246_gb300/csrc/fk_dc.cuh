@@ -112,6 +112,20 @@ __device__ __forceinline__ void add_at(typename Pol::V (&a)[N], int c, const typ
     for (int k = 0; k < N; ++k) a[k] = sel_t(c == k, s, a[k]);
 }
 
+// Asynchronous 8-byte global -> shared copies (cp.async): a thread waits only
+// for its own copies, so no barrier is needed when it reads back only what it
+// copied.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Merge path: number of elements taken from A among the first q outputs of a
 // stable merge (A first on ties) of sorted A[0,la) and B[0,lb).
 template <class Acc>
@@ -362,20 +376,22 @@ __device__ __forceinline__ MergeTile merge_tile_load(const MergeArgs& a, uint32_
         t.cs = s_co[0];
         t.ds = s_co[2];
         t.ldd = s_co[3];
-        for (int64_t i = threadIdx.x; i < t.lc; i += MT) {
-            s_key[mpd(i)] = a.key_in[t.cs + i];
-            s_meta[mpd(i)] = a.meta_in[t.cs + i];
-        }
-        for (int64_t i = threadIdx.x; i < t.ldd; i += MT) {
-            s_key[mpd(t.lc + i)] = a.key_in[t.ds + i];
-            s_meta[mpd(t.lc + i)] = a.meta_in[t.ds + i];
-        }
-    } else {
-        for (int64_t i = threadIdx.x; i < t.ln; i += MT) {
-            s_key[mpd(i)] = a.key_in[o0 + i];
-            s_meta[mpd(i)] = a.meta_in[o0 + i];
+    }
+    // Tile slot i holds C element i (i < lc) or D element i - lc; a tile of
+    // whole runs is the contiguous range from o0.  Asynchronous copies: every
+    // thread has all its slots in flight at once, so the tile arrives in one
+    // memory round trip without staging through registers.
+#pragma unroll
+    for (int j = 0; j < MI; ++j) {
+        const int i = (int)threadIdx.x + j * MT;
+        const int64_t g = !t.big ? o0 + i : (i < t.lc ? t.cs + i : t.ds + (i - t.lc));
+        if (i < t.ln) {
+            cp_async4(&s_key[mpd(i)], &a.key_in[g]);
+            cp_async4(&s_meta[mpd(i)], &a.meta_in[g]);
         }
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
     return t;
 }
@@ -1369,6 +1385,10 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
     __shared__ uint32_t s_meta[MP];
     __shared__ int64_t s_co[6];
     __shared__ V s_scan[2 * NCH * (MT / 32)];
+    // the sweep's running target sums, copied in asynchronously while the
+    // walks and the scan run (8-byte sums only; others are read at the end)
+    constexpr bool kPreFA = PHASE == PH_SWEEP && sizeof(FA) * NW == 8;
+    __shared__ __align__(8) FA s_fa[kPreFA ? MTILE * NW : 1];
 
     const int64_t n = a.n;
     const int64_t R2 = (int64_t)2 << a.logR;
@@ -1382,17 +1402,32 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
         V tf[NCH], tb[NCH];
 #pragma unroll
         for (int c = 0; c < NCH; ++c) { tf[c] = Pol::zero(); tb[c] = Pol::zero(); }
-        for (int64_t i = threadIdx.x; i < ln; i += MT) {
-            const uint32_t m = s_meta[mpd(i)];
-            if (pol.is_src(m & kItemMask)) {
+        // the thread's slots in batches of TB: all record loads of a batch
+        // are issued before its first sum
+        constexpr int TB = MI / 2;
+#pragma unroll
+        for (int j0 = 0; j0 < MI; j0 += TB) {
+            M f0[TB], f1[TB], wt[TB];
+            int g0[TB], g1[TB], ch[TB];
+            bool sv[TB];
+#pragma unroll
+            for (int j = 0; j < TB; ++j) {
+                const int i = (int)threadIdx.x + (j0 + j) * MT;
+                const uint32_t m = i < ln ? s_meta[mpd(i)] : 0u;
                 const int half = (i >= lc) ? 1 : 0;
-                const int64_t g = half ? mt.ds + (i - lc) : mt.cs + i;
-                M f0, f1, wt;
-                int g0, g1;
-                rec_move<Pol>(rin, g, rin, -1, half, f0, f1, g0, g1, wt);
-                const int ch = (half << CLSB) | (int)(m >> kItemBits);
-                add_at<Pol>(tf, ch, Pol::fold_src_g(f0, g0, wt, true));
-                add_at<Pol>(tb, ch, Pol::fold_src_g(f1, g1, wt, true));
+                sv[j] = i < ln && pol.is_src(m & kItemMask);
+                ch[j] = (half << CLSB) | (int)(m >> kItemBits);
+                f0[j] = f1[j] = wt[j] = (M)0;
+                g0[j] = g1[j] = 0;
+                if (sv[j]) rec_move<Pol>(rin, half ? mt.ds + (i - lc) : mt.cs + i, rin, -1, half, f0[j], f1[j],
+                                         g0[j], g1[j], wt[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < TB; ++j) {
+                if (sv[j]) {
+                    add_at<Pol>(tf, ch[j], Pol::fold_src_g(f0[j], g0[j], wt[j], true));
+                    add_at<Pol>(tb, ch[j], Pol::fold_src_g(f1[j], g1[j], wt[j], true));
+                }
             }
         }
         V fe[NCH], be[NCH];
@@ -1442,6 +1477,13 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
         g0[e] = g1[e] = 0;
         if (e < cnt)
             rec_move<Pol>(rin, gpos(es[e]), rout, last ? -1 : o0 + p0 + e, eh[e], f0[e], f1[e], g0[e], g1[e], wt[e]);
+    }
+    if constexpr (kPreFA) {
+        // slot e * MT + thread: each thread copies and later reads only its own
+#pragma unroll
+        for (int e = 0; e < MI; ++e)
+            if (e < cnt) cp_async8(&s_fa[e * MT + threadIdx.x], &rin.fa[gpos(es[e]) * NW]);
+        cp_async_commit();
     }
     // walks from zero over the thread's elements
     const int ts = big ? MT : (int)(R2 / MI);   // threads per merged block (0/1: thread-local)
@@ -1499,6 +1541,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
         }
     }
     // target sums: read, add this level's kernel values, write on (or flush)
+    if constexpr (kPreFA) cp_async_wait_all();
 #pragma unroll
     for (int e = 0; e < MI; ++e) {
         if (e < cnt) {
@@ -1506,7 +1549,10 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
             const int64_t src = gpos(es[e]);
             FA acc[NW];
 #pragma unroll
-            for (int q = 0; q < NW; ++q) acc[q] = rin.fa[src * NW + q];
+            for (int q = 0; q < NW; ++q) {
+                if constexpr (kPreFA) acc[q] = s_fa[e * MT + threadIdx.x];
+                else acc[q] = rin.fa[src * NW + q];
+            }
             if (pol.is_tgt(item)) {
                 M sf, sb;
                 pol.signs(eh[e], em[e] >> kItemBits, sf, sb);

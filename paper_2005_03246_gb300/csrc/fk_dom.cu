@@ -434,21 +434,26 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
         ldd = (int)s_co[3];
         cnext = (uint32_t)s_co[4];
         dnext = (uint32_t)s_co[5];
-        const int64_t cs = s_co[0], ds = s_co[2];
-        for (int i = threadIdx.x; i < lc; i += GT) {
-            const int q = pd(i);
-            s_key[q] = key_in[cs + i]; s_meta[q] = meta_in[cs + i]; s_pref[q] = pref_in[cs + i]; s_acc[q] = acc_in[cs + i];
+    }
+    {
+        // Tile slot i holds C element i (i < lc) or D element i - lc of a long
+        // run, else element o0 + i.  Asynchronous copies: every thread has all
+        // its slots in flight at once (one memory round trip per tile).
+        const int64_t cs = big ? s_co[0] : 0, ds = big ? s_co[2] : 0;
+#pragma unroll
+        for (int j = 0; j < GI; ++j) {
+            const int i = (int)threadIdx.x + j * GT;
+            const int64_t g = !big ? o0 + i : (i < lc ? cs + i : ds + (i - lc));
+            if (i < ln) {
+                const int q = pd(i);
+                dc::cp_async4(&s_key[q], &key_in[g]);
+                dc::cp_async4(&s_meta[q], &meta_in[g]);
+                dc::cp_async4(&s_pref[q], &pref_in[g]);
+                dc::cp_async4(&s_acc[q], &acc_in[g]);
+            }
         }
-        for (int i = threadIdx.x; i < ldd; i += GT) {
-            const int q = pd(lc + i);
-            s_key[q] = key_in[ds + i]; s_meta[q] = meta_in[ds + i];
-            s_pref[q] = pref_in[ds + i]; s_acc[q] = acc_in[ds + i];
-        }
-    } else {
-        for (int i = threadIdx.x; i < ln; i += GT) {
-            const int q = pd(i);
-            s_key[q] = key_in[o0 + i]; s_meta[q] = meta_in[o0 + i]; s_pref[q] = pref_in[o0 + i]; s_acc[q] = acc_in[o0 + i];
-        }
+        dc::cp_async_commit();
+        dc::cp_async_wait_all();
     }
     __syncthreads();
     const int p0 = threadIdx.x * GI;
