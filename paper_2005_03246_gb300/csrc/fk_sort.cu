@@ -1,6 +1,7 @@
 // fk_sort.cu -- device-wide exclusive scan and a stable LSD radix sort of
 // (key, value) pairs, written for the rank transform of the sample-point path
 // (Sec. 2.2, Algorithm 2: the per-axis sort permutations phi^j).
+#include <algorithm>
 #include <mutex>
 
 #include "fk_internal.cuh"
@@ -102,37 +103,91 @@ fk_status scan_u32_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint3
 }
 
 // ============================================================== LSD radix sort
+// One sweep per digit: a single pass over the keys histograms every digit
+// position at once; each digit pass is then one launch whose CTAs take tiles
+// in launch order (an atomic tile counter) and find the global start of each
+// of their digit runs by a decoupled look-back over the tiles before them
+// (each tile publishes its per-digit count, then its inclusive prefix).
 namespace {
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortChunks = 16;                                  // 32-key chunks per warp
 constexpr int kSortTile = kSortThreads * kSortChunks;             // 4096 keys per CTA
+constexpr int kHistCtasPerSm = 4;
 
-template <class K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict__ keys, int64_t n,
-                                                             int shift, uint32_t* __restrict__ hist,
-                                                             int64_t tiles) {
-    __shared__ uint32_t cnt[kRadixBins];
-    for (int b = threadIdx.x; b < kRadixBins; b += kSortThreads) cnt[b] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
-    for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
-        int64_t i = base + j;
-        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & (kRadixBins - 1)], 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kRadixBins; b += kSortThreads)
-        hist[(int64_t)b * tiles + blockIdx.x] = cnt[b];
+// Look-back status word of (tile, digit): bits 63..56 the pass it belongs to
+// (pass + 1; any other value, e.g. the zero of the reset, means "not yet
+// published"), bit 55 set once the value is the inclusive prefix over tiles
+// 0..tile (clear: the tile's own count only), bits 54..0 the value.
+constexpr uint64_t kStatInc = 1ull << 55;
+constexpr uint64_t kStatVal = kStatInc - 1;
+// Bound of every look-back wait, in polls of one status word (with a short
+// sleep between polls): about a tenth of a second per thread in total.  On
+// expiry the wait records DEV_TIMEOUT in the error word and continues, so
+// the kernel always ends.
+constexpr int kLookbackPolls = 1 << 20;
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Stable scatter in two steps: the tile's keys are first ranked and placed
-// in shared memory in (digit, original position) order, then written out so
-// that consecutive threads store consecutive elements of each digit's run
-// (runs of ~16 keys per digit and tile instead of one 4-byte store per key).
-// Warp w owns keys [base + w*512, base + (w+1)*512) in chunk order, which is
-// the tile's original order, so the ranking is stable.
+// Scratch layout at the start of `tmp`: status [tiles][256] u64, the digit
+// histograms [kMaxPasses][256] u32 and the tile counters [kMaxPasses] u32;
+// all of it is zeroed once per sort.
+struct SortScratch {
+    uint64_t* status;
+    uint32_t* ghist;
+    uint32_t* ctr;
+    size_t bytes;
+    static size_t size(int64_t tiles) {
+        return (size_t)tiles * kRadixBins * 8 + (size_t)kMaxPasses * kRadixBins * 4 + 256;
+    }
+    static SortScratch at(void* tmp, int64_t tiles) {
+        SortScratch s;
+        s.status = (uint64_t*)tmp;
+        s.ghist = (uint32_t*)(s.status + (size_t)tiles * kRadixBins);
+        s.ctr = s.ghist + kMaxPasses * kRadixBins;
+        s.bytes = size(tiles);
+        return s;
+    }
+};
+
+// Histograms of all `passes` digit positions in one read of the keys.
+template <class K>
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist_all(const K* __restrict__ keys, int64_t n, int passes,
+                                                                 uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t cnt[kMaxPasses][kRadixBins];
+    for (int b = threadIdx.x; b < kMaxPasses * kRadixBins; b += kSortThreads) (&cnt[0][0])[b] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * kSortThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n; i += stride) {
+        const K k = keys[i];
+#pragma unroll
+        for (int p = 0; p < kMaxPasses; ++p)
+            if (p < passes) atomicAdd(&cnt[p][(uint32_t)(k >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < passes * kRadixBins; b += kSortThreads) {
+        const uint32_t c = (&cnt[0][0])[b];
+        if (c) atomicAdd(&ghist[b], c);
+    }
+}
+
+// Stable scatter of one digit pass in three steps: the tile's keys are ranked
+// and placed in shared memory in (digit, original position) order, the
+// global start of each digit run comes from the digit histogram and the
+// look-back, and the runs are written so that consecutive threads store
+// consecutive elements of a digit's run.  Warp w owns keys
+// [base + w*512, base + (w+1)*512) in chunk order, which is the tile's
+// original order, so the ranking is stable.
 template <class K>
 struct ScatterSmem {
     static constexpr size_t o_key = 0;
@@ -141,18 +196,35 @@ struct ScatterSmem {
     static constexpr size_t o_dstart = o_wcnt + 4 * kSortWarps * kRadixBins;
     static constexpr size_t o_gofs = o_dstart + 4 * kRadixBins;
     static constexpr size_t o_wsum = o_gofs + 4 * kRadixBins;
-    static constexpr size_t bytes = o_wsum + 4 * kSortWarps;
+    static constexpr size_t o_misc = o_wsum + 4 * 2 * kSortWarps;
+    static constexpr size_t bytes = o_misc + 16;
 };
 
+// Block-wide exclusive scan over one value per thread (256 threads); wsum
+// holds kSortWarps words.  Ends with a barrier.
+__device__ __forceinline__ uint32_t sort_block_excl(uint32_t v, uint32_t* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    __syncthreads();
+    return before + x - v;
+}
+
 template <class K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restrict__ keys,
-                                                                const uint32_t* __restrict__ vals,
-                                                                K* __restrict__ keys_out,
-                                                                uint32_t* __restrict__ vals_out,
-                                                                int64_t n, int shift,
-                                                                const uint32_t* __restrict__ offs,
-                                                                int64_t tiles) {
-    static_assert(kSortThreads == kRadixBins, "one thread per digit in the tile-local scan");
+__global__ void __launch_bounds__(kSortThreads) k_radix_onesweep(const K* __restrict__ keys,
+                                                                 const uint32_t* __restrict__ vals,
+                                                                 K* __restrict__ keys_out,
+                                                                 uint32_t* __restrict__ vals_out, int64_t n, int pass,
+                                                                 SortScratch sc, int* err) {
+    static_assert(kSortThreads == kRadixBins, "one thread per digit");
     typedef ScatterSmem<K> L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* s_key = reinterpret_cast<K*>(smem_raw + L::o_key);
@@ -161,12 +233,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
     uint32_t* dstart = reinterpret_cast<uint32_t*>(smem_raw + L::o_dstart);
     uint32_t* gofs = reinterpret_cast<uint32_t*>(smem_raw + L::o_gofs);
     uint32_t* wsum = reinterpret_cast<uint32_t*>(smem_raw + L::o_wsum);
+    uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem_raw + L::o_misc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int shift = pass * kRadixBits;
+    if (threadIdx.x == 0) *s_tile = atomicAdd(&sc.ctr[pass], 1u);
     for (int b = threadIdx.x; b < kSortWarps * kRadixBins; b += kSortThreads) (&wcnt[0][0])[b] = 0;
     __syncthreads();
-    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t tile = *s_tile;
+    const int64_t tbase = tile * kSortTile;
     const int64_t wbase = tbase + (int64_t)warp * (32 * kSortChunks);
-    // pass 1: keys into registers, per-warp digit counts
+    // keys into registers, per-warp digit counts
     K kr[kSortChunks];
     uint32_t vr[kSortChunks];
 #pragma unroll
@@ -181,37 +257,50 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
         }
     }
     __syncthreads();
-    // thread b: the tile-local start of digit b (exclusive scan over digits of
-    // the tile's counts), the start of each warp's share of it, and the
-    // global start of this tile's digit-b run
-    {
-        const int b = threadIdx.x;
-        uint32_t tot = 0;
+    // thread b owns digit b: the tile's count, published at once; the global
+    // start of digit b (exclusive scan of the pass histogram) and the count
+    // of digit b in the tiles before this one (look-back)
+    const int b = threadIdx.x;
+    uint32_t tot = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) tot += wcnt[w][b];
-        uint32_t x = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+    for (int w = 0; w < kSortWarps; ++w) tot += wcnt[w][b];
+    const uint64_t tag = (uint64_t)(pass + 1) << 56;
+    uint64_t* my = sc.status + tile * kRadixBins + b;
+    if (tile == 0) st_relaxed_u64(my, tag | kStatInc | tot);
+    else st_relaxed_u64(my, tag | tot);
+    const uint32_t ex = sort_block_excl(tot, wsum);
+    const uint32_t dg = sort_block_excl(sc.ghist[pass * kRadixBins + b], wsum + kSortWarps);
+    uint64_t before = 0;
+    if (tile > 0) {
+        int polls = 0;
+        for (int64_t t = tile - 1; t >= 0; --t) {
+            const uint64_t* q = sc.status + t * kRadixBins + b;
+            uint64_t w = ld_relaxed_u64(q);
+            while ((w & ~(kStatInc | kStatVal)) != tag && polls < kLookbackPolls) {
+                ++polls;
+                __nanosleep(64);
+                w = ld_relaxed_u64(q);
+            }
+            if ((w & ~(kStatInc | kStatVal)) != tag) {
+                if (err && *(volatile int*)err == 0) atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                break;
+            }
+            before += w & kStatVal;
+            if (w & kStatInc) break;
         }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        const uint32_t ex = before + x - tot;
-        dstart[b] = ex;
-        gofs[b] = offs[(int64_t)b * tiles + blockIdx.x];
-        uint32_t run = ex;
+        st_relaxed_u64(my, tag | kStatInc | (before + tot));
+    }
+    dstart[b] = ex;
+    gofs[b] = dg + (uint32_t)before;
+    uint32_t run = ex;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t c = wcnt[w][b];
-            wcnt[w][b] = run;
-            run += c;
-        }
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = wcnt[w][b];
+        wcnt[w][b] = run;
+        run += c;
     }
     __syncthreads();
-    // pass 2: tile-local positions, keys and values into shared memory
+    // tile-local positions, keys and values into shared memory
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int c = 0; c < kSortChunks; ++c) {
@@ -219,23 +308,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
         const bool valid = i < n;
         const unsigned active = __ballot_sync(0xffffffffu, valid);
         if (valid) {
-            const uint32_t b = (uint32_t)(kr[c] >> shift) & (kRadixBins - 1);
-            const unsigned peers = __match_any_sync(active, b);
-            const uint32_t pos = wcnt[warp][b] + __popc(peers & lt);
+            const uint32_t d = (uint32_t)(kr[c] >> shift) & (kRadixBins - 1);
+            const unsigned peers = __match_any_sync(active, d);
+            const uint32_t pos = wcnt[warp][d] + __popc(peers & lt);
             s_key[pos] = kr[c];
             s_val[pos] = vr[c];
             __syncwarp(active);
-            if ((peers & lt) == 0) wcnt[warp][b] += __popc(peers);
+            if ((peers & lt) == 0) wcnt[warp][d] += __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
-    // pass 3: runs of equal digits to consecutive global positions
+    // runs of equal digits to consecutive global positions
     const int ln = (int)min((int64_t)kSortTile, n - tbase);
     for (int j = threadIdx.x; j < ln; j += kSortThreads) {
         const K k = s_key[j];
-        const uint32_t b = (uint32_t)(k >> shift) & (kRadixBins - 1);
-        const uint32_t g = gofs[b] + ((uint32_t)j - dstart[b]);
+        const uint32_t d = (uint32_t)(k >> shift) & (kRadixBins - 1);
+        const uint32_t g = gofs[d] + ((uint32_t)j - dstart[d]);
         keys_out[g] = k;
         vals_out[g] = s_val[j];
     }
@@ -252,7 +341,7 @@ fk_status scatter_smem_attr() {
     if (dev < 0 || dev >= 64) return set_error(FK_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
-        FK_CUDA(cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        FK_CUDA(cudaFuncSetAttribute(k_radix_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)ScatterSmem<K>::bytes));
         done[dev] = true;
     }
@@ -265,22 +354,31 @@ fk_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_a
                           bool* in_alt) {
     *in_alt = false;
     if (n <= 1) return FK_OK;
-    int64_t tiles = (n + kSortTile - 1) / kSortTile;
-    int64_t hn = tiles * kRadixBins;
+    if (n >= ((int64_t)1 << 32)) return set_error(FK_ERR_UNSUPPORTED, "radix sort of 2^32 or more keys");
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
     if (radix_sort_tmp_bytes(n, key_bits) > tmp_bytes)
         return set_error(FK_ERR_WORKSPACE, "radix sort scratch too small");
-    uint32_t* hist = (uint32_t*)tmp;
-    uint32_t* stmp = hist + ((hn + 63) & ~int64_t(63));
+    const int passes = std::min(kMaxPasses, (std::max(key_bits, 1) + kRadixBits - 1) / kRadixBits);
+    const SortScratch sc = SortScratch::at(tmp, tiles);
     FK_TRY(scatter_smem_attr<K>());
+    int* errw = nullptr;
+    FK_TRY(device_error_word(&errw));
+    int dev = 0, sms = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FK_CUDA(cudaMemsetAsync(tmp, 0, sc.bytes, st));
+    {
+        ProfScope ps(PF_RADIX, (double)n * sizeof(K), st);
+        const int64_t g = std::min<int64_t>((n + kSortThreads - 1) / kSortThreads, (int64_t)sms * kHistCtasPerSm);
+        k_radix_hist_all<K><<<(unsigned)g, kSortThreads, 0, st>>>(keys, n, passes, sc.ghist);
+        FK_LAUNCH_CHECK();
+    }
     K* src_k = keys; uint32_t* src_v = vals;
     K* dst_k = keys_alt; uint32_t* dst_v = vals_alt;
-    for (int shift = 0; shift < key_bits; shift += kRadixBits) {
-        ProfScope ps(PF_RADIX, 3.0 * n * (sizeof(K) + 4), st);
-        k_radix_hist<K><<<(unsigned)tiles, kSortThreads, 0, st>>>(src_k, n, shift, hist, tiles);
-        FK_LAUNCH_CHECK();
-        FK_TRY(scan_u32_exclusive(hist, hist, hn, stmp, st));
-        k_radix_scatter<K><<<(unsigned)tiles, kSortThreads, ScatterSmem<K>::bytes, st>>>(
-            src_k, src_v, dst_k, dst_v, n, shift, hist, tiles);
+    for (int p = 0; p < passes; ++p) {
+        ProfScope ps(PF_RADIX, 2.0 * n * (sizeof(K) + 4), st);
+        k_radix_onesweep<K><<<(unsigned)tiles, kSortThreads, ScatterSmem<K>::bytes, st>>>(
+            src_k, src_v, dst_k, dst_v, n, p, sc, errw);
         FK_LAUNCH_CHECK();
         K* tk = src_k; src_k = dst_k; dst_k = tk;
         uint32_t* tv = src_v; src_v = dst_v; dst_v = tv;
@@ -292,9 +390,8 @@ fk_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_a
 
 size_t radix_sort_tmp_bytes(int64_t n, int key_bits) {
     (void)key_bits;
-    int64_t tiles = (n + kSortTile - 1) / kSortTile;
-    int64_t hn = tiles * kRadixBins;
-    return (size_t)(((hn + 63) & ~int64_t(63)) + scan_u32_tmp_words(hn)) * sizeof(uint32_t);
+    const int64_t tiles = (std::max<int64_t>(n, 1) + kSortTile - 1) / kSortTile;
+    return SortScratch::size(tiles);
 }
 
 fk_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
