@@ -482,6 +482,21 @@ fk_status fk_release_cached_memory(void);
 fk_status fk_device_status(fk_stream_t stream);
 
 /*
+ * fk_debug_lookback_timeout -- a test hook for the bounded device waits (not
+ * part of the paper's problem).  The rank transform's radix sort (Sec. 2.2)
+ * runs one launch per digit pass in which each tile of 4096 keys waits, in a
+ * decoupled look-back, for the per-digit counts the tiles before it publish;
+ * every such wait gives up after a fixed number of polls (a fraction of a
+ * second), records FK_ERR_TIMEOUT in the device error word and lets the
+ * kernel finish.  This call runs one digit pass over n zero keys (n in
+ * [8192, 2^24]) in which the first tile is never processed, so the waits run
+ * out, then returns fk_device_status(stream): FK_ERR_TIMEOUT when the bound
+ * works.  It allocates and frees its own device buffers and synchronises
+ * `stream`; the device stays usable afterwards.  Other n: FK_ERR_INVALID_ARG.
+ */
+fk_status fk_debug_lookback_timeout(int64_t n, fk_stream_t stream);
+
+/*
  * ---------------------------------------------------------------- diagnostics
  * Not part of the paper's problem statement: counters used to report
  * performance.  fk_kernel_launches returns the number of CUDA kernels this

@@ -39,6 +39,7 @@ SIGNATURES = {
     "fk_last_error": (ctypes.c_char_p, []),
     "fk_version": (ctypes.c_char_p, []),
     "fk_device_status": (I, [P]),
+    "fk_debug_lookback_timeout": (I, [I64, P]),
     "fk_ecdf_grid_workspace": (SZ, [I64, I, P, I, I]),
     "fk_ecdf_grid": (I, [P, I, I64, I, P, P, P, P, P, I, P, SZ, P]),
     "fk_kde_grid_workspace": (SZ, [I64, I, P, I]),

@@ -307,6 +307,11 @@ fk_status fk_device_status(fk_stream_t stream) {
     }
 }
 
+fk_status fk_debug_lookback_timeout(int64_t n, fk_stream_t stream) {
+    FK_TRY(radix_lookback_timeout_probe(n, (cudaStream_t)stream));
+    return fk_device_status(stream);
+}
+
 // ------------------------------------------------------------------ grid path
 static fk_status grid_validate(const void* x, fk_dtype xd, int64_t N, int d, const int64_t* M,
                                fk_path path) {

@@ -268,6 +268,7 @@ fk_status scan_u32_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint3
 
 // sort.cu -- stable LSD radix sort of (key, value) pairs.
 size_t radix_sort_tmp_bytes(int64_t n, int key_bits);
+fk_status radix_lookback_timeout_probe(int64_t n, cudaStream_t st);
 fk_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                                uint32_t* vals_alt, int64_t n, int key_bits, void* tmp,
                                size_t tmp_bytes, cudaStream_t st, bool* result_in_alt);

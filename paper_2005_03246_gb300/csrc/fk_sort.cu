@@ -124,11 +124,12 @@ constexpr int kHistCtasPerSm = 4;
 // 0..tile (clear: the tile's own count only), bits 54..0 the value.
 constexpr uint64_t kStatInc = 1ull << 55;
 constexpr uint64_t kStatVal = kStatInc - 1;
-// Bound of every look-back wait, in polls of one status word (with a short
-// sleep between polls): about a tenth of a second per thread in total.  On
-// expiry the wait records DEV_TIMEOUT in the error word and continues, so
+// Bound of every look-back wait, in polls of one status word (each an L2
+// round trip plus a short sleep): a fraction of a second per thread in total,
+// far beyond the microseconds a running predecessor tile needs to publish.
+// On expiry the wait records DEV_TIMEOUT in the error word and continues, so
 // the kernel always ends.
-constexpr int kLookbackPolls = 1 << 20;
+constexpr int kLookbackPolls = 1 << 18;
 
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
     uint64_t v;
@@ -387,6 +388,44 @@ fk_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_a
     return FK_OK;
 }
 }  // namespace
+
+// One digit pass whose first tile is never processed: the tile counter starts
+// at 1 and only tiles - 1 CTAs run, so tile 1's look-back waits on a status
+// word that nothing publishes, and every later tile reaches that word too.
+// Each wait runs out after kLookbackPolls polls and records DEV_TIMEOUT.  The
+// output is incomplete but every store stays inside it (a look-back that gave
+// up sums fewer counts than the true prefix).  Buffers are allocated and freed
+// here; the stream is synchronised before returning.
+fk_status radix_lookback_timeout_probe(int64_t n, cudaStream_t st) {
+    if (n < 2 * (int64_t)kSortTile || n > ((int64_t)1 << 24))
+        return set_error(FK_ERR_INVALID_ARG, "probe size must be in [2 * 4096, 2^24]");
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    const size_t tb = SortScratch::size(tiles);
+    void* buf = nullptr;
+    FK_CUDA(cudaMalloc(&buf, (size_t)n * 16 + tb));
+    uint32_t* k0 = (uint32_t*)buf;
+    uint32_t* v0 = k0 + n;
+    uint32_t* k1 = v0 + n;
+    uint32_t* v1 = k1 + n;
+    void* tmp = (void*)(v1 + n);
+    const SortScratch sc = SortScratch::at(tmp, tiles);
+    fk_status rc = FK_OK;
+    int* errw = nullptr;
+    const uint32_t one = 1;
+    if ((rc = scatter_smem_attr<uint32_t>()) != FK_OK || (rc = device_error_word(&errw)) != FK_OK) goto done;
+    if (cudaMemsetAsync(buf, 0, (size_t)n * 16 + tb, st) != cudaSuccess ||
+        cudaMemcpyAsync(&sc.ctr[0], &one, sizeof(one), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = set_error(FK_ERR_CUDA, "probe set-up failed");
+        goto done;
+    }
+    k_radix_onesweep<uint32_t><<<(unsigned)(tiles - 1), kSortThreads, ScatterSmem<uint32_t>::bytes, st>>>(
+        k0, v0, k1, v1, n, 0, sc, errw);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        rc = set_error(FK_ERR_CUDA, "probe launch failed");
+done:
+    cudaFree(buf);
+    return rc;
+}
 
 size_t radix_sort_tmp_bytes(int64_t n, int key_bits) {
     (void)key_bits;

@@ -124,6 +124,7 @@ CASES = [
      INVALID, "h must be > 0"),
     ("batched nothing", lambda: _lib.load().fk_batched(_sets(), 2, 0, 0, 0.1, p(OUTI), p(OUT), 0, None, 0, None),
      INVALID, "nothing requested"),
+    ("lookback probe n", lambda: _lib.load().fk_debug_lookback_timeout(100, None), INVALID, "probe size"),
     ("batched host data", lambda: _lib.load().fk_batched(_sets(), 2, 0, 3, 0.1, p(OUTI), p(OUT), 0, None, 0, None),
      INVALID, "device"),
 ]
