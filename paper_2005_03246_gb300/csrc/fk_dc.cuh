@@ -38,7 +38,7 @@ namespace fk {
 namespace dc {
 
 constexpr int MT = 256;            // threads per CTA
-constexpr int MI = 8;              // outputs per thread
+constexpr int MI = 4;              // outputs per thread
 constexpr int MTILE = MT * MI;     // outputs per CTA
 constexpr int kItemBits = 26;      // meta = item | cls << 26
 constexpr uint32_t kItemMask = (1u << kItemBits) - 1u;
@@ -465,10 +465,11 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
         if (cnt == MI) {
             uint4* kk = reinterpret_cast<uint4*>(a.key_out + p0);
             uint4* mm = reinterpret_cast<uint4*>(a.meta_out + p0);
-            kk[0] = make_uint4(ek[0], ek[1], ek[2], ek[3]);
-            kk[1] = make_uint4(ek[4], ek[5], ek[6], ek[7]);
-            mm[0] = make_uint4(em[0], em[1], em[2], em[3]);
-            mm[1] = make_uint4(em[4], em[5], em[6], em[7]);
+#pragma unroll
+            for (int v = 0; v < MI / 4; ++v) {
+                kk[v] = make_uint4(ek[4 * v], ek[4 * v + 1], ek[4 * v + 2], ek[4 * v + 3]);
+                mm[v] = make_uint4(em[4 * v], em[4 * v + 1], em[4 * v + 2], em[4 * v + 3]);
+            }
         } else {
             for (int e = 0; e < cnt; ++e) { a.key_out[p0 + e] = ek[e]; a.meta_out[p0 + e] = em[e]; }
         }
@@ -1368,7 +1369,8 @@ __device__ __forceinline__ void rec_move(const FoldRecs<Pol>& in, int64_t s, con
 template <class Pol, int CLSB, int PHASE>
 struct FoldOcc {
     static constexpr size_t bytes = sizeof(typename Pol::V) * (2 << CLSB);
-    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= 64 ? 2 : 1) : (bytes <= 48 ? 2 : 1);
+    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= 64 ? 2 : 1)
+                                                    : (bytes <= 48 ? (MI <= 4 ? 3 : 2) : 1);
 };
 
 template <class Pol, int CLSB, int PHASE>
@@ -1456,10 +1458,11 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
         if (cnt == MI) {
             uint4* kk = reinterpret_cast<uint4*>(a.key_out + q0);
             uint4* mm = reinterpret_cast<uint4*>(a.meta_out + q0);
-            kk[0] = make_uint4(ek[0], ek[1], ek[2], ek[3]);
-            kk[1] = make_uint4(ek[4], ek[5], ek[6], ek[7]);
-            mm[0] = make_uint4(em[0], em[1], em[2], em[3]);
-            mm[1] = make_uint4(em[4], em[5], em[6], em[7]);
+#pragma unroll
+            for (int v = 0; v < MI / 4; ++v) {
+                kk[v] = make_uint4(ek[4 * v], ek[4 * v + 1], ek[4 * v + 2], ek[4 * v + 3]);
+                mm[v] = make_uint4(em[4 * v], em[4 * v + 1], em[4 * v + 2], em[4 * v + 3]);
+            }
         } else {
             for (int e = 0; e < cnt; ++e) { a.key_out[q0 + e] = ek[e]; a.meta_out[q0 + e] = em[e]; }
         }
