@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(NTN) k_dom_nested(const uint32_t* __restrict__
     }
 }
 
-constexpr int GT = 256, GI = 8, GTILE = GT * GI;
+constexpr int GT = 256, GI = 4, GTILE = GT * GI;
 
 // One global merge level with propagated prefixes.  The last level flushes
 // the received counts instead of writing the state.
@@ -469,15 +469,18 @@ __global__ void __launch_bounds__(GT) k_dom_merge(const uint32_t* __restrict__ k
     if (last) return;
     const int64_t ob = o0 + p0;
     if (cnt == GI) {
-        // eight consecutive outputs per thread: two 16-byte stores per array
+        // GI consecutive outputs per thread: GI / 4 16-byte stores per array
         uint4* a = reinterpret_cast<uint4*>(key_out + ob);
         uint4* b = reinterpret_cast<uint4*>(meta_out + ob);
         uint4* c = reinterpret_cast<uint4*>(pref_out + ob);
         uint4* dd = reinterpret_cast<uint4*>(acc_out + ob);
-        a[0] = make_uint4(rk[0], rk[1], rk[2], rk[3]); a[1] = make_uint4(rk[4], rk[5], rk[6], rk[7]);
-        b[0] = make_uint4(rm[0], rm[1], rm[2], rm[3]); b[1] = make_uint4(rm[4], rm[5], rm[6], rm[7]);
-        c[0] = make_uint4(rp[0], rp[1], rp[2], rp[3]); c[1] = make_uint4(rp[4], rp[5], rp[6], rp[7]);
-        dd[0] = make_uint4(ra[0], ra[1], ra[2], ra[3]); dd[1] = make_uint4(ra[4], ra[5], ra[6], ra[7]);
+#pragma unroll
+        for (int v = 0; v < GI / 4; ++v) {
+            a[v] = make_uint4(rk[4 * v], rk[4 * v + 1], rk[4 * v + 2], rk[4 * v + 3]);
+            b[v] = make_uint4(rm[4 * v], rm[4 * v + 1], rm[4 * v + 2], rm[4 * v + 3]);
+            c[v] = make_uint4(rp[4 * v], rp[4 * v + 1], rp[4 * v + 2], rp[4 * v + 3]);
+            dd[v] = make_uint4(ra[4 * v], ra[4 * v + 1], ra[4 * v + 2], ra[4 * v + 3]);
+        }
     } else {
         for (int e = 0; e < cnt; ++e) {
             key_out[ob + e] = rk[e]; meta_out[ob + e] = rm[e]; pref_out[ob + e] = rp[e]; acc_out[ob + e] = ra[e];
