@@ -786,6 +786,10 @@ struct OuterBuffers {
     uint32_t* k[kPoolStreams + 1];   // level states: ping-pong, or a ring of S + 1 (concurrent levels)
     uint32_t* m[kPoolStreams + 1];
     uint32_t* idx;    // index of every item inside its axis-k node
+    // axis 2 with concurrent levels, for the policies whose longer levels add
+    // to the target sums in place (no atomics): the nested launch's private
+    // accumulator, summed into the caller's after the sweep
+    double* nacc;
 };
 
 // Inner sorts of concurrent levels: streams used at the lowest tree axis.
@@ -813,20 +817,21 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         idx = o.idx;
     }
     FK_TRY(gather_outer(seq, n, P[k - 1], o.k[0], o.m[0], st));
-    // Outer levels of axis 2 whose nodes fit a tile (folded sums on records,
-    // whose flushes are atomic): their inner sorts run in one launch of
-    // k_nested_fold, beside the merges and the inner sorts of the longer
-    // levels (on a stream of its own when the levels run concurrently).
+    // Outer levels of axis 2 whose nodes fit a tile (folded sums): their inner
+    // sorts run in one launch of k_nested_fold, beside the merges and the
+    // inner sorts of the longer levels (on a stream of its own when the levels
+    // run concurrently; its flushes are atomic, and it gets a private
+    // accumulator where the longer levels update target sums in place).
     int l0 = 0;
-    if constexpr (Pol::kCanFold && Pol::kRecords && CLSB <= 2) {
+    if constexpr (Pol::kCanFold && CLSB <= 2) {
         if (k == 2 && !pol.terms) {
             int lt = 0;
             while ((2 << lt) <= NFT) ++lt;
             l0 = E < lt ? E : lt;
         }
     }
-    auto launch_nested = [&](cudaStream_t s2) -> fk_status {
-        if constexpr (Pol::kCanFold && Pol::kRecords && CLSB <= 2) {
+    auto launch_nested = [&](cudaStream_t s2, const Pol& pl) -> fk_status {
+        if constexpr (Pol::kCanFold && CLSB <= 2) {
             typedef NestedCfg<Pol, CLSB> NC;
             static bool attr_set = false;
             if (!attr_set) {
@@ -837,7 +842,7 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
             const double lbytes = 4.0 * n + (double)pol.n_src * Pol::kSrcBytes +
                                   (double)pol.n_tgt * (Pol::kTgtBytes + Pol::kTgtFacBytes);
             ProfScope ps(PF_KLOCAL, (double)n * (l0 * (l0 + 1) / 2) * kKernelOpsPerItemLevel, s2, l0 * lbytes);
-            k_nested_fold<Pol, CLSB><<<grid_for(n, NFT), NFN, NC::bytes, s2>>>(seq, n, P[0], P[1], cs, l0, pol);
+            k_nested_fold<Pol, CLSB><<<grid_for(n, NFT), NFN, NC::bytes, s2>>>(seq, n, P[0], P[1], cs, l0, pl);
             FK_LAUNCH_CHECK();
         }
         return FK_OK;
@@ -861,7 +866,13 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         cudaEvent_t ready = fork.ev[0];
         cudaEvent_t* done = fork.ev + 1;
         fk_status rc = FK_OK;
-        if (l0 > 0) rc = launch_nested(fork.s[S]);
+        if (l0 > 0) {
+            Pol pn = pol;
+            if constexpr (Pol::kCanFold) {
+                if (o.nacc) pn.acc = o.nacc;
+            }
+            rc = launch_nested(fork.s[S], pn);
+        }
         for (int l = 0; l < E && rc == FK_OK; ++l) {
             const int in = l % R, out = (l + 1) % R;
             if (l >= R) {
@@ -894,7 +905,7 @@ fk_status recurse(int k, const uint32_t* seq, int64_t n, int E, const uint32_t* 
         const fk_status rj = fork.end();
         return rc != FK_OK ? rc : rj;
     }
-    if (l0 > 0) FK_TRY(launch_nested(st));
+    if (l0 > 0) FK_TRY(launch_nested(st, pol));
     int cur = 0;
     for (int l = 0; l < E; ++l) {
         MergeArgs a{o.k[cur], o.m[cur], o.k[cur ^ 1], o.m[cur ^ 1], n, l};
@@ -919,6 +930,9 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
         const int nb = (k == 2 && S > 1) ? S + 1 : 2;
         for (int q = 0; q < nb; ++q) { ob[k].k[q] = ar.take<uint32_t>(n); ob[k].m[q] = ar.take<uint32_t>(n); }
         ob[k].idx = (k < d_eff - 1) ? ar.take<uint32_t>(n) : nullptr;
+    }
+    if constexpr (Pol::kCanFold && !Pol::kRecords && CLSB <= 2) {
+        if (d_eff >= 3 && S > 1 && !pol.terms) ob[2].nacc = ar.take<double>((size_t)Pol::kNW * pol.n_tgt);
     }
     DCBuffers ib[kPoolStreams] = {};
     const int64_t ctas = (n + MTILE - 1) / MTILE;
@@ -955,10 +969,12 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
     if (d_eff - 1 >= 2) ob[d_eff - 1].idx = nullptr;
     for (int s = 1; s < S; ++s)
         if (ib[s].acc) FK_CUDA(cudaMemsetAsync(ib[s].acc, 0, sizeof(double) * Pol::kNW * pol.n_tgt, st));
+    if (ob[2].nacc) FK_CUDA(cudaMemsetAsync(ob[2].nacc, 0, sizeof(double) * Pol::kNW * pol.n_tgt, st));
     FK_TRY((recurse<Pol, CLSB>(d_eff - 1, seq_top, n, E, P, cs, pol, ob, ib, S, opts, st)));
     if constexpr (Pol::kCanFold) {
         for (int s = 1; s < S; ++s)
             if (ib[s].acc) FK_TRY(add_f64(pol.acc, ib[s].acc, Pol::kNW * pol.n_tgt, st));
+        if (ob[2].nacc) FK_TRY(add_f64(pol.acc, ob[2].nacc, Pol::kNW * pol.n_tgt, st));
     }
     return FK_OK;
 }
