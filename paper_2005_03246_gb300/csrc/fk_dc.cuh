@@ -37,9 +37,17 @@
 namespace fk {
 namespace dc {
 
-constexpr int MT = 256;            // threads per CTA
-constexpr int MI = 4;              // outputs per thread
-constexpr int MTILE = MT * MI;     // outputs per CTA
+constexpr int MT = 256;            // threads per CTA of a merge level
+// Outputs per thread of a merge level (its tile: MT x that many items): four,
+// so that the narrow channel sums fit three CTAs per SM; the wide ones (more
+// than 96 bytes of running sums per thread, e.g. the two-channel sums at
+// d = 4) need so many registers that one or two CTAs per SM fit either way,
+// and keep eight, which halves their co-rank searches per item.
+template <class Pol, int CLSB>
+struct MergeItems {
+    static constexpr int value = sizeof(typename Pol::V) * (2 << CLSB) > 96 ? 8 : 4;
+};
+constexpr int kMergeTileMin = MT * 4;   // the smallest merge tile (buffer sizing)
 constexpr int kItemBits = 26;      // meta = item | cls << 26
 constexpr uint32_t kItemMask = (1u << kItemBits) - 1u;
 
@@ -281,6 +289,7 @@ __device__ __forceinline__ void seg_scan(typename Pol::V (&fe)[NCH], typename Po
 // keys at the heads of C and D stay in registers, so an output reads only
 // its meta and the key of the head it advances.  eh: 0 from C, 1 from D; sl:
 // the output's slot in the tile.  Returns the outputs made.
+template <int MI>
 __device__ __forceinline__ int tile_merge(const uint32_t* s_key, const uint32_t* s_meta, int ln, int lc, bool big,
                                           int64_t R2l, int p0, uint32_t (&ek)[MI], uint32_t (&em)[MI], int (&eh)[MI],
                                           int (&sl)[MI]) {
@@ -327,8 +336,10 @@ struct MergeTile {
     int64_t ln, lc, cs, ds, ldd;
     bool big;
 };
+template <int MI>
 __device__ __forceinline__ MergeTile merge_tile_load(const MergeArgs& a, uint32_t* s_key, uint32_t* s_meta,
                                                      int64_t* s_co) {
+    constexpr int MTILE = MT * MI;
     const int64_t n = a.n;
     const int64_t R = (int64_t)1 << a.logR;
     const int64_t R2 = R << 1;
@@ -403,6 +414,7 @@ template <class Pol, int CLSB, int PHASE>
 __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol::V* __restrict__ totals,
                                               const typename Pol::V* __restrict__ carries) {
     typedef typename Pol::V V;
+    constexpr int MI = MergeItems<Pol, CLSB>::value, MTILE = MT * MI;
     constexpr int NCH = 2 << CLSB;
     constexpr uint32_t CMASK = (1u << CLSB) - 1u;
     constexpr int MP = MTILE + MTILE / 32;   // padded tile (bank conflicts)
@@ -415,7 +427,7 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     const int64_t R2 = (int64_t)2 << a.logR;
     const int64_t o0 = (int64_t)blockIdx.x * MTILE;
     if (o0 >= n) return;
-    const MergeTile mt = merge_tile_load(a, s_key, s_meta, s_co);
+    const MergeTile mt = merge_tile_load<MI>(a, s_key, s_meta, s_co);
     const int64_t ln = mt.ln, lc = mt.lc;
     const bool big = mt.big;
     if (PHASE == PH_TOTALS) {
@@ -1369,8 +1381,9 @@ __device__ __forceinline__ void rec_move(const FoldRecs<Pol>& in, int64_t s, con
 template <class Pol, int CLSB, int PHASE>
 struct FoldOcc {
     static constexpr size_t bytes = sizeof(typename Pol::V) * (2 << CLSB);
-    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= 64 ? 2 : 1)
-                                                    : (bytes <= 48 ? (MI <= 4 ? 3 : 2) : 1);
+    static constexpr int MI = MergeItems<Pol, CLSB>::value;
+    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= (MI <= 4 ? 96 : 64) ? 2 : 1)
+                                                    : (bytes <= 48 ? (MI <= 4 ? 3 : 2) : (MI <= 4 && bytes <= 96) ? 2 : 1);
 };
 
 template <class Pol, int CLSB, int PHASE>
@@ -1380,6 +1393,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
     typedef typename Pol::V V;
     typedef typename Pol::M M;
     typedef typename Pol::FA FA;
+    constexpr int MI = MergeItems<Pol, CLSB>::value, MTILE = MT * MI;
     constexpr int NW = Pol::kNW;
     constexpr int NCH = 2 << CLSB;
     constexpr int MP = MTILE + MTILE / 32;
@@ -1396,7 +1410,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
     const int64_t R2 = (int64_t)2 << a.logR;
     const int64_t o0 = (int64_t)blockIdx.x * MTILE;
     if (o0 >= n) return;
-    const MergeTile mt = merge_tile_load(a, s_key, s_meta, s_co);
+    const MergeTile mt = merge_tile_load<MI>(a, s_key, s_meta, s_co);
     const int64_t ln = mt.ln, lc = mt.lc;
     const bool big = mt.big;
 
@@ -1576,7 +1590,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
 // each merged block.  One warp per (block, channel, direction): each lane
 // sums a contiguous run of CTAs (in scan order), a warp scan combines the
 // lanes, and each lane writes the carries of its run.
-template <class Pol, int NCH>
+template <class Pol, int NCH, int MTILE>
 __global__ void k_carries(const typename Pol::V* __restrict__ totals, typename Pol::V* __restrict__ carries,
                           int64_t n, int logR) {
     typedef typename Pol::V V;

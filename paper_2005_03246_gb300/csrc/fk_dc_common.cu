@@ -181,7 +181,8 @@ namespace dc {
 fk_status plain_merge_level(const MergeArgs& a, cudaStream_t st) {
     PolCount dummy{};
     ProfScope ps(PF_MERGE_PLAIN, 16.0 * a.n, st);
-    k_merge<PolCount, 0, PH_PLAIN><<<grid_for(a.n, MTILE), MT, 0, st>>>(a, dummy, nullptr, nullptr);
+    k_merge<PolCount, 0, PH_PLAIN><<<grid_for(a.n, MT * MergeItems<PolCount, 0>::value), MT, 0, st>>>(a, dummy,
+                                                                                                    nullptr, nullptr);
     FK_LAUNCH_CHECK();
     return FK_OK;
 }

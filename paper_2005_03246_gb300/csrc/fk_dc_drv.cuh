@@ -681,6 +681,7 @@ template <class Pol, int CLSB>
 fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cudaStream_t st) {
     typedef typename Pol::V V;
     constexpr int NCH = 2 << CLSB;
+    constexpr int MTILE = MT * MergeItems<Pol, CLSB>::value;
     const unsigned ctas = grid_for(n, MTILE);
     // algorithmic bytes of one level: key, meta and the record in and out
     const double rec_bytes = 8.0 + 8.0 * sizeof(typename Pol::M) + 16.0 + Pol::kNW * sizeof(typename Pol::FA);
@@ -701,7 +702,7 @@ fk_status fold_levels(int64_t n, int E, int L0, const Pol& pol, DCBuffers& b, cu
             }
             const int64_t per = R2 / MTILE;
             const int64_t nblk = ((int64_t)ctas + per - 1) / per;
-            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
+            k_carries<Pol, NCH, MTILE><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
                                                                               (V*)b.carries, n, m);
             FK_LAUNCH_CHECK();
             carries = (const V*)b.carries;
@@ -742,6 +743,7 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
         return FK_OK;   // not reached: the folded records handled every level above
     } else {
     int cur = 0;
+    constexpr int MTILE = MT * MergeItems<Pol, CLSB>::value;
     const unsigned ctas = grid_for(n, MTILE);
     // algorithmic bytes of one sweep merge: keys+metas in and out, source
     // weights read once, target accumulators read and written once
@@ -759,7 +761,7 @@ fk_status inner_sort(const uint32_t* seq, int64_t n, int E, const uint32_t* P0, 
             }
             const int64_t per = R2 / MTILE;
             const int64_t nblk = ((int64_t)ctas + per - 1) / per;
-            k_carries<Pol, NCH><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
+            k_carries<Pol, NCH, MTILE><<<grid_for(nblk * NCH * 2 * 32, 256), 256, 0, st>>>((const V*)b.totals,
                                                                               (V*)b.carries, n, m);
             FK_LAUNCH_CHECK();
             a.co_read = 1;
@@ -935,7 +937,7 @@ fk_status dc_sweep(int d_eff, int64_t n, const uint32_t* const* P, const uint32_
         if (d_eff >= 3 && S > 1 && !pol.terms) ob[2].nacc = ar.take<double>((size_t)Pol::kNW * pol.n_tgt);
     }
     DCBuffers ib[kPoolStreams] = {};
-    const int64_t ctas = (n + MTILE - 1) / MTILE;
+    const int64_t ctas = (n + kMergeTileMin - 1) / kMergeTileMin;   // at most, whatever the tile
     for (int s = 0; s < S; ++s) {
         for (int q = 0; q < 2; ++q) { ib[s].k[q] = ar.take<uint32_t>(n); ib[s].m[q] = ar.take<uint32_t>(n); }
         ib[s].totals = ar.take<V>((size_t)ctas * 2 * NCH);
