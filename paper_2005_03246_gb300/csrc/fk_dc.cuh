@@ -38,14 +38,16 @@ namespace fk {
 namespace dc {
 
 constexpr int MT = 256;            // threads per CTA of a merge level
-// Outputs per thread of a merge level (its tile: MT x that many items): four,
-// so that the narrow channel sums fit three CTAs per SM; the wide ones (more
-// than 96 bytes of running sums per thread, e.g. the two-channel sums at
-// d = 4) need so many registers that one or two CTAs per SM fit either way,
-// and keep eight, which halves their co-rank searches per item.
+// Outputs per thread of a merge level (its tile: MT x that many items).  The
+// folded kernel sums on records with at most 96 bytes of running sums per
+// thread take four: their merge kernels are then held to two or three CTAs
+// per SM (FoldOcc) and hide more latency.  Everything else takes eight: the
+// wider sums need so many registers that the CTAs per SM do not change, and
+// the plain, counting and weighted merges (no occupancy bound) gain nothing
+// from smaller tiles but twice the co-rank searches per item.
 template <class Pol, int CLSB>
 struct MergeItems {
-    static constexpr int value = sizeof(typename Pol::V) * (2 << CLSB) > 96 ? 8 : 4;
+    static constexpr int value = (Pol::kRecords && sizeof(typename Pol::V) * (2 << CLSB) <= 96) ? 4 : 8;
 };
 constexpr int kMergeTileMin = MT * 4;   // the smallest merge tile (buffer sizing)
 constexpr int kItemBits = 26;      // meta = item | cls << 26
