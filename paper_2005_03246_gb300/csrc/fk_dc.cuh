@@ -338,7 +338,7 @@ struct MergeTile {
     int64_t ln, lc, cs, ds, ldd;
     bool big;
 };
-template <int MI>
+template <int MI, bool KEYS = true>   // KEYS: also stage the keys (a totals pass reads only metas)
 __device__ __forceinline__ MergeTile merge_tile_load(const MergeArgs& a, uint32_t* s_key, uint32_t* s_meta,
                                                      int64_t* s_co) {
     constexpr int MTILE = MT * MI;
@@ -399,7 +399,7 @@ __device__ __forceinline__ MergeTile merge_tile_load(const MergeArgs& a, uint32_
         const int i = (int)threadIdx.x + j * MT;
         const int64_t g = !t.big ? o0 + i : (i < t.lc ? t.cs + i : t.ds + (i - t.lc));
         if (i < t.ln) {
-            cp_async4(&s_key[mpd(i)], &a.key_in[g]);
+            if constexpr (KEYS) cp_async4(&s_key[mpd(i)], &a.key_in[g]);
             cp_async4(&s_meta[mpd(i)], &a.meta_in[g]);
         }
     }
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(MT) k_merge(MergeArgs a, Pol pol, typename Pol
     const int64_t R2 = (int64_t)2 << a.logR;
     const int64_t o0 = (int64_t)blockIdx.x * MTILE;
     if (o0 >= n) return;
-    const MergeTile mt = merge_tile_load<MI>(a, s_key, s_meta, s_co);
+    const MergeTile mt = merge_tile_load<MI, PHASE != PH_TOTALS>(a, s_key, s_meta, s_co);
     const int64_t ln = mt.ln, lc = mt.lc;
     const bool big = mt.big;
     if (PHASE == PH_TOTALS) {
@@ -1412,7 +1412,7 @@ __global__ void __launch_bounds__(MT, (FoldOcc<Pol, CLSB, PHASE>::value)) k_merg
     const int64_t R2 = (int64_t)2 << a.logR;
     const int64_t o0 = (int64_t)blockIdx.x * MTILE;
     if (o0 >= n) return;
-    const MergeTile mt = merge_tile_load<MI>(a, s_key, s_meta, s_co);
+    const MergeTile mt = merge_tile_load<MI, PHASE != PH_TOTALS>(a, s_key, s_meta, s_co);
     const int64_t ln = mt.ln, lc = mt.lc;
     const bool big = mt.big;
 
