@@ -1378,14 +1378,18 @@ __device__ __forceinline__ void rec_move(const FoldRecs<Pol>& in, int64_t s, con
 // segmented scan over threads and the inter-CTA carries give the prefix /
 // suffix before them, and every target adds the kernel values of its
 // forward and backward sums to its record (flushed on the last level).
-// Resident CTAs per SM asked of the compiler: small channel sums leave room
-// for two (sweep) or three (totals) CTAs without spilling.
+// Resident CTAs per SM asked of the compiler, by the bytes of running sums a
+// thread holds and its items per thread:
+//   sums <= 48 B (one channel, d <= 3):   totals 3, sweep 3 on 4-item tiles (2 on 8-item tiles)
+//   sums <= 96 B (d = 4, or two channels): 2 on 4-item tiles; on 8-item tiles totals 2 up to 64 B
+//   wider sums:                            1
 template <class Pol, int CLSB, int PHASE>
 struct FoldOcc {
     static constexpr size_t bytes = sizeof(typename Pol::V) * (2 << CLSB);
-    static constexpr int MI = MergeItems<Pol, CLSB>::value;
-    static constexpr int value = PHASE == PH_TOTALS ? (bytes <= 48 ? 3 : bytes <= (MI <= 4 ? 96 : 64) ? 2 : 1)
-                                                    : (bytes <= 48 ? (MI <= 4 ? 3 : 2) : (MI <= 4 && bytes <= 96) ? 2 : 1);
+    static constexpr bool small_tile = MergeItems<Pol, CLSB>::value <= 4;
+    static constexpr int totals = bytes <= 48 ? 3 : bytes <= (small_tile ? 96 : 64) ? 2 : 1;
+    static constexpr int sweep = bytes <= 48 ? (small_tile ? 3 : 2) : (small_tile && bytes <= 96) ? 2 : 1;
+    static constexpr int value = PHASE == PH_TOTALS ? totals : sweep;
 };
 
 template <class Pol, int CLSB, int PHASE>
